@@ -1,0 +1,254 @@
+"""Oracle B: the Spectral Ewald k-space algorithm (Alg. 4) written out plainly.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  FP64 numpy; numpy's
+FFT serves as the transform step (a library primitive), everything else is
+plain array code in the order of Alg. 4:
+
+  0. set-up: h, M~, L~, R, delta_L (Alg. 4 step 0; Sec. 3.3);
+  1. gridding, Eq. (gridding), on M^D x M~^(3-D) points;
+  2. FFT (D = 3), AFT (Alg. 1, D = 1, 2) or (2 M~)^3-point FFT (D = 0);
+  3. scaling, Eq. (scale), with G^{DP} of Eqs. (G_hat_3d)-(G_hat_0d), or the
+     precomputed G^{0P}_R of Alg. 3 for D = 0;
+  4. IFFT / AIFT (Alg. 2, truncating to M~ in each free direction);
+  5. gathering, Eq. (complete_integral) by the trapezoidal rule, and its
+     gradient, Eq. (force-method-1).
+
+Discrete scaling (derived from Def. 1 with the trapezoidal rule; the paper
+does not print it): with an unnormalised forward DFT and a 1/n inverse over
+the (padded) transform length,
+    phi_m = 4 pi h^3 sum_j W(x_m - x_j) [IDFT(sigma * DFT(H))]_j,
+since the free-direction quadrature weight (Delta kappa / 2 pi) = 1/(s_f M~ h)
+equals the inverse-DFT factor of the padded length.
+
+Grid arrays are indexed [ix, iy, iz]; x (and y for D = 2) are the periodic
+directions, the free ones come last.  Free-direction node j sits at
+-delta_L/2 + j h, periodic node j at j h.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import j0, j1
+
+from . import params as prm
+from .windows import Window
+
+
+def green(D: int, R: float, kper2, kap):
+    """Modified Green's functions G^{DP}([k, kappa]) of Eqs. (G_hat_3d), (G_hat_2d),
+    (G_hat_1d), (G_hat_0d).  ``kper2`` = |k|^2 of the periodic part (0 for D = 0),
+    ``kap`` = |kappa| of the free part (0 for D = 3)."""
+    kper2 = np.asarray(kper2, dtype=np.float64)
+    kap = np.asarray(kap, dtype=np.float64)
+    kper2, kap = np.broadcast_arrays(kper2, kap)
+    out = np.empty(kper2.shape)
+    tot = kper2 + kap * kap
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if D == 3:
+            out = np.where(tot > 0, 1.0 / np.where(tot > 0, tot, 1.0), 0.0)
+        elif D == 0:
+            k = kap
+            ks = np.where(k > 0, k, 1.0)
+            out = np.where(k > 0, 2.0 * (np.sin(R * ks / 2.0) / ks) ** 2, R * R / 2.0)
+        else:
+            zero = kper2 == 0
+            ks = np.where(kap > 0, kap, 1.0)
+            if D == 2:
+                g0 = np.where(kap > 0, (1.0 - np.cos(R * ks) - R * ks * np.sin(R * ks)) / ks ** 2,
+                              -R * R / 2.0)
+            else:
+                g0 = np.where(kap > 0,
+                              (1.0 - j0(R * ks)) / ks ** 2 - R * math.log(R) * j1(R * ks) / ks,
+                              R * R / 4.0 * (1.0 - 2.0 * math.log(R)))
+            out = np.where(zero, g0, 1.0 / np.where(tot > 0, tot, 1.0))
+    return out
+
+
+class SEOracle:
+    """Discrete Spectral Ewald evaluation with the paper's parameters.
+
+    window: 'gaussian', 'kb' or 'pkb'.  ``lam``, ``s0``, ``s_mt`` (= s M~),
+    ``nl`` override the Sec. 6 rules; ``eps_rel`` feeds Eqs. (estimate-s),
+    (estimate-nl).
+    """
+
+    def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
+                 eps_rel: float = 1e-10, lam=None, s0=None, s_mt=None, nl=None, nu=None,
+                 shape=None):
+        if M % 2 or P % 2 or P > M:
+            raise ValueError("M and P must be even with P <= M (Sec. 3.3)")
+        self.D, self.L, self.xi, self.M, self.P = D, L, xi, M, P
+        self.g = prm.grid(D, L, M, P, window, eps_rel=eps_rel, lam=lam, s0=s0)
+        if s_mt is not None:
+            self.g["sMt"] = s_mt
+        if nl is not None:
+            self.g["nl"] = nl
+        self.h = self.g["h"]
+        self.Mt = self.g["Mt"]
+        self.n = [M if i < D else self.Mt for i in range(3)]
+        self.off = [0.0 if i < D else self.g["dL"] / 2.0 for i in range(3)]
+        kind = window
+        self.shape = prm.shape("gaussian" if kind == "gaussian" else "kb", P) if shape is None else shape
+        self.nu = prm.degree(P) if nu is None else nu
+        self.win = Window(kind, P, self.h, self.shape, self.nu)
+        if D == 0:
+            self.GR = self._precompute_free_space()
+
+    # ---- Alg. 3 ---------------------------------------------------------
+    def _precompute_free_space(self):
+        """Alg. 3: sample G^{0P} on (s0 M~)^3 at k = 2 pi n/(s0 L~), inverse FFT,
+        keep the indices -M~ <= j <= M~-1 (wrapped) on a (2 M~)^3 grid, FFT.
+        The result is G^{0P}_R at k = pi n / L~, n = -M~..M~-1 (FFT order)."""
+        Mt, Lt, R = self.Mt, self.g["Lt"], self.g["R"]
+        ns = self.g["s0Mt"]
+        k1 = 2.0 * np.pi * np.fft.fftfreq(ns, d=Lt / Mt)          # 2 pi n / (s0 L~)
+        kk = np.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + k1[None, None, :] ** 2)
+        G = np.fft.ifftn(green(0, R, 0.0, kk)).real
+        idx = np.arange(-Mt, Mt)
+        GR = np.zeros((2 * Mt,) * 3)
+        GR[np.ix_(idx % (2 * Mt), idx % (2 * Mt), idx % (2 * Mt))] = G[np.ix_(idx % ns, idx % ns, idx % ns)]
+        return np.fft.fftn(GR).real
+
+    # ---- step 1 ----------------------------------------------------------
+    def _stencil(self, x):
+        """Grid coordinate t = (x + offset)/h per axis, the P support indices
+        j = floor(t) - P/2 + 1 ... floor(t) + P/2, and x_m - x_j = (t - j) h."""
+        P = self.P
+        t = (np.asarray(x, dtype=np.float64) + np.array(self.off)) / self.h      # (N, 3)
+        j = np.floor(t)[:, :, None] + np.arange(-P // 2 + 1, P // 2 + 1)[None, None, :]
+        dist = (t[:, :, None] - j) * self.h                                      # (N, 3, P)
+        j = j.astype(np.int64)
+        for a in range(3):
+            if a < self.D:
+                j[:, a, :] %= self.n[a]
+            elif j[:, a, :].min() < 0 or j[:, a, :].max() >= self.n[a]:
+                raise ValueError("support leaves the extended box in a free direction")
+        return j, dist
+
+    def grid_charges(self, x, q):
+        """Eq. (gridding): H_j = sum_n q_n W(x_j - x_n)_* on the M^D x M~^(3-D) grid."""
+        j, dist = self._stencil(x)
+        w = self.win(dist)                                                       # (N, 3, P)
+        H = np.zeros(self.n)
+        q = np.asarray(q, dtype=np.float64)
+        P = self.P
+        nx, ny, nz = self.n
+        for a in range(P):
+            for b in range(P):
+                for c in range(P):
+                    flat = (j[:, 0, a] * ny + j[:, 1, b]) * nz + j[:, 2, c]
+                    val = q * w[:, 0, a] * w[:, 1, b] * w[:, 2, c]
+                    H.reshape(-1)[:] += np.bincount(flat, weights=val, minlength=H.size)
+        return H
+
+    # ---- steps 2-4 -------------------------------------------------------
+    def _sigma(self, kper2, kvecs_hat, kap, kap_hats):
+        """Eq. (scale): e^{-|k|^2/4 xi^2} W^(k)^{-2} G^{DP}(k) with the 3D W^ the
+        product of 1D transforms."""
+        xi = self.xi
+        tot = kper2 + kap ** 2
+        what = kvecs_hat * kap_hats
+        return np.exp(-tot / (4.0 * xi * xi)) / what ** 2 * green(self.D, self.g["R"], kper2, kap)
+
+    def convolve(self, H):
+        """Steps 2-4 of Alg. 4: returns H~ on the same grid as H."""
+        D, h, M, Mt = self.D, self.h, self.M, self.Mt
+        hat = self.win.hat
+        if D == 3:
+            k = 2.0 * np.pi * np.fft.fftfreq(M, d=h)
+            kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+            sig = self._sigma(kx ** 2 + ky ** 2 + kz ** 2, hat(kx) * hat(ky) * hat(kz), 0.0, 1.0)
+            return np.fft.ifftn(sig * np.fft.fftn(H)).real
+        if D == 0:
+            n2 = 2 * Mt
+            Hp = np.zeros((n2,) * 3)
+            Hp[:Mt, :Mt, :Mt] = H
+            k = 2.0 * np.pi * np.fft.fftfreq(n2, d=h)                            # pi n / L~
+            kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+            sig = np.exp(-(kx ** 2 + ky ** 2 + kz ** 2) / (4.0 * self.xi ** 2)) \
+                / (hat(kx) * hat(ky) * hat(kz)) ** 2 * self.GR
+            return np.fft.ifftn(sig * np.fft.fftn(Hp)).real[:Mt, :Mt, :Mt]
+        return self._aft_scale_aift(H)
+
+    def _classes(self):
+        """Periodic-mode classes of Sec. 3.4: zero mode, I (Eq. I: a box
+        |k_i| <= 2 pi n_l / L), J (the rest), with upsampling s0, s, 1
+        (Eq. upsamplings).  Returns boolean masks over the periodic mode grid."""
+        M, D, nl = self.M, self.D, self.g["nl"]
+        m = np.fft.fftfreq(M, d=1.0 / M).astype(np.int64)                        # signed mode index
+        grids = np.meshgrid(*([m] * D), indexing="ij")
+        amax = np.max(np.abs(np.stack(grids)), axis=0)
+        zero = amax == 0
+        inner = (amax <= nl) & ~zero
+        outer = ~zero & ~inner
+        return [(zero, self.g["s0Mt"]), (inner, self.g["sMt"]), (outer, self.Mt)]
+
+    def _aft_scale_aift(self, H):
+        """Alg. 1 (AFT), scaling, Alg. 2 (AIFT) for D = 1, 2."""
+        D, h, M, Mt = self.D, self.h, self.M, self.Mt
+        hat = self.win.hat
+        per_axes = tuple(range(D))
+        free_axes_n = 3 - D
+        Hk = np.fft.fftn(H, axes=per_axes)                       # Alg. 1 step 1
+        kp = 2.0 * np.pi * np.fft.fftfreq(M, d=h)
+        kgrid = np.meshgrid(*([kp] * D), indexing="ij")
+        kper2_all = sum(g ** 2 for g in kgrid)
+        khat_all = np.prod([hat(g) for g in kgrid], axis=0)
+        out = np.empty_like(Hk)
+        for mask, nf in self._classes():                         # Alg. 1 steps 2-4
+            if not mask.any():
+                continue
+            lines = Hk[mask]                                     # (nc, Mt[, Mt])
+            padded = np.zeros((lines.shape[0],) + (nf,) * free_axes_n, dtype=complex)
+            sl = (slice(None),) + (slice(0, Mt),) * free_axes_n
+            padded[sl] = lines
+            fax = tuple(range(1, 1 + free_axes_n))
+            Fk = np.fft.fftn(padded, axes=fax)
+            kf = 2.0 * np.pi * np.fft.fftfreq(nf, d=h)            # 2 pi n / (s_f L~)
+            if free_axes_n == 1:
+                kap = np.abs(kf)[None, :]
+                kaph = hat(kf)[None, :]
+            else:
+                a, b = np.meshgrid(kf, kf, indexing="ij")
+                kap = np.sqrt(a ** 2 + b ** 2)[None]
+                kaph = (hat(a) * hat(b))[None]
+            kper2 = kper2_all[mask].reshape((-1,) + (1,) * free_axes_n)
+            khat = khat_all[mask].reshape((-1,) + (1,) * free_axes_n)
+            sig = self._sigma(kper2, khat, kap, kaph)
+            back = np.fft.ifftn(sig * Fk, axes=fax)               # Alg. 2 steps 1-3
+            out[mask] = back[sl]                                 # truncate to M~, merge (step 4)
+        return np.fft.ifftn(out, axes=per_axes).real             # Alg. 2 step 5
+
+    # ---- step 5 ----------------------------------------------------------
+    def gather(self, Ht, xt, grad: bool = False):
+        """Eq. (complete_integral) by the trapezoidal rule, and with grad=True
+        Eq. (force-method-1): the gradient with W' in place of W per axis."""
+        j, dist = self._stencil(xt)
+        w = self.win(dist)
+        dw = self.win.dx(dist) if grad else None
+        scale = 4.0 * math.pi * self.h ** 3
+        P = self.P
+        phi = np.zeros(j.shape[0])
+        g = np.zeros((j.shape[0], 3)) if grad else None
+        for a in range(P):
+            for b in range(P):
+                for c in range(P):
+                    v = Ht[j[:, 0, a], j[:, 1, b], j[:, 2, c]]
+                    phi += w[:, 0, a] * w[:, 1, b] * w[:, 2, c] * v
+                    if grad:
+                        g[:, 0] += dw[:, 0, a] * w[:, 1, b] * w[:, 2, c] * v
+                        g[:, 1] += w[:, 0, a] * dw[:, 1, b] * w[:, 2, c] * v
+                        g[:, 2] += w[:, 0, a] * w[:, 1, b] * dw[:, 2, c] * v
+        phi *= scale
+        if grad:
+            g *= scale
+        return phi, g
+
+    def potential(self, x, q, xt=None, grad: bool = False):
+        """phi~^{DP,F} (Eq. fourier_space_ewald) at the targets (default: the
+        sources) and, with grad=True, its gradient with respect to the target."""
+        H = self.grid_charges(x, q)
+        Ht = self.convolve(H)
+        return self.gather(Ht, x if xt is None else xt, grad)
+
