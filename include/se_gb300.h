@@ -1,0 +1,187 @@
+/*
+ * se_gb300.h -- C ABI of the GB300 (sm_103a) Spectral Ewald k-space library.
+ *
+ * The library computes the Fourier-space part of the Ewald potential,
+ * phi~^{DP,F} of Eq. (fourier_space_ewald), and its gradient, for N point
+ * charges in a cubic box [0, L)^3 that is periodic in its first D directions
+ * (D = 3: x, y, z; D = 2: x, y; D = 1: x; D = 0: none), by the unified
+ * Spectral Ewald method of Shamshirgar, Bagge & Tornberg, Alg. 4:
+ *   1. gridding (Eq. gridding) with a truncated Gaussian (Eq. gaussian) or a
+ *      polynomial Kaiser-Bessel window (PKB, Sec. 4.1) of P^3 support,
+ *   2. FFT; for D = 1, 2 the adaptive FFT of Alg. 1, for D = 0 a zero-padded
+ *      (2 M~)^3 FFT,
+ *   3. scaling by e^{-|k|^2/4xi^2} W^(k)^{-2} G^{DP}(k) (Eq. scale) with the
+ *      truncated Green's functions of Eqs. (G_hat_3d)-(G_hat_0d) and, for
+ *      D = 0, the precomputed G^{0P}_R of Alg. 3,
+ *   4. inverse FFT / AIFT (Alg. 2),
+ *   5. gathering (Eq. complete_integral) and, for forces, the window
+ *      gradient gather of Eq. (force-method-1).
+ *
+ * Conventions that hold for every entry point:
+ *  - Precision.  A plan is created for SE_F32 or SE_F64; every array passed
+ *    to it holds float or double accordingly.  Positions x are row-major
+ *    [N][3], charges q and potentials phi are [N], forces F are [N][3].
+ *  - Memory.  Unless SE_HOST_IO is given, x, q and every output are DEVICE
+ *    pointers owned by the caller.  The plan owns its grids, FFT plans, tables
+ *    and particle workspace; the workspace grows on demand (cudaMalloc) or
+ *    once up front through se_plan_reserve.
+ *  - Streams.  Work is issued on the plan's stream (se_plan_set_stream;
+ *    default: the legacy stream) and is asynchronous: a returned SE_OK means
+ *    the work was validated and launched.  Errors detected on the device
+ *    (coordinates outside the box in a free direction, non-finite input) are
+ *    latched in the plan and reported by se_plan_check (which synchronises)
+ *    or at the end of a call made with SE_SYNC_CHECK.
+ *  - Errors.  Every function returns an se_status; se_status_str names it.
+ *    Nothing aborts the process.  A failed call leaves the plan usable.
+ *  - Threads.  A plan must not be used by two host threads at once.
+ */
+#ifndef SE_GB300_H
+#define SE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct se_plan_s *se_plan_t;
+
+typedef enum { SE_WIN_GAUSSIAN = 0, SE_WIN_PKB = 1 } se_window;
+typedef enum { SE_F32 = 0, SE_F64 = 1 } se_dtype;
+
+typedef enum {
+    SE_OK = 0,
+    SE_EINVAL = 1,        /* an argument is out of range (message: se_last_error) */
+    SE_ENONNEUTRAL = 2,   /* SE_CHECK_NEUTRAL: |sum q| > 1e-12 sum |q| */
+    SE_EOUTOFBOX = 3,     /* a coordinate in a free direction is outside [0, L) */
+    SE_ENOMEM = 4,        /* device allocation failed */
+    SE_ECUDA = 5,         /* a CUDA runtime call failed */
+    SE_ECUFFT = 6,        /* a cuFFT call failed */
+    SE_ETIMEOUT = 7,      /* reserved for bounded device-side waits */
+    SE_ENOTFINITE = 8,    /* a position or charge is NaN or infinite */
+    SE_ECAPACITY = 9      /* the request exceeds a fixed capacity of the entry point */
+} se_status;
+
+/* Call flags (bitwise OR). */
+#define SE_ADD_SELF      1u  /* add phi^self_m = -2 xi / sqrt(pi) q_m (Sec. 2) to phi */
+#define SE_CHECK_NEUTRAL 2u  /* verify sum q = 0 first (synchronises the stream) */
+#define SE_SYNC_CHECK    4u  /* synchronise at the end and report device-side input errors */
+#define SE_HOST_IO       8u  /* x, q and the outputs are HOST pointers; the call copies
+                                them to and from the device on the plan's stream and
+                                returns after the results are in host memory */
+
+/* Optional overrides of the paper's parameter rules (Sec. 6).  A field left at
+ * its "unset" value (given in brackets) takes the paper's default. */
+typedef struct {
+    double lambda;   /* [<= 0] extension factor, M~ = 2 ceil((M + lambda P)/2); Table (lambda) */
+    double s0;       /* [<= 0] zero-mode / free-space upsampling: 2 (D=2), 2.5 (D=1), 2.8 (D=0) */
+    int    s_mt;     /* [<= 0] s M~ of the upsampled modes of the set I, Eq. (estimate-s) */
+    int    n_l;      /* [< 0]  size of the set I, Eq. (estimate-nl) */
+    int    nu;       /* [<= 0] PKB polynomial degree, min(P/2 + 2, 9) */
+    double shape;    /* [<= 0] alpha = (pi/2) P 0.91 (Gaussian) or beta = 2.5 P (PKB) */
+    double aft_eps;  /* [<= 0] relative tolerance in Eqs. (estimate-s), (estimate-nl):
+                        1e-5 for SE_F32 plans, 1e-10 for SE_F64 plans */
+    int    tile;     /* [<= 0] edge of the gridding tile in grid cells (4, 8 or 16) */
+} se_opts;
+
+/* Derived parameters of a plan (read-only report). */
+typedef struct {
+    int D, M, P, nu, Mt, s0_mt, s_mt, n_l;
+    int grid[3];          /* real grid n_x, n_y, n_z (M or M~ per axis) */
+    int tile[3];          /* gridding tile edge per axis */
+    int n_tiles;
+    double h, L, Lt, R, delta_L, xi, shape;
+    int64_t capacity;     /* particles the workspace holds now */
+    int64_t device_bytes; /* device memory held by the plan */
+} se_plan_info_t;
+
+/* Fill *o with the "unset" values. */
+void se_opts_default(se_opts *o);
+
+/* Create a plan.  box[3] = side lengths (must be equal: cubic box); D = number
+ * of periodic directions (the first D axes); xi = Ewald splitting parameter
+ * (Eq. gamma); M = grid intervals per periodic direction (even); P = window
+ * support in grid intervals (even, 2 <= P <= 16, P <= M); w, dt = window and
+ * precision; opts may be NULL.  Sec. 3.3, Alg. 4 step 0, Sec. 6.  For D = 0 the
+ * call also runs the precomputation of Alg. 3 on the current device (FP64).
+ * Errors: SE_EINVAL (arguments), SE_ENOMEM, SE_ECUDA, SE_ECUFFT. */
+se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P,
+                         se_window w, se_dtype dt, const se_opts *opts);
+
+/* Release every resource of the plan (NULL is accepted). */
+se_status se_plan_destroy(se_plan_t plan);
+
+/* Issue all later work of the plan on this CUDA stream (a cudaStream_t). */
+se_status se_plan_set_stream(se_plan_t plan, void *stream);
+
+/* Grow the particle workspace to hold n_max particles now, so that later calls
+ * with N <= n_max allocate nothing (required before capturing a CUDA graph). */
+se_status se_plan_reserve(se_plan_t plan, int64_t n_max);
+
+/* Report the derived parameters. */
+se_status se_plan_get_info(se_plan_t plan, se_plan_info_t *info);
+
+/* Synchronise the plan's stream and report (then clear) the device-side input
+ * errors latched since the last check: SE_EOUTOFBOX or SE_ENOTFINITE. */
+se_status se_plan_check(se_plan_t plan);
+
+/* phi~^{DP,F}(x_m), m = 1..N: Alg. 4 steps 1-5 (Eq. fourier_space_ewald).
+ * x [N][3], q [N] in, phi [N] out.  Periodic coordinates may take any value
+ * (they are wrapped into [0, L)); free coordinates must lie in [0, L).
+ * flags: SE_ADD_SELF, SE_CHECK_NEUTRAL, SE_SYNC_CHECK, SE_HOST_IO.
+ * N = 0 is a no-op.  Errors: SE_EINVAL, SE_ENONNEUTRAL, SE_EOUTOFBOX,
+ * SE_ENOTFINITE, SE_ENOMEM, SE_ECUDA, SE_ECUFFT. */
+se_status se_potential(se_plan_t plan, int64_t N, const void *x, const void *q, void *phi,
+                       unsigned flags);
+
+/* Fourier-space forces F_m = -q_m grad phi~(x_m) (Sec. 7.2, method 1,
+ * Eq. force-method-1: one inverse transform, gradient gather with the exact
+ * derivative of the window).  F [N][3] out; phi [N] out if non-NULL;
+ * energy (DEVICE pointer to one double, may be NULL) receives
+ * E = 1/2 sum_m q_m phi_m accumulated in FP64 (with SE_ADD_SELF the self
+ * term is part of phi and of E).  Flags and errors as se_potential. */
+se_status se_force(se_plan_t plan, int64_t N, const void *x, const void *q, void *F, void *phi,
+                   double *energy, unsigned flags);
+
+/* Vector-Jacobian product of phi = A(x) q (the adjoint of se_potential):
+ * given g = dL/dphi [N], returns g_q = dL/dq = A g [N] and
+ * g_x = dL/dx [N][3] = g_m grad_m (A q)_m + q_m grad_m (A g)_m.  The operator
+ * A = S^T G S is symmetric because the scaling is real and even in k, so
+ * the adjoint re-runs the forward pipeline on g (reverse spread/gather
+ * through the same grid).  Either output may be NULL.  Device pointers. */
+se_status se_vjp(se_plan_t plan, int64_t N, const void *x, const void *q, const void *g_phi,
+                 void *g_x, void *g_q);
+
+/* Stage profiling (measurement aid).  While enabled, every se_potential /
+ * se_force call records CUDA events between its stages on the plan's stream,
+ * waits for the call to finish, and adds each stage's duration to per-plan
+ * accumulators.  Stages (index into ms[]):
+ *   0 binning (tile counts, scan, sorted records)   1 gridding (per-tile blocks)
+ *   2 block merge into the FFT input                3 forward FFT / AFT
+ *   4 scaling                                       5 inverse FFT / AIFT
+ *   6 gathering (phi, forces)                       7 energy reduction
+ * se_plan_get_profile copies SE_N_STAGES accumulated milliseconds into ms,
+ * the number of profiled calls into *calls and the number of kernels the
+ * library launched itself (cuFFT's kernels excluded) since the plan was
+ * created into *launches; any pointer may be NULL.  Enabling resets the
+ * accumulators. */
+#define SE_N_STAGES 8
+se_status se_plan_set_profiling(se_plan_t plan, int enable);
+se_status se_plan_get_profile(se_plan_t plan, double *ms, int64_t *calls, int64_t *launches);
+
+/* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
+ * approximation-error estimates of Sec. 5.2, rounded up to even, with the
+ * error-pollution rule of Eq. error_pollution) for an absolute rms tolerance
+ * eps, splitting parameter xi, box side L and Q = sum q^2. */
+se_status se_params_from_tolerance(double eps, double xi, double L, double Q, se_window w,
+                                   int *M, int *P);
+
+/* Name of a status code; text of the last error raised in this thread. */
+const char *se_status_str(se_status s);
+const char *se_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE_GB300_H */

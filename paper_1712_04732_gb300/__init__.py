@@ -1,0 +1,218 @@
+"""GB300-native Spectral Ewald k-space library (sm_103a CUDA behind a C ABI).
+
+Computes the Fourier-space part of the Ewald potential, and its forces, for
+point charges with periodicity in 3, 2, 1 or 0 directions by the unified
+Spectral Ewald method of Shamshirgar, Bagge & Tornberg (Alg. 4).  PyTorch is
+used here only for device memory and streams; every step of the computation
+runs in the CUDA library ``_build/libse_gb300.so`` (see ``include/se_gb300.h``).
+
+    plan = Plan(D=0, L=1.0, xi=8.0, M=48, P=8, window="pkb", dtype=torch.float32)
+    phi = plan.potential(x, q)                # x (N, 3), q (N,) CUDA tensors
+    F, phi, E = plan.force(x, q, energy=True)
+    E = energy(plan, x, q); E.backward()      # dE/dx = -F, dE/dq = phi
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as nat
+from ._native import SEError
+
+__all__ = ["Plan", "SEError", "potential", "energy", "params_from_tolerance"]
+
+_WINDOWS = {"gaussian": nat.SE_WIN_GAUSSIAN, "pkb": nat.SE_WIN_PKB}
+_DTYPES = {torch.float32: nat.SE_F32, torch.float64: nat.SE_F64}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """One Spectral Ewald configuration on one GPU (``se_plan_create``).
+
+    D: periodic directions (the first D axes); L: box side; xi: Ewald splitting
+    parameter; M: grid intervals per periodic direction; P: window support;
+    window: "pkb" or "gaussian"; dtype: torch.float32 or torch.float64.
+    Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
+    shape, aft_eps, tile.
+    """
+
+    def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
+                 dtype=torch.float32, device=None, lam=None, s0=None, s_mt=None, n_l=None, nu=None,
+                 shape=None, aft_eps=None, tile=None):
+        self._lib = nat.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("the Spectral Ewald library runs on CUDA devices only")
+        self.dtype = dtype
+        self.D, self.L, self.xi, self.M, self.P, self.window = D, float(L), float(xi), M, P, window
+        o = nat.Opts()
+        self._lib.se_opts_default(ctypes.byref(o))
+        if lam is not None: o.lambda_ = lam
+        if s0 is not None: o.s0 = s0
+        if s_mt is not None: o.s_mt = s_mt
+        if n_l is not None: o.n_l = n_l
+        if nu is not None: o.nu = nu
+        if shape is not None: o.shape = shape
+        if aft_eps is not None: o.aft_eps = aft_eps
+        if tile is not None: o.tile = tile
+        box = (ctypes.c_double * 3)(L, L, L)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(self._lib.se_plan_create(ctypes.byref(h), box, D, float(xi), M, P, _WINDOWS[window],
+                                               _DTYPES[dtype], ctypes.byref(o)))
+        self._h = h
+        self._stream = None
+
+    # ------------------------------------------------------------------ admin
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.se_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = nat.Info()
+        nat.check(self._lib.se_plan_get_info(self._h, ctypes.byref(i)))
+        out = {f: getattr(i, f) for f, _ in nat.Info._fields_}
+        out["grid"] = tuple(i.grid)
+        out["tile"] = tuple(i.tile)
+        return out
+
+    def set_profiling(self, enable: bool = True):
+        nat.check(self._lib.se_plan_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self) -> dict:
+        """Accumulated per-stage milliseconds, profiled calls, library kernel launches."""
+        ms = (ctypes.c_double * nat.SE_N_STAGES)()
+        calls, launches = ctypes.c_int64(), ctypes.c_int64()
+        nat.check(self._lib.se_plan_get_profile(self._h, ms, ctypes.byref(calls), ctypes.byref(launches)))
+        return {"ms": dict(zip(nat.STAGES, list(ms))), "calls": calls.value, "launches": launches.value}
+
+    def reserve(self, n: int):
+        nat.check(self._lib.se_plan_reserve(self._h, int(n)))
+
+    def check(self):
+        nat.check(self._lib.se_plan_check(self._h))
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            nat.check(self._lib.se_plan_set_stream(self._h, ctypes.c_void_p(s)))
+            self._stream = s
+
+    def _args(self, x, q):
+        if x.device != self.device or q.device != self.device:
+            raise ValueError("x and q must live on the plan's device")
+        if x.dtype != self.dtype or q.dtype != self.dtype:
+            raise TypeError(f"x and q must be {self.dtype}")
+        x = x.contiguous()
+        q = q.contiguous()
+        if x.dim() != 2 or x.shape[1] != 3 or q.shape != (x.shape[0],):
+            raise ValueError("expected x of shape (N, 3) and q of shape (N,)")
+        self._sync_stream()
+        return x, q
+
+    @staticmethod
+    def _flags(add_self, check_neutral, sync_check):
+        return ((nat.SE_ADD_SELF if add_self else 0) | (nat.SE_CHECK_NEUTRAL if check_neutral else 0)
+                | (nat.SE_SYNC_CHECK if sync_check else 0))
+
+    # ------------------------------------------------------------------ compute
+    def potential(self, x, q, add_self=False, check_neutral=False, sync_check=False):
+        """phi~^{DP,F} at the particles (``se_potential``)."""
+        x, q = self._args(x, q)
+        phi = torch.empty(x.shape[0], dtype=self.dtype, device=self.device)
+        nat.check(self._lib.se_potential(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(phi),
+                                         self._flags(add_self, check_neutral, sync_check)))
+        return phi
+
+    def force(self, x, q, add_self=False, energy=False, want_phi=True, check_neutral=False, sync_check=False,
+              out=None):
+        """(F, phi, E): F = -q grad phi (``se_force``); E = 1/2 sum q phi (FP64) or None.
+        ``out`` = (F, phi, E) preallocated outputs (phi, E may be None)."""
+        x, q = self._args(x, q)
+        n = x.shape[0]
+        if out is not None:
+            F, phi, E = out
+        else:
+            F = torch.empty((n, 3), dtype=self.dtype, device=self.device)
+            phi = torch.empty(n, dtype=self.dtype, device=self.device) if want_phi else None
+            E = torch.empty((), dtype=torch.float64, device=self.device) if energy else None
+        nat.check(self._lib.se_force(self._h, n, _ptr(x), _ptr(q), _ptr(F), _ptr(phi), _ptr(E),
+                                     self._flags(add_self, check_neutral, sync_check)))
+        return F, phi, E
+
+    def vjp(self, x, q, g):
+        """(dL/dx, dL/dq) for phi = A(x) q and cotangent g (``se_vjp``)."""
+        x, q = self._args(x, q)
+        g = g.to(self.dtype).contiguous()
+        gx = torch.empty((x.shape[0], 3), dtype=self.dtype, device=self.device)
+        gq = torch.empty(x.shape[0], dtype=self.dtype, device=self.device)
+        nat.check(self._lib.se_vjp(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(g), _ptr(gx), _ptr(gq)))
+        return gx, gq
+
+    def force_host(self, x, q, F, phi=None, energy=None, add_self=False):
+        """``se_force`` with SE_HOST_IO on pinned host tensors (copies inside the call)."""
+        self._sync_stream()
+        flags = nat.SE_HOST_IO | (nat.SE_ADD_SELF if add_self else 0)
+        nat.check(self._lib.se_force(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(F), _ptr(phi), _ptr(energy),
+                                     flags))
+
+
+class _PotentialFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, x, q):
+        ctx.plan = plan
+        ctx.save_for_backward(x, q)
+        return plan.potential(x, q)
+
+    @staticmethod
+    def backward(ctx, g):
+        x, q = ctx.saved_tensors
+        gx, gq = ctx.plan.vjp(x, q, g)
+        return None, gx, gq
+
+
+class _EnergyFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, plan, x, q, add_self):
+        F, phi, E = plan.force(x, q, add_self=add_self, energy=True)
+        ctx.save_for_backward(F, phi)
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        F, phi = ctx.saved_tensors
+        s = gE.to(F.dtype)
+        return None, -F * s, phi * s, None
+
+
+def potential(plan: Plan, x, q):
+    """Differentiable phi~^{DP,F}(x; q): backward runs the adjoint kernel ``se_vjp``."""
+    return _PotentialFn.apply(plan, x, q)
+
+
+def energy(plan: Plan, x, q, add_self: bool = False):
+    """Differentiable E = 1/2 sum q_m phi_m (FP64): dE/dx = -F, dE/dq = phi."""
+    return _EnergyFn.apply(plan, x, q, add_self)
+
+
+def params_from_tolerance(eps: float, xi: float, L: float, Q: float, window: str = "pkb"):
+    """(M, P) from the rules of Sec. 6 (``se_params_from_tolerance``)."""
+    lib = nat.load()
+    M, P = ctypes.c_int(), ctypes.c_int()
+    nat.check(lib.se_params_from_tolerance(eps, xi, L, Q, _WINDOWS[window], ctypes.byref(M), ctypes.byref(P)))
+    return M.value, P.value

@@ -1,0 +1,394 @@
+// C ABI entry points (include/se_gb300.h): argument validation, the pipeline
+// of Alg. 4 on the plan's stream, host staging for SE_HOST_IO, error codes.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "se_internal.h"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace se {
+
+se_status fail(se_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+se_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(SE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+se_status cufft_fail(cufftResult r, const char *where)
+{
+    return fail(SE_ECUFFT, std::string(where) + ": cuFFT error " + std::to_string(int(r)));
+}
+
+// Lambert W (principal branch, x >= 0) by Halley's iteration.
+static double lambert_w(double x)
+{
+    double w = x < 3.0 ? std::log1p(x) : std::log(x) - std::log(std::log(x));
+    for (int it = 0; it < 100; ++it) {
+        const double ew = std::exp(w), f = w * ew - x;
+        const double dw = f / (ew * (w + 1.0) - (w + 2.0) * f / (2.0 * w + 2.0));
+        w -= dw;
+        if (std::fabs(dw) < 1e-15 * (1.0 + std::fabs(w))) break;
+    }
+    return w;
+}
+
+static int even_up(double v)
+{
+    int n = int(std::ceil(v - 1e-12));
+    return n + (n & 1);
+}
+
+// Pipeline of Alg. 4 for one precision.  HOST_IO stages through the plan's
+// io buffer; the neutrality check and the device-error check synchronise.
+template <typename T>
+static se_status run(se_plan_s *p, int64_t N, const void *x, const void *q, void *phi, void *F, double *energy,
+                     unsigned flags, bool grad)
+{
+    se_status st;
+    if ((st = plan_reserve(p, N)) != SE_OK) return st;
+    const T *dx = static_cast<const T *>(x);
+    const T *dq = static_cast<const T *>(q);
+    T *dphi = static_cast<T *>(phi);
+    T *dF = static_cast<T *>(F);
+    double *den = energy;
+    const bool host = flags & SE_HOST_IO;
+    cudaError_t e = cudaSuccess;
+    if (host) {
+        if ((st = plan_io_reserve(p, N)) != SE_OK) return st;
+        T *b = static_cast<T *>(p->io_buf);
+        T *bx = b, *bq = b + 3 * N, *bphi = b + 4 * N, *bF = b + 5 * N;
+        double *ben = reinterpret_cast<double *>(b + 8 * N);
+        if ((e = cudaMemcpyAsync(bx, x, sizeof(T) * 3 * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy x");
+        if ((e = cudaMemcpyAsync(bq, q, sizeof(T) * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy q");
+        dx = bx;
+        dq = bq;
+        dphi = phi ? bphi : nullptr;
+        dF = F ? bF : nullptr;
+        den = energy ? ben : nullptr;
+    }
+    if (flags & SE_CHECK_NEUTRAL) {
+        if ((st = Ops<T>::charge_sums(p, N, dq)) != SE_OK) return st;
+        double sums[2];
+        if ((e = cudaMemcpyAsync(sums, p->red, sizeof(sums), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "read charge sums");
+        if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "sync");
+        if (std::fabs(sums[0]) > 1e-12 * sums[1])
+            return fail(SE_ENONNEUTRAL, "sum of charges " + std::to_string(sums[0]) + " is not zero");
+    }
+    prof_mark(p, 0);
+    if ((st = Ops<T>::bin(p, N, dx, dq)) != SE_OK) return st;
+    if ((st = Ops<T>::spread(p, N, nullptr, p->grid_in)) != SE_OK) return st;
+    if ((st = Ops<T>::convolve(p, p->grid_in, p->grid_out)) != SE_OK) return st;
+    if ((st = Ops<T>::gather(p, N, dq, dphi, dF, den, flags & SE_ADD_SELF, grad)) != SE_OK) return st;
+    if (p->prof) {
+        if ((e = cudaEventSynchronize(p->ev[SE_N_STAGES])) != cudaSuccess) return cuda_fail(e, "profile sync");
+        for (int i = 0; i < SE_N_STAGES; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) == cudaSuccess) p->prof_ms[i] += ms;
+        }
+        ++p->prof_calls;
+    }
+    if (host) {
+        if (phi && (e = cudaMemcpyAsync(phi, dphi, sizeof(T) * N, cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy phi");
+        if (F && (e = cudaMemcpyAsync(F, dF, sizeof(T) * 3 * N, cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy F");
+        if (energy && (e = cudaMemcpyAsync(energy, den, sizeof(double), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy energy");
+        if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    }
+    if (flags & SE_SYNC_CHECK) return se_plan_check(p);
+    return SE_OK;
+}
+
+template <typename T>
+static se_status run_vjp(se_plan_s *p, int64_t N, const void *x, const void *q, const void *g, void *gx, void *gq)
+{
+    se_status st;
+    if ((st = plan_reserve(p, N)) != SE_OK) return st;
+    if ((st = plan_second_grid(p)) != SE_OK) return st;
+    const T *dx = static_cast<const T *>(x), *dq = static_cast<const T *>(q), *dg = static_cast<const T *>(g);
+    if ((st = Ops<T>::bin(p, N, dx, dq)) != SE_OK) return st;
+    if ((st = Ops<T>::spread(p, N, nullptr, p->grid_in)) != SE_OK) return st;
+    if ((st = Ops<T>::convolve(p, p->grid_in, p->grid_out)) != SE_OK) return st;
+    if ((st = Ops<T>::spread(p, N, dg, p->grid_in2)) != SE_OK) return st;
+    if ((st = Ops<T>::convolve(p, p->grid_in2, p->grid_out2)) != SE_OK) return st;
+    return Ops<T>::gather_vjp(p, N, dq, dg, p->grid_out, p->grid_out2, static_cast<T *>(gx), static_cast<T *>(gq));
+}
+
+}  // namespace se
+
+using namespace se;
+
+extern "C" {
+
+const char *se_status_str(se_status s)
+{
+    switch (s) {
+    case SE_OK: return "SE_OK";
+    case SE_EINVAL: return "SE_EINVAL";
+    case SE_ENONNEUTRAL: return "SE_ENONNEUTRAL";
+    case SE_EOUTOFBOX: return "SE_EOUTOFBOX";
+    case SE_ENOMEM: return "SE_ENOMEM";
+    case SE_ECUDA: return "SE_ECUDA";
+    case SE_ECUFFT: return "SE_ECUFFT";
+    case SE_ETIMEOUT: return "SE_ETIMEOUT";
+    case SE_ENOTFINITE: return "SE_ENOTFINITE";
+    case SE_ECAPACITY: return "SE_ECAPACITY";
+    }
+    return "SE_UNKNOWN";
+}
+
+const char *se_last_error(void) { return g_last_error.c_str(); }
+
+void se_opts_default(se_opts *o)
+{
+    if (!o) return;
+    o->lambda = 0.0;
+    o->s0 = 0.0;
+    o->s_mt = 0;
+    o->n_l = -1;
+    o->nu = 0;
+    o->shape = 0.0;
+    o->aft_eps = 0.0;
+    o->tile = 0;
+}
+
+se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P, se_window w,
+                         se_dtype dt, const se_opts *opts)
+{
+    if (!out) return fail(SE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!box) return fail(SE_EINVAL, "box is NULL");
+    if (!(box[0] > 0) || box[0] != box[1] || box[0] != box[2] || !std::isfinite(box[0]))
+        return fail(SE_EINVAL, "the box must be cubic with a positive finite side");
+    if (D < 0 || D > 3) return fail(SE_EINVAL, "D must be 0, 1, 2 or 3");
+    if (!(xi > 0) || !std::isfinite(xi)) return fail(SE_EINVAL, "xi must be positive");
+    if (M < 2 || M % 2) return fail(SE_EINVAL, "M must be even and >= 2 (Sec. 3.3)");
+    if (P < 2 || P % 2 || P > M || P > kMaxP) return fail(SE_EINVAL, "P must be even with 2 <= P <= min(M, 16) (Sec. 3.3)");
+    if (w != SE_WIN_GAUSSIAN && w != SE_WIN_PKB) return fail(SE_EINVAL, "unknown window");
+    if (dt != SE_F32 && dt != SE_F64) return fail(SE_EINVAL, "unknown dtype");
+    se_opts o;
+    se_opts_default(&o);
+    if (opts) o = *opts;
+
+    se_plan_s *p = new (std::nothrow) se_plan_s();
+    if (!p) return fail(SE_ENOMEM, "host allocation");
+    p->D = D; p->M = M; p->P = P; p->window = w; p->dtype = dt;
+    p->L = box[0]; p->xi = xi;
+    p->h = p->L / M;
+    p->inv_h = M / p->L;
+    p->tile_pref = o.tile;
+    if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
+    // Sec. 6: shape parameters and PKB degree
+    p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
+    p->nu = o.nu > 0 ? o.nu : std::min(P / 2 + 2, 9);
+    if (p->nu > kMaxNu) { delete p; return fail(SE_EINVAL, "nu must be <= 12"); }
+    p->aft_eps = o.aft_eps > 0 ? o.aft_eps : (dt == SE_F32 ? 1e-5 : 1e-10);
+    // Alg. 4 step 0 / Sec. 3.3: extended grid in the free directions
+    if (D == 3) {
+        p->Mt = M; p->Lt = p->L; p->R = 0; p->dL = 0;
+    } else {
+        static const double lam_g[3] = {1.0, 1.5, 1.5}, lam_k[3] = {1.3, 2.4, 2.4};
+        const double lam = o.lambda > 0 ? o.lambda : (w == SE_WIN_GAUSSIAN ? lam_g[D] : lam_k[D]);
+        if (lam < 1.0) { delete p; return fail(SE_EINVAL, "lambda must be >= 1 (Sec. 3.3)"); }
+        p->Mt = 2 * int(std::ceil((M + lam * P) / 2.0 - 1e-12));
+        p->Lt = p->h * p->Mt;
+        p->R = std::sqrt(double(3 - D)) * p->Lt;
+        p->dL = p->Lt - p->L;
+        static const double s0d[3] = {2.8, 2.5, 2.0};
+        p->s0 = o.s0 > 0 ? o.s0 : s0d[D];
+        if (p->s0 < 2.0) { delete p; return fail(SE_EINVAL, "s0 must be >= 2"); }
+        p->s0Mt = even_up(p->s0 * p->Mt);
+        if (D != 0) {
+            const double lg = std::log(1.0 / (2.0 * p->aft_eps)) / (2.0 * M_PI);
+            // Eqs. (estimate-s), (estimate-nl), with eps_rms / B = aft_eps
+            p->sMt = o.s_mt > 0 ? o.s_mt : even_up(M * (1.0 + lg));
+            p->nl = o.n_l >= 0 ? o.n_l : std::max(0, int(std::ceil(double(M) / (p->Mt - M) * lg - 1.0 - 1e-12)));
+            if (p->sMt < p->Mt) p->sMt = p->Mt;
+            if (p->sMt % 2) { delete p; return fail(SE_EINVAL, "s M~ must be even"); }
+            p->nl = std::min(p->nl, M / 2 - 1);
+        }
+    }
+    cudaError_t ce = cudaStreamSynchronize(nullptr);
+    if (ce != cudaSuccess) { delete p; return cuda_fail(ce, "device not usable"); }
+    se_status st = plan_build(p);
+    if (st != SE_OK) {
+        plan_release(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return SE_OK;
+}
+
+se_status se_plan_destroy(se_plan_t p)
+{
+    if (!p) return SE_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
+    for (int i = 0; i <= SE_N_STAGES; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    plan_release(p);
+    delete p;
+    return SE_OK;
+}
+
+se_status se_plan_set_stream(se_plan_t p, void *stream)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    p->stream = static_cast<cudaStream_t>(stream);
+    return plan_set_fft_stream(p);
+}
+
+se_status se_plan_reserve(se_plan_t p, int64_t n)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    if (n < 0) return fail(SE_EINVAL, "negative size");
+    return plan_reserve(p, n);
+}
+
+se_status se_plan_get_info(se_plan_t p, se_plan_info_t *info)
+{
+    if (!p || !info) return fail(SE_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->D = p->D; info->M = p->M; info->P = p->P; info->nu = p->nu; info->Mt = p->Mt;
+    info->s0_mt = p->s0Mt; info->s_mt = p->sMt; info->n_l = p->nl;
+    for (int a = 0; a < 3; ++a) { info->grid[a] = p->tg.n[a]; info->tile[a] = p->tg.T[a]; }
+    info->n_tiles = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    info->h = p->h; info->L = p->L; info->Lt = p->Lt; info->R = p->R; info->delta_L = p->dL;
+    info->xi = p->xi; info->shape = p->shape;
+    info->capacity = p->cap;
+    info->device_bytes = p->device_bytes;
+    return SE_OK;
+}
+
+se_status se_plan_check(se_plan_t p)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "check");
+    if (flag) {
+        e = cudaMemsetAsync(p->err, 0, sizeof(int), p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "check reset");
+        if (flag & 2) return fail(SE_ENOTFINITE, "a position or charge is not finite");
+        return fail(SE_EOUTOFBOX, "a coordinate in a free direction lies outside [0, L)");
+    }
+    return SE_OK;
+}
+
+static se_status check_call(se_plan_t p, int64_t N, const void *x, const void *q)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    if (N < 0) return fail(SE_EINVAL, "N < 0");
+    if (N > 0 && (!x || !q)) return fail(SE_EINVAL, "x or q is NULL");
+    return SE_OK;
+}
+
+se_status se_potential(se_plan_t p, int64_t N, const void *x, const void *q, void *phi, unsigned flags)
+{
+    se_status st = check_call(p, N, x, q);
+    if (st != SE_OK) return st;
+    if (N > 0 && !phi) return fail(SE_EINVAL, "phi is NULL");
+    if (N == 0) return SE_OK;
+    return p->dtype == SE_F32 ? run<float>(p, N, x, q, phi, nullptr, nullptr, flags, false)
+                              : run<double>(p, N, x, q, phi, nullptr, nullptr, flags, false);
+}
+
+se_status se_force(se_plan_t p, int64_t N, const void *x, const void *q, void *F, void *phi, double *energy,
+                   unsigned flags)
+{
+    se_status st = check_call(p, N, x, q);
+    if (st != SE_OK) return st;
+    if (N > 0 && !F) return fail(SE_EINVAL, "F is NULL");
+    if (N == 0) {
+        if (energy) {
+            if (flags & SE_HOST_IO) *energy = 0.0;
+            else {
+                cudaError_t e = cudaMemsetAsync(energy, 0, sizeof(double), p->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "memset energy");
+            }
+        }
+        return SE_OK;
+    }
+    return p->dtype == SE_F32 ? run<float>(p, N, x, q, phi, F, energy, flags, true)
+                              : run<double>(p, N, x, q, phi, F, energy, flags, true);
+}
+
+se_status se_vjp(se_plan_t p, int64_t N, const void *x, const void *q, const void *g, void *gx, void *gq)
+{
+    se_status st = check_call(p, N, x, q);
+    if (st != SE_OK) return st;
+    if (N > 0 && !g) return fail(SE_EINVAL, "g is NULL");
+    if (N == 0) return SE_OK;
+    return p->dtype == SE_F32 ? run_vjp<float>(p, N, x, q, g, gx, gq) : run_vjp<double>(p, N, x, q, g, gx, gq);
+}
+
+se_status se_plan_set_profiling(se_plan_t p, int enable)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    if (enable && !p->ev[0]) {
+        for (int i = 0; i <= SE_N_STAGES; ++i) {
+            cudaError_t e = cudaEventCreate(&p->ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    p->prof = enable != 0;
+    for (int i = 0; i < SE_N_STAGES; ++i) p->prof_ms[i] = 0.0;
+    p->prof_calls = 0;
+    return SE_OK;
+}
+
+se_status se_plan_get_profile(se_plan_t p, double *ms, int64_t *calls, int64_t *launches)
+{
+    if (!p) return fail(SE_EINVAL, "plan is NULL");
+    if (ms)
+        for (int i = 0; i < SE_N_STAGES; ++i) ms[i] = p->prof_ms[i];
+    if (calls) *calls = p->prof_calls;
+    if (launches) *launches = p->launches;
+    return SE_OK;
+}
+
+se_status se_params_from_tolerance(double eps, double xi, double L, double Q, se_window w, int *M, int *P)
+{
+    if (!M || !P) return fail(SE_EINVAL, "NULL output");
+    if (!(eps > 0) || !(xi > 0) || !(L > 0) || !(Q > 0)) return fail(SE_EINVAL, "arguments must be positive");
+    // B = sqrt(Q) f_c(xi L) / L, Eq. (fc-expression)
+    const double xl = xi * L;
+    const double fc = std::exp(-12.62 / (xl * xl)) * (0.8909 + 0.01411 * xl + 4.315e-5 * xl * xl);
+    const double B = std::sqrt(Q) * fc / L;
+    // M = 2 k_inf with k_inf from Eq. (KP_kinf)
+    const double arg = 4.0 / 3.0 * std::pow(Q / (M_PI * xi * L * L * L * eps * eps), 2.0 / 3.0);
+    const double kinf = std::sqrt(3.0) * xi * L / (2.0 * M_PI) * std::sqrt(lambert_w(arg));
+    int m = 2 * int(std::ceil(kinf - 1e-12));
+    // P from 2 B e^{-(pi/2) P c} (Gaussian) or 10 B e^{-2.5 P} (PKB), rounded up to even
+    double pr = (w == SE_WIN_GAUSSIAN) ? std::log(2.0 * B / eps) / (M_PI / 2.0 * std::sqrt(0.91))
+                                       : std::log(10.0 * B / eps) / 2.5;
+    int pp = std::max(2, even_up(pr));
+    // Eq. (error_pollution)
+    const double xx = m / (xi * L);
+    const double fw = (w == SE_WIN_GAUSSIAN) ? xx * xx + 0.2 * xx + 2.25 : 0.7 * xx * xx + 0.2 * xx + 1.8;
+    if (pp > fw) {
+        m = even_up(1.05 * m);
+        pp += 4;
+    }
+    *M = m;
+    *P = pp;
+    return SE_OK;
+}
+
+}  // extern "C"

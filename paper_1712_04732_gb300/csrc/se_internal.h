@@ -1,0 +1,173 @@
+// Internal declarations of the Spectral Ewald library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/se_gb300.h"
+
+namespace se {
+
+constexpr int kMaxP = 16;       // largest window support compiled in
+constexpr int kMaxNu = 12;      // largest PKB degree accepted
+constexpr int kThreads = 256;   // threads per CTA of the tile kernels
+
+// Window description passed by value to the tile kernels.  For the PKB the
+// coefficient c[j][k] multiplies xbar^j at stencil point k (k = 0..P-1 counted
+// from the lowest grid index), already mapped to the subinterval that point
+// falls in; dc[j][k] are the coefficients of 2 d/dxbar (derivative in grid
+// units).  For the Gaussian only alpha is used.
+template <typename T>
+struct WindowArgs {
+    int kind;      // SE_WIN_GAUSSIAN or SE_WIN_PKB
+    int nu;
+    T alpha;       // Gaussian shape
+    T c[(kMaxNu + 1) * kMaxP];
+    T dc[kMaxNu * kMaxP];
+};
+
+// Geometry of the gridding tiles.
+struct TileGeom {
+    int n[3];      // logical grid extent per axis
+    int periodic[3];
+    int T[3];      // tile edge
+    int nt[3];     // tiles per axis
+    int B[3];      // extended block edge T + P - 1
+    int blk;       // B0 * B1 * B2
+};
+
+// Grid accessor: element (i, j, k) of a real grid lives at
+// base[i + j * s1 + k * s2].
+struct GridView {
+    int64_t s1, s2;
+};
+
+struct Particles {   // sorted-by-tile particle records
+    void *frac_q;    // float4 / double4: fractional grid coordinate per axis, charge
+    int2 *idx_code;  // original index, packed local anchor (8 bits per axis)
+};
+
+// Per-axis scaling factors of one spectral box: sigma = norm * f0 f1 f2 / (k0 + k1 + k2)
+// with k the squared wave numbers; excl selects modes whose value is set to 0.
+template <typename T>
+struct ScaleBox {
+    int n0, n1, n2;
+    const T *f0, *f1, *f2, *k0, *k1, *k2;
+    T norm;
+    int excl;      // 0: none; 1: i0 <= nl (D = 1); 2: i0 <= nl and (i1 <= nl or i1 >= n1 - nl) (D = 2)
+    int nl;
+};
+
+}  // namespace se
+
+struct se_plan_s {
+    // ---- parameters (Alg. 4 step 0, Sec. 6) ----
+    int D = 3, M = 0, P = 0, window = 0, dtype = 0;
+    double L = 1, xi = 1, h = 1, inv_h = 1;
+    int Mt = 0, s0Mt = 0, sMt = 0, nl = 0, nu = 0;
+    double Lt = 1, R = 0, dL = 0, s0 = 0, shape = 0, aft_eps = 0;
+    double off[3] = {0, 0, 0};
+    se::TileGeom tg{};
+    std::vector<double> coef, dcoef;     // PKB coefficients in stencil order (FP64 master copy)
+    int dev = 0;
+    int tile_pref = 0;
+    cudaStream_t stream = nullptr;
+
+    // ---- device memory ----
+    size_t elem = 4;                     // sizeof(T)
+    void *grid_in = nullptr;             // real grid handed to the forward FFT
+    void *grid_out = nullptr;            // real grid returned by the inverse FFT
+    se::GridView gin{}, gout{};
+    size_t grid_in_elems = 0, grid_out_elems = 0;
+    void *spec = nullptr;                // complex spectrum of the main transform
+    size_t spec_elems = 0;
+    void *U = nullptr;                   // D = 1, 2: padded lines / planes of the set I
+    size_t U_elems = 0;
+    void *Z = nullptr;                   // D = 1, 2: padded zero mode
+    size_t Z_elems = 0;
+    int nI = 0;                          // D = 2: number of I lines
+    int2 *I_lines = nullptr;              // D = 2: (kx, ky index) of each I line
+    void *tabs = nullptr;                // per-axis scaling tables (T)
+    size_t tabs_bytes = 0;
+    se::ScaleBox<float> sb_spec_f{}, sb_U_f{};
+    se::ScaleBox<double> sb_spec_d{}, sb_U_d{};
+    void *sigma_tab = nullptr;           // D = 0: full table on the R2C box; D = 1, 2: zero mode
+    size_t sigma_elems = 0;
+    void *scratch = nullptr;             // per-tile extended blocks of the gridding
+    size_t scratch_bytes = 0;
+    int *tile_cnt = nullptr;             // n_tiles + 1
+    int *tile_off = nullptr;             // n_tiles + 1
+    double *tile_part = nullptr;         // per-tile FP64 partial sums (energy, neutrality)
+    double *red = nullptr;               // small FP64 reduction outputs
+    int *err = nullptr;                  // latched device-side input errors
+    // particle workspace
+    int64_t cap = 0;
+    int2 *tile_rank = nullptr;           // (tile, rank) per input particle
+    se::Particles prt{};
+    void *io_buf = nullptr;              // SE_HOST_IO staging (x, q, phi, F, energy)
+    size_t io_bytes = 0;
+    // second grid set for the adjoint (vjp)
+    void *grid_in2 = nullptr, *grid_out2 = nullptr;
+    // FFT plans
+    cufftHandle fwd = 0, inv = 0;        // main real <-> complex transform
+    cufftHandle free_main = 0;           // D = 1, 2: in-place free-direction transform of spec
+    cufftHandle free_I = 0, free_Z = 0;  // D = 1, 2: transforms of U and Z
+    bool have_fwd = false, have_inv = false, have_free_main = false, have_free_I = false, have_free_Z = false;
+    int64_t device_bytes = 0;
+    // profiling (se_plan_set_profiling)
+    bool prof = false;
+    cudaEvent_t ev[SE_N_STAGES + 1] = {};
+    double prof_ms[SE_N_STAGES] = {};
+    int64_t prof_calls = 0;
+    int64_t launches = 0;
+};
+
+namespace se {
+
+// Record stage boundary i when profiling (se_api.cu).
+inline void prof_mark(se_plan_s *p, int i)
+{
+    if (p->prof) cudaEventRecord(p->ev[i], p->stream);
+}
+
+// status helpers (se_api.cu)
+se_status fail(se_status s, const std::string &msg);
+se_status cuda_fail(cudaError_t e, const char *where);
+se_status cufft_fail(cufftResult r, const char *where);
+
+// allocation with accounting (se_plan.cu)
+se_status dev_alloc(se_plan_s *p, void **ptr, size_t bytes);
+void dev_free(se_plan_s *p, void **ptr);
+
+// plan construction (se_plan.cu)
+se_status plan_build(se_plan_s *p);
+se_status plan_reserve(se_plan_s *p, int64_t n);
+se_status plan_io_reserve(se_plan_s *p, int64_t n);
+se_status plan_second_grid(se_plan_s *p);
+se_status plan_set_fft_stream(se_plan_s *p);
+void plan_release(se_plan_s *p);
+
+// per-precision launchers (se_kern_f32.cu / se_kern_f64.cu)
+template <typename T>
+struct Ops {
+    // stage: bin particles into tiles, sort them; x, q device arrays
+    static se_status bin(se_plan_s *p, int64_t N, const T *x, const T *q);
+    // spread the sorted particles (or the charges g instead of q when g != nullptr)
+    // into grid `dst` (the forward-FFT input layout)
+    static se_status spread(se_plan_s *p, int64_t N, const T *g, void *dst);
+    // forward transform, scaling and inverse transform: grid_in -> grid_out
+    static se_status convolve(se_plan_s *p, void *gin, void *gout);
+    // gather phi (and grad) from grid_out at the sorted particles
+    static se_status gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, double *energy,
+                            bool add_self, bool grad);
+    // adjoint gather with two grids
+    static se_status gather_vjp(se_plan_s *p, int64_t N, const T *q, const T *g, const void *grid_q,
+                                const void *grid_g, T *gx, T *gq);
+    // device reduction of sum q and sum |q| into p->red[0..1]
+    static se_status charge_sums(se_plan_s *p, int64_t N, const T *q);
+};
+
+}  // namespace se

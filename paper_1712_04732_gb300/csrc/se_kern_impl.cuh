@@ -1,0 +1,311 @@
+// Host-side launchers of the device kernels for one arithmetic type T.
+// Included once by se_kern_f32.cu (T = float) and se_kern_f64.cu (T = double).
+#pragma once
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "se_kernels.cuh"
+
+namespace se {
+
+#define SE_LAUNCH_CHECK(where)                                      \
+    do {                                                            \
+        ++p->launches;                                              \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);         \
+    } while (0)
+
+#define SE_DISPATCH_P(PV, ...)                                                  \
+    switch (PV) {                                                               \
+    case 2: { constexpr int PP = 2; __VA_ARGS__; } break;                       \
+    case 4: { constexpr int PP = 4; __VA_ARGS__; } break;                       \
+    case 6: { constexpr int PP = 6; __VA_ARGS__; } break;                       \
+    case 8: { constexpr int PP = 8; __VA_ARGS__; } break;                       \
+    case 10: { constexpr int PP = 10; __VA_ARGS__; } break;                     \
+    case 12: { constexpr int PP = 12; __VA_ARGS__; } break;                     \
+    case 14: { constexpr int PP = 14; __VA_ARGS__; } break;                     \
+    case 16: { constexpr int PP = 16; __VA_ARGS__; } break;                     \
+    default: return fail(SE_EINVAL, "window support P not compiled in");        \
+    }
+
+static inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+static inline size_t al16(size_t n) { return (n + 15) & ~size_t(15); }
+
+template <typename T>
+static BinArgs<T> bin_args(const se_plan_s *p)
+{
+    BinArgs<T> a;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = p->tg.n[d];
+        a.periodic[d] = p->tg.periodic[d];
+        a.T[d] = p->tg.T[d];
+        a.nt[d] = p->tg.nt[d];
+        a.off[d] = T(p->off[d]);
+        // largest representable t below M + delta_M/2 (free axes): keeps the
+        // support inside the extended grid for x within an ulp of L
+        double tm = (p->L + p->off[d]) * p->inv_h;
+        a.tmax[d] = std::nextafter(T(tm), T(0));
+        if (double(a.tmax[d]) >= tm) a.tmax[d] = std::nextafter(a.tmax[d], T(0));
+    }
+    a.L = T(p->L);
+    a.inv_L = T(1.0 / p->L);
+    a.inv_h = T(p->inv_h);
+    a.half = p->P / 2 - 1;
+    return a;
+}
+
+template <typename T>
+static WindowArgs<T> window_args(const se_plan_s *p)
+{
+    WindowArgs<T> w;
+    std::memset(&w, 0, sizeof(w));
+    w.kind = p->window;
+    w.nu = p->nu;
+    w.alpha = T(p->shape);
+    if (p->window == SE_WIN_PKB) {
+        for (size_t i = 0; i < p->coef.size(); ++i) w.c[i] = T(p->coef[i]);
+        for (size_t i = 0; i < p->dcoef.size(); ++i) w.dc[i] = T(p->dcoef[i]);
+    }
+    return w;
+}
+
+template <typename T>
+static size_t spread_smem(const se_plan_s *p)
+{
+    const int nw = kThreads / 32;
+    return (al16(p->tg.blk) + al16((p->nu + 1) * p->P) + size_t(nw) * 3 * p->P) * sizeof(T);
+}
+
+template <typename T>
+static size_t gather_smem(const se_plan_s *p, int nblocks)
+{
+    const int nw = kThreads / 32;
+    return (nblocks * al16(p->tg.blk) + al16((p->nu + 1) * p->P) + al16(p->nu * p->P) +
+            size_t(nw) * 6 * p->P) * sizeof(T);
+}
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory; the attribute is
+// set once per kernel and size (so that captured launches make no such call).
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::unordered_map<const void *, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(reinterpret_cast<const void *>(kernel));
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) done[reinterpret_cast<const void *>(kernel)] = bytes;
+    return e;
+}
+
+template <typename T>
+se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
+{
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    cudaError_t e = cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * (nt + 1), p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
+    BinArgs<T> a = bin_args<T>(p);
+    k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err);
+    SE_LAUNCH_CHECK("bin_count");
+    k_scan<<<1, 1024, 0, p->stream>>>(nt, p->tile_cnt, p->tile_off);
+    SE_LAUNCH_CHECK("scan");
+    k_bin_scatter<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(
+        a, N, x, q, p->tile_off, p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
+        p->prt.idx_code);
+    SE_LAUNCH_CHECK("bin_scatter");
+    prof_mark(p, 1);
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::spread(se_plan_s *p, int64_t N, const T *g, void *dst)
+{
+    (void)N;
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    const size_t sm = spread_smem<T>(p);
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    SE_DISPATCH_P(p->P, {
+        auto kern = k_spread<T, PP>;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, g, wa,
+                                              reinterpret_cast<T *>(p->scratch));
+    });
+    SE_LAUNCH_CHECK("spread");
+    prof_mark(p, 2);
+    const int64_t ng = int64_t(p->tg.n[0]) * p->tg.n[1] * p->tg.n[2];
+    k_merge<T><<<blocks_for(ng, 256), 256, 0, p->stream>>>(p->tg, p->P, p->tile_off,
+                                                            reinterpret_cast<const T *>(p->scratch),
+                                                            reinterpret_cast<T *>(dst), p->gin);
+    SE_LAUNCH_CHECK("merge");
+    prof_mark(p, 3);
+    return SE_OK;
+}
+
+// cuFFT wrappers per precision
+static inline cufftResult fft_r2c(cufftHandle h, float *in, cufftComplex *out) { return cufftExecR2C(h, in, out); }
+static inline cufftResult fft_r2c(cufftHandle h, double *in, cufftDoubleComplex *out) { return cufftExecD2Z(h, in, out); }
+static inline cufftResult fft_c2r(cufftHandle h, cufftComplex *in, float *out) { return cufftExecC2R(h, in, out); }
+static inline cufftResult fft_c2r(cufftHandle h, cufftDoubleComplex *in, double *out) { return cufftExecZ2D(h, in, out); }
+static inline cufftResult fft_c2c(cufftHandle h, cufftComplex *d, int dir) { return cufftExecC2C(h, d, d, dir); }
+static inline cufftResult fft_c2c(cufftHandle h, cufftDoubleComplex *d, int dir) { return cufftExecZ2Z(h, d, d, dir); }
+
+template <typename T> static const ScaleBox<T> &sb_spec(const se_plan_s *p);
+template <> const ScaleBox<float> &sb_spec<float>(const se_plan_s *p) { return p->sb_spec_f; }
+template <> const ScaleBox<double> &sb_spec<double>(const se_plan_s *p) { return p->sb_spec_d; }
+template <typename T> static const ScaleBox<T> &sb_U(const se_plan_s *p);
+template <> const ScaleBox<float> &sb_U<float>(const se_plan_s *p) { return p->sb_U_f; }
+template <> const ScaleBox<double> &sb_U<double>(const se_plan_s *p) { return p->sb_U_d; }
+
+template <typename T>
+se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
+{
+    using C = typename Cplx<T>::type;
+    C *spec = reinterpret_cast<C *>(p->spec);
+    cufftResult r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec);
+    if (r != CUFFT_SUCCESS) return cufft_fail(r, "forward transform");
+    if (p->D == 3 || p->D == 0) prof_mark(p, 4);
+    if (p->D == 3) {
+        const ScaleBox<T> &sb = sb_spec<T>(p);
+        k_scale_box<T><<<blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256), 256, 0, p->stream>>>(sb, spec);
+        SE_LAUNCH_CHECK("scale");
+        prof_mark(p, 5);
+    } else if (p->D == 0) {
+        k_scale_tab<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(
+            int64_t(p->spec_elems), reinterpret_cast<const T *>(p->sigma_tab), spec);
+        SE_LAUNCH_CHECK("scale");
+        prof_mark(p, 5);
+    } else {
+        C *U = reinterpret_cast<C *>(p->U);
+        C *Z = reinterpret_cast<C *>(p->Z);
+        const int row = p->M / 2 + 1;
+        // Alg. 1 steps 2-3: zero mode and set I into their padded buffers
+        if (p->D == 2) {
+            const int64_t n = int64_t(p->nI) * p->sMt + p->s0Mt;
+            k_pad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, p->s0Mt, row,
+                                                                   int64_t(p->M) * row, spec, U, Z);
+        } else {
+            const int64_t n = int64_t(p->nl) * p->sMt * p->sMt + int64_t(p->s0Mt) * p->s0Mt;
+            k_pad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
+        }
+        SE_LAUNCH_CHECK("pad");
+        // Alg. 1 steps 2-4: free-direction transforms of every class
+        if ((r = fft_c2c(p->free_main, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "free fwd");
+        if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "I fwd");
+        if ((r = fft_c2c(p->free_Z, Z, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "zero fwd");
+        prof_mark(p, 4);
+        // Eq. (scale) per class
+        const ScaleBox<T> &sb = sb_spec<T>(p);
+        k_scale_box<T><<<blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256), 256, 0, p->stream>>>(sb, spec);
+        SE_LAUNCH_CHECK("scale J");
+        if (p->have_free_I) {
+            const ScaleBox<T> &su = sb_U<T>(p);
+            k_scale_box<T><<<blocks_for(int64_t(su.n0) * su.n1 * su.n2, 256), 256, 0, p->stream>>>(su, U);
+            SE_LAUNCH_CHECK("scale I");
+        }
+        k_scale_tab<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(
+            int64_t(p->Z_elems), reinterpret_cast<const T *>(p->sigma_tab), Z);
+        SE_LAUNCH_CHECK("scale 0");
+        prof_mark(p, 5);
+        // Alg. 2 steps 1-3
+        if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "free inv");
+        if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "I inv");
+        if ((r = fft_c2c(p->free_Z, Z, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "zero inv");
+        // Alg. 2 steps 2-4: truncate to M~ and merge back
+        if (p->D == 2) {
+            const int64_t n = int64_t(p->nI) * p->Mt + p->Mt;
+            k_unpad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, row,
+                                                                     int64_t(p->M) * row, spec, U, Z);
+        } else {
+            const int64_t n = int64_t(p->nl) * p->Mt * p->Mt + int64_t(p->Mt) * p->Mt;
+            k_unpad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
+        }
+        SE_LAUNCH_CHECK("unpad");
+    }
+    r = fft_c2r(p->inv, spec, reinterpret_cast<T *>(gout));
+    if (r != CUFFT_SUCCESS) return cufft_fail(r, "inverse transform");
+    prof_mark(p, 6);
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, double *energy, bool add_self,
+                         bool grad)
+{
+    (void)N;
+    (void)q;
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    const size_t sm = gather_smem<T>(p, 1);
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    const T self = add_self ? T(-2.0 * p->xi / std::sqrt(M_PI)) : T(0);
+    double *part = energy ? p->tile_part : nullptr;
+    const T *grid = reinterpret_cast<const T *>(p->grid_out);
+    SE_DISPATCH_P(p->P, {
+        if (grad) {
+            auto kern = k_gather<T, PP, true>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+            kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi, F,
+                                                  part, T(p->inv_h), self);
+        } else {
+            auto kern = k_gather<T, PP, false>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+            kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi,
+                                                  nullptr, part, T(p->inv_h), self);
+        }
+    });
+    SE_LAUNCH_CHECK("gather");
+    prof_mark(p, 7);
+    if (energy) {
+        k_sum_fixed<<<1, 256, 0, p->stream>>>(nt, p->tile_part, energy);
+        SE_LAUNCH_CHECK("energy");
+    }
+    prof_mark(p, 8);
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::gather_vjp(se_plan_s *p, int64_t N, const T *q, const T *g, const void *grid_q,
+                             const void *grid_g, T *gx, T *gq)
+{
+    (void)N;
+    (void)q;
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    const size_t sm = gather_smem<T>(p, 2);
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    SE_DISPATCH_P(p->P, {
+        auto kern = k_gather_vjp<T, PP>;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e != cudaSuccess) return cuda_fail(e, "vjp smem attribute");
+        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa,
+                                              reinterpret_cast<const T *>(grid_q), reinterpret_cast<const T *>(grid_g),
+                                              p->gout, g, gx, gq, T(p->inv_h));
+    });
+    SE_LAUNCH_CHECK("gather_vjp");
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::charge_sums(se_plan_s *p, int64_t N, const T *q)
+{
+    const int nb = 64;
+    k_charge_part<T><<<nb, 256, 0, p->stream>>>(N, q, p->tile_part);
+    SE_LAUNCH_CHECK("charge sums");
+    k_sum_fixed<<<1, 256, 0, p->stream>>>(nb, p->tile_part, p->red);
+    k_sum_fixed<<<1, 256, 0, p->stream>>>(nb, p->tile_part + nb, p->red + 1);
+    SE_LAUNCH_CHECK("charge sums");
+    return SE_OK;
+}
+
+template struct Ops<T_INST>;
+
+}  // namespace se

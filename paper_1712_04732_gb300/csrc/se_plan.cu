@@ -1,0 +1,615 @@
+// Plan construction: the parameters of Alg. 4 step 0 and Sec. 6, the PKB fit
+// (Sec. 4.1), the scaling tables of Eq. (scale) with the truncated Green's
+// functions, the FP64 precomputation of Alg. 3 (D = 0), device buffers and
+// cuFFT plans.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "se_internal.h"
+
+namespace se {
+
+// ------------------------------------------------------------ allocation
+
+se_status dev_alloc(se_plan_s *p, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) return SE_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(SE_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+    }
+    p->device_bytes += int64_t(bytes);
+    return SE_OK;
+}
+
+void dev_free(se_plan_s *p, void **ptr)
+{
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    (void)p;
+}
+
+// ------------------------------------------------------------ host special functions
+
+// Modified Bessel function I0 by its power series sum ((x/2)^2)^k / (k!)^2
+// (all terms positive: no cancellation).
+static double bessel_i0(double x)
+{
+    double t = 1.0, s = 1.0, y = 0.25 * x * x;
+    for (int k = 1; k < 500; ++k) {
+        t *= y / (double(k) * k);
+        s += t;
+        if (t < 1e-17 * s) break;
+    }
+    return s;
+}
+
+// Kaiser-Bessel window, Eq. (kaiser_window).
+static double kb_window(double x, double w, double beta)
+{
+    double r = x / w;
+    if (std::fabs(r) > 1.0) return 0.0;
+    return bessel_i0(beta * std::sqrt(1.0 - r * r)) / bessel_i0(beta);
+}
+
+// Fourier transform of the window used in the scaling: the untruncated
+// Gaussian (Sec. 4) or Eq. (kaiser_ft) (continued past k w = beta by
+// sin(sqrt(k^2 w^2 - beta^2)) / sqrt(.)).
+static double window_hat(int kind, double k, double w, double shape)
+{
+    if (kind == SE_WIN_GAUSSIAN) return std::sqrt(M_PI / shape) * w * std::exp(-k * k * w * w / (4.0 * shape));
+    double a = shape * shape - k * k * w * w;
+    double f;
+    if (a > 0) { double r = std::sqrt(a); f = std::sinh(r) / r; }
+    else if (a < 0) { double r = std::sqrt(-a); f = std::sin(r) / r; }
+    else f = 1.0;
+    return 2.0 * w * f / bessel_i0(shape);
+}
+
+// Truncated Green's functions at periodic wave vector zero, Eqs. (G_hat_2d)
+// and (G_hat_1d); kap = |kappa|.
+static double green_zero_2p(double R, double kap)
+{
+    if (kap == 0.0) return -R * R / 2.0;
+    return (1.0 - std::cos(R * kap) - R * kap * std::sin(R * kap)) / (kap * kap);
+}
+
+static double green_zero_1p(double R, double kap)
+{
+    if (kap == 0.0) return R * R / 4.0 * (1.0 - 2.0 * std::log(R));
+    return (1.0 - ::j0(R * kap)) / (kap * kap) - R * std::log(R) * ::j1(R * kap) / kap;
+}
+
+// Solve the (n x n) system A c = b by Gaussian elimination with partial pivoting.
+static void solve_dense(std::vector<double> A, std::vector<double> b, int n, double *c)
+{
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) std::swap(A[col * n + j], A[piv * n + j]);
+            std::swap(b[col], b[piv]);
+        }
+        for (int r = col + 1; r < n; ++r) {
+            double f = A[r * n + col] / A[col * n + col];
+            for (int j = col; j < n; ++j) A[r * n + j] -= f * A[col * n + j];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < n; ++j) s -= A[r * n + j] * c[j];
+        c[r] = s / A[r * n + r];
+    }
+}
+
+// PKB fit (Sec. 4.1, Eqs. polynomial-ansatz, polynomial-linsys): on subinterval
+// i = 0..P-1 of the support [-w, w] the degree-nu polynomial in
+// xbar = 2 (x - x_i)/h - 1 interpolating W_KB at the Chebyshev points
+// xbar_k = cos(pi (k - 1/2)/(nu + 1)).  Stored per stencil point k = P-1-i
+// (the point at offset k from the lowest support index lies in subinterval
+// P-1-k, with xbar = 2 frac - 1): coef[j P + k]; dcoef[j P + k] holds the
+// coefficients of 2 d/dxbar, the derivative in grid units.
+static void fit_pkb(se_plan_s *p)
+{
+    const int P = p->P, nu = p->nu, n = nu + 1;
+    const double h = p->h, w = P * h / 2.0, beta = p->shape;
+    std::vector<double> nodes(n), V(n * n);
+    for (int k = 0; k < n; ++k) {
+        nodes[k] = std::cos(M_PI * (k + 0.5) / n);
+        double t = 1.0;
+        for (int j = 0; j < n; ++j) { V[k * n + j] = t; t *= nodes[k]; }
+    }
+    p->coef.assign(size_t(n) * P, 0.0);
+    p->dcoef.assign(size_t(nu) * P, 0.0);
+    std::vector<double> c(n), rhs(n);
+    for (int i = 0; i < P; ++i) {
+        const double xi = -w + i * h;
+        for (int k = 0; k < n; ++k) rhs[k] = kb_window((nodes[k] + 1.0) / 2.0 * h + xi, w, beta);
+        solve_dense(V, rhs, n, c.data());
+        const int kk = P - 1 - i;
+        for (int j = 0; j < n; ++j) p->coef[size_t(j) * P + kk] = c[j];
+        for (int j = 0; j < nu; ++j) p->dcoef[size_t(j) * P + kk] = 2.0 * (j + 1) * c[j + 1];
+    }
+}
+
+// Per-axis factor of Eq. (scale) on a transform of length nf with spacing h:
+// f(k) = e^{-k^2/(4 xi^2)} / W^0(k)^2 and k^2, at k = 2 pi m / (nf h), m signed.
+static void axis_tables(const se_plan_s *p, int nf, std::vector<double> &f, std::vector<double> &k2)
+{
+    f.resize(nf);
+    k2.resize(nf);
+    const double w = p->P * p->h / 2.0;
+    for (int m = 0; m < nf; ++m) {
+        int ms = (m < (nf + 1) / 2) ? m : m - nf;
+        if (nf % 2 == 0 && m == nf / 2) ms = -nf / 2;
+        const double k = 2.0 * M_PI * ms / (nf * p->h);
+        const double wh = window_hat(p->window, k, w, p->shape);
+        f[m] = std::exp(-k * k / (4.0 * p->xi * p->xi)) / (wh * wh);
+        k2[m] = k * k;
+    }
+}
+
+// ------------------------------------------------------------ Alg. 3 (D = 0), FP64 on the device
+
+__global__ void k_green0_samples(int ns, double dk, double R, cufftDoubleComplex *out)
+{
+    const int64_t n = int64_t(ns) * ns * ns;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int a = int(i % ns), b = int((i / ns) % ns), c = int(i / (int64_t(ns) * ns));
+    const int sa = a < ns / 2 ? a : a - ns, sb = b < ns / 2 ? b : b - ns, sc = c < ns / 2 ? c : c - ns;
+    const double k = dk * sqrt(double(sa) * sa + double(sb) * sb + double(sc) * sc);
+    double g;
+    if (k == 0.0) g = R * R / 2.0;                         // Eq. (G_hat_0d) at k = 0
+    else { const double s = sin(R * k / 2.0) / k; g = 2.0 * s * s; }
+    out[i].x = g;
+    out[i].y = 0.0;
+}
+
+// keep j in [-M~, M~ - 1]^3 (wrapped) of the (s0 M~)^3 inverse transform on a (2 M~)^3 grid
+__global__ void k_green0_truncate(int ns, int Mt, double scale, const cufftDoubleComplex *in, double *out)
+{
+    const int n2 = 2 * Mt;
+    const int64_t n = int64_t(n2) * n2 * n2;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int a = int(i % n2), b = int((i / n2) % n2), c = int(i / (int64_t(n2) * n2));
+    const int sa = a < Mt ? a : a - n2, sb = b < Mt ? b : b - n2, sc = c < Mt ? c : c - n2;
+    const int ia = (sa + ns) % ns, ib = (sb + ns) % ns, ic = (sc + ns) % ns;
+    out[i] = in[(int64_t(ic) * ns + ib) * ns + ia].x * scale;
+}
+
+template <typename T>
+__global__ void k_sigma0(int Mt, double norm, const double *fax, const cufftDoubleComplex *gr, T *out)
+{
+    const int n2 = 2 * Mt, nx = Mt + 1;
+    const int64_t n = int64_t(n2) * n2 * nx;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int a = int(i % nx), b = int((i / nx) % n2), c = int(i / (int64_t(nx) * n2));
+    out[i] = T(norm * fax[a] * fax[b] * fax[c] * gr[i].x);
+}
+
+static se_status precompute_free_space(se_plan_s *p)
+{
+    const int Mt = p->Mt, ns = p->s0Mt, n2 = 2 * Mt;
+    const int64_t nsamp = int64_t(ns) * ns * ns;
+    const int64_t ngr = int64_t(n2) * n2 * n2;
+    const int64_t nhat = int64_t(n2) * n2 * (Mt + 1);
+    void *samp = nullptr, *gr = nullptr, *grh = nullptr, *fax = nullptr;
+    se_status st = SE_OK;
+    cufftHandle h1 = 0, h2 = 0;
+    bool have1 = false, have2 = false;
+    cufftResult r;
+    std::vector<double> f, k2;
+    axis_tables(p, n2, f, k2);
+    const double norm = 4.0 * M_PI * p->h * p->h * p->h / (double(n2) * n2 * n2);
+    if ((st = dev_alloc(p, &samp, sizeof(cufftDoubleComplex) * nsamp)) != SE_OK) goto done;
+    if ((st = dev_alloc(p, &gr, sizeof(double) * ngr)) != SE_OK) goto done;
+    if ((st = dev_alloc(p, &grh, sizeof(cufftDoubleComplex) * nhat)) != SE_OK) goto done;
+    if ((st = dev_alloc(p, &fax, sizeof(double) * n2)) != SE_OK) goto done;
+    if (cudaMemcpy(fax, f.data(), sizeof(double) * n2, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError(), "precompute upload");
+        goto done;
+    }
+    // step 1: samples of G^{0P} at k = 2 pi n / (s0 L~)
+    k_green0_samples<<<unsigned((nsamp + 255) / 256), 256, 0, p->stream>>>(ns, 2.0 * M_PI / (ns * p->h), p->R,
+                                                                           (cufftDoubleComplex *)samp);
+    // step 2: 3D inverse FFT (normalised by 1/(s0 M~)^3 in step 3)
+    if ((r = cufftPlan3d(&h1, ns, ns, ns, CUFFT_Z2Z)) != CUFFT_SUCCESS) { st = cufft_fail(r, "precompute plan"); goto done; }
+    have1 = true;
+    cufftSetStream(h1, p->stream);
+    if ((r = cufftExecZ2Z(h1, (cufftDoubleComplex *)samp, (cufftDoubleComplex *)samp, CUFFT_INVERSE)) != CUFFT_SUCCESS) {
+        st = cufft_fail(r, "precompute inverse");
+        goto done;
+    }
+    // step 3: truncate to (2 M~)^3
+    k_green0_truncate<<<unsigned((ngr + 255) / 256), 256, 0, p->stream>>>(
+        ns, Mt, 1.0 / double(nsamp), (const cufftDoubleComplex *)samp, (double *)gr);
+    // step 4: 3D FFT -> G^{0P}_R at k = pi n / L~
+    if ((r = cufftPlan3d(&h2, n2, n2, n2, CUFFT_D2Z)) != CUFFT_SUCCESS) { st = cufft_fail(r, "precompute plan 2"); goto done; }
+    have2 = true;
+    cufftSetStream(h2, p->stream);
+    if ((r = cufftExecD2Z(h2, (double *)gr, (cufftDoubleComplex *)grh)) != CUFFT_SUCCESS) {
+        st = cufft_fail(r, "precompute forward");
+        goto done;
+    }
+    // sigma = 4 pi h^3 / (2 M~)^3 * prod_i e^{-k_i^2/4xi^2} / W^0(k_i)^2 * G^{0P}_R
+    if (p->dtype == SE_F32)
+        k_sigma0<float><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
+            Mt, norm, (const double *)fax, (const cufftDoubleComplex *)grh, (float *)p->sigma_tab);
+    else
+        k_sigma0<double><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
+            Mt, norm, (const double *)fax, (const cufftDoubleComplex *)grh, (double *)p->sigma_tab);
+    {
+        cudaError_t e = cudaStreamSynchronize(p->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(e, "precompute");
+    }
+done:
+    if (have1) cufftDestroy(h1);
+    if (have2) cufftDestroy(h2);
+    dev_free(p, &samp);
+    dev_free(p, &gr);
+    dev_free(p, &grh);
+    dev_free(p, &fax);
+    return st;
+}
+
+// ------------------------------------------------------------ tables
+
+template <typename T>
+static void to_type(const std::vector<double> &src, std::vector<unsigned char> &dst)
+{
+    dst.resize(src.size() * sizeof(T));
+    T *d = reinterpret_cast<T *>(dst.data());
+    for (size_t i = 0; i < src.size(); ++i) d[i] = T(src[i]);
+}
+
+struct TabBuilder {
+    std::vector<double> v;
+    size_t add(const std::vector<double> &a)
+    {
+        size_t o = v.size();
+        v.insert(v.end(), a.begin(), a.end());
+        while (v.size() % 4) v.push_back(0.0);
+        return o;
+    }
+};
+
+template <typename T>
+static ScaleBox<T> make_box(const se_plan_s *p, int n0, int n1, int n2, size_t f0, size_t k0, size_t f1, size_t k1,
+                            size_t f2, size_t k2, double norm, int excl)
+{
+    const T *base = reinterpret_cast<const T *>(p->tabs);
+    ScaleBox<T> b;
+    b.n0 = n0; b.n1 = n1; b.n2 = n2;
+    b.f0 = base + f0; b.k0 = base + k0;
+    b.f1 = base + f1; b.k1 = base + k1;
+    b.f2 = base + f2; b.k2 = base + k2;
+    b.norm = T(norm);
+    b.excl = excl;
+    b.nl = p->nl;
+    return b;
+}
+
+static se_status upload(const void *host, void *dev, size_t bytes, const char *what)
+{
+    cudaError_t e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? SE_OK : cuda_fail(e, what);
+}
+
+static se_status build_tables(se_plan_s *p)
+{
+    const int M = p->M, Mt = p->Mt, D = p->D;
+    const double h3 = p->h * p->h * p->h, fpi = 4.0 * M_PI * h3;
+    TabBuilder tb;
+    std::vector<double> fper, kper, fJ, kJ, fI, kI, fZ, kZ;
+    axis_tables(p, M, fper, kper);
+    const size_t o_fper = tb.add(fper), o_kper = tb.add(kper);
+    const size_t o_one = tb.add({1.0}), o_zero = tb.add({0.0});
+    size_t o_fJ = 0, o_kJ = 0, o_fI = 0, o_kI = 0, o_fl = 0, o_kl = 0;
+    std::vector<double> sig0;
+    std::vector<int2> lines;
+    if (D == 1 || D == 2) {
+        axis_tables(p, Mt, fJ, kJ);
+        o_fJ = tb.add(fJ);
+        o_kJ = tb.add(kJ);
+        if (p->nl > 0) {
+            axis_tables(p, p->sMt, fI, kI);
+            o_fI = tb.add(fI);
+            o_kI = tb.add(kI);
+        }
+        axis_tables(p, p->s0Mt, fZ, kZ);
+        std::vector<double> fl, kl;
+        if (D == 2) {
+            for (int ky = -p->nl; ky <= p->nl; ++ky)
+                for (int kx = 0; kx <= p->nl; ++kx) {
+                    if (kx == 0 && ky == 0) continue;
+                    const int iy = (ky + M) % M;
+                    lines.push_back(make_int2(kx, iy));
+                    fl.push_back(fper[kx] * fper[iy]);
+                    kl.push_back(kper[kx] + kper[iy]);
+                }
+            p->nI = int(lines.size());
+            // zero mode: sigma(kz) = 4 pi h^3 / (M^2 s0 M~) f(0)^2 f(kz) G^{2P}(0, kz)
+            sig0.resize(p->s0Mt);
+            const double nz = fpi / (double(M) * M * p->s0Mt);
+            for (int m = 0; m < p->s0Mt; ++m)
+                sig0[m] = nz * fper[0] * fper[0] * fZ[m] * green_zero_2p(p->R, std::sqrt(kZ[m]));
+        } else {
+            for (int pl = 0; pl < p->nl; ++pl) {
+                fl.push_back(fper[pl + 1]);
+                kl.push_back(kper[pl + 1]);
+            }
+            // zero plane: sigma(ky, kz) = 4 pi h^3 / (M (s0 M~)^2) f(0) f(ky) f(kz) G^{1P}(0, |kappa|)
+            const int s = p->s0Mt;
+            sig0.resize(size_t(s) * s);
+            const double nz = fpi / (double(M) * s * s);
+            for (int z = 0; z < s; ++z)
+                for (int y = 0; y < s; ++y)
+                    sig0[size_t(z) * s + y] = nz * fper[0] * fZ[y] * fZ[z] * green_zero_1p(p->R, std::sqrt(kZ[y] + kZ[z]));
+        }
+        if (!fl.empty()) {
+            o_fl = tb.add(fl);
+            o_kl = tb.add(kl);
+        }
+    }
+    // upload the axis tables in the plan's precision
+    std::vector<unsigned char> bytes;
+    if (p->dtype == SE_F32) to_type<float>(tb.v, bytes); else to_type<double>(tb.v, bytes);
+    se_status st = dev_alloc(p, &p->tabs, bytes.size());
+    if (st != SE_OK) return st;
+    p->tabs_bytes = bytes.size();
+    if ((st = upload(bytes.data(), p->tabs, bytes.size(), "tables")) != SE_OK) return st;
+    if (!lines.empty()) {
+        if ((st = dev_alloc(p, (void **)&p->I_lines, sizeof(int2) * lines.size())) != SE_OK) return st;
+        if ((st = upload(lines.data(), p->I_lines, sizeof(int2) * lines.size(), "I lines")) != SE_OK) return st;
+    }
+    if (!sig0.empty()) {
+        if (p->dtype == SE_F32) to_type<float>(sig0, bytes); else to_type<double>(sig0, bytes);
+        if ((st = upload(bytes.data(), p->sigma_tab, bytes.size(), "zero-mode table")) != SE_OK) return st;
+    }
+    // scaling boxes
+    const int row = M / 2 + 1;
+    auto boxes = [&](auto tag) {
+        using T = decltype(tag);
+        ScaleBox<T> spec{}, U{};
+        if (D == 3) {
+            spec = make_box<T>(p, row, M, M, o_fper, o_kper, o_fper, o_kper, o_fper, o_kper,
+                               fpi / (double(M) * M * M), 0);
+        } else if (D == 2) {
+            spec = make_box<T>(p, row, M, Mt, o_fper, o_kper, o_fper, o_kper, o_fJ, o_kJ,
+                               fpi / (double(M) * M * Mt), 2);
+            if (p->nI > 0)
+                U = make_box<T>(p, p->sMt, p->nI, 1, o_fI, o_kI, o_fl, o_kl, o_one, o_zero,
+                                fpi / (double(M) * M * p->sMt), 0);
+        } else if (D == 1) {
+            spec = make_box<T>(p, row, Mt, Mt, o_fper, o_kper, o_fJ, o_kJ, o_fJ, o_kJ,
+                               fpi / (double(M) * Mt * Mt), 1);
+            if (p->nl > 0)
+                U = make_box<T>(p, p->sMt, p->sMt, p->nl, o_fI, o_kI, o_fI, o_kI, o_fl, o_kl,
+                                fpi / (double(M) * p->sMt * p->sMt), 0);
+        }
+        return std::make_pair(spec, U);
+    };
+    if (p->dtype == SE_F32) { auto b = boxes(float()); p->sb_spec_f = b.first; p->sb_U_f = b.second; }
+    else { auto b = boxes(double()); p->sb_spec_d = b.first; p->sb_U_d = b.second; }
+    if (D == 0) return precompute_free_space(p);
+    return SE_OK;
+}
+
+// ------------------------------------------------------------ FFT plans
+
+static se_status make_plans(se_plan_s *p)
+{
+    const bool f32 = p->dtype == SE_F32;
+    const cufftType R2C = f32 ? CUFFT_R2C : CUFFT_D2Z, C2R = f32 ? CUFFT_C2R : CUFFT_Z2D, C2C = f32 ? CUFFT_C2C : CUFFT_Z2Z;
+    const int M = p->M, Mt = p->Mt, row = M / 2 + 1;
+    cufftResult r;
+#define SE_PLAN(call, flag, what)                                   \
+    if ((r = (call)) != CUFFT_SUCCESS) return cufft_fail(r, what);  \
+    flag = true;
+    if (p->D == 3) {
+        SE_PLAN(cufftPlan3d(&p->fwd, M, M, M, R2C), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlan3d(&p->inv, M, M, M, C2R), p->have_inv, "plan inv");
+    } else if (p->D == 0) {
+        const int n2 = 2 * Mt;
+        SE_PLAN(cufftPlan3d(&p->fwd, n2, n2, n2, R2C), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlan3d(&p->inv, n2, n2, n2, C2R), p->have_inv, "plan inv");
+    } else if (p->D == 2) {
+        int n[2] = {M, M};
+        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt), p->have_inv, "plan inv");
+        int nz[1] = {Mt};
+        SE_PLAN(cufftPlanMany(&p->free_main, 1, nz, nz, M * row, 1, nz, M * row, 1, C2C, M * row), p->have_free_main,
+                "plan free");
+        if (p->nI > 0) {
+            int ns[1] = {p->sMt};
+            SE_PLAN(cufftPlanMany(&p->free_I, 1, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nI), p->have_free_I, "plan I");
+        }
+        int n0[1] = {p->s0Mt};
+        SE_PLAN(cufftPlanMany(&p->free_Z, 1, n0, nullptr, 1, 0, nullptr, 1, 0, C2C, 1), p->have_free_Z, "plan zero");
+    } else {
+        int n[1] = {M};
+        SE_PLAN(cufftPlanMany(&p->fwd, 1, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt * Mt), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 1, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt * Mt), p->have_inv, "plan inv");
+        int nz[2] = {Mt, Mt};
+        SE_PLAN(cufftPlanMany(&p->free_main, 2, nz, nz, row, 1, nz, row, 1, C2C, row), p->have_free_main, "plan free");
+        if (p->nl > 0) {
+            int ns[2] = {p->sMt, p->sMt};
+            SE_PLAN(cufftPlanMany(&p->free_I, 2, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nl), p->have_free_I, "plan I");
+        }
+        int n0[2] = {p->s0Mt, p->s0Mt};
+        SE_PLAN(cufftPlanMany(&p->free_Z, 2, n0, nullptr, 1, 0, nullptr, 1, 0, C2C, 1), p->have_free_Z, "plan zero");
+    }
+#undef SE_PLAN
+    return SE_OK;
+}
+
+se_status plan_set_fft_stream(se_plan_s *p)
+{
+    cufftHandle hs[5] = {p->fwd, p->inv, p->free_main, p->free_I, p->free_Z};
+    bool have[5] = {p->have_fwd, p->have_inv, p->have_free_main, p->have_free_I, p->have_free_Z};
+    for (int i = 0; i < 5; ++i)
+        if (have[i]) {
+            cufftResult r = cufftSetStream(hs[i], p->stream);
+            if (r != CUFFT_SUCCESS) return cufft_fail(r, "cufftSetStream");
+        }
+    return SE_OK;
+}
+
+// ------------------------------------------------------------ build / reserve / release
+
+static int choose_tile(int n, bool periodic, int pref)
+{
+    if (!periodic) return pref;
+    if (n % pref == 0) return pref;
+    for (int t = 16; t >= 4; --t)
+        if (n % t == 0) return t;
+    for (int t = 3; t >= 1; --t)
+        if (n % t == 0) return t;
+    return 1;
+}
+
+se_status plan_build(se_plan_s *p)
+{
+    cudaError_t ce = cudaGetDevice(&p->dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    p->elem = p->dtype == SE_F32 ? 4 : 8;
+    // grid geometry (Alg. 4 step 1)
+    for (int a = 0; a < 3; ++a) {
+        const bool per = a < p->D;
+        p->tg.n[a] = per ? p->M : p->Mt;
+        p->tg.periodic[a] = per ? 1 : 0;
+        p->off[a] = per ? 0.0 : p->dL / 2.0;
+    }
+    if (p->window == SE_WIN_PKB) fit_pkb(p);
+    // tiles: pick the edge so that the extended block fits in shared memory
+    int pref = p->tile_pref > 0 ? p->tile_pref : 8;
+    for (;;) {
+        int blk = 1;
+        for (int a = 0; a < 3; ++a) {
+            p->tg.T[a] = choose_tile(p->tg.n[a], p->tg.periodic[a], std::min(pref, p->tg.n[a]));
+            p->tg.nt[a] = (p->tg.n[a] + p->tg.T[a] - 1) / p->tg.T[a];
+            p->tg.B[a] = p->tg.T[a] + p->P - 1;
+            blk *= p->tg.B[a];
+        }
+        p->tg.blk = blk;
+        const size_t need = (2 * ((size_t(blk) + 15) & ~size_t(15)) + 512 + (kThreads / 32) * 6 * p->P) * p->elem;
+        if (need <= 220 * 1024) break;
+        if (pref <= 4) return fail(SE_EINVAL, "gridding block does not fit in shared memory");
+        pref /= 2;
+    }
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    se_status st;
+    if ((st = dev_alloc(p, (void **)&p->tile_cnt, sizeof(int) * (nt + 1))) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->tile_off, sizeof(int) * (nt + 1))) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * std::max(nt, 256))) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->red, sizeof(double) * 8)) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->err, sizeof(int))) != SE_OK) return st;
+    if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(cudaGetLastError(), "memset");
+    p->scratch_bytes = size_t(nt) * p->tg.blk * p->elem;
+    if ((st = dev_alloc(p, &p->scratch, p->scratch_bytes)) != SE_OK) return st;
+    // grids and spectra
+    const int M = p->M, Mt = p->Mt, row = M / 2 + 1;
+    const int64_t nlog = int64_t(p->tg.n[0]) * p->tg.n[1] * p->tg.n[2];
+    if (p->D == 0) {
+        const int64_t n2 = 2 * int64_t(Mt);
+        p->grid_in_elems = p->grid_out_elems = size_t(n2 * n2 * n2);
+        p->gin.s1 = p->gout.s1 = n2;
+        p->gin.s2 = p->gout.s2 = n2 * n2;
+        p->spec_elems = size_t(n2 * n2 * (Mt + 1));
+        p->sigma_elems = p->spec_elems;
+    } else {
+        p->grid_in_elems = p->grid_out_elems = size_t(nlog);
+        p->gin.s1 = p->gout.s1 = p->tg.n[0];
+        p->gin.s2 = p->gout.s2 = int64_t(p->tg.n[0]) * p->tg.n[1];
+        p->spec_elems = size_t(nlog / p->tg.n[0]) * row;
+        if (p->D == 2) {
+            int nI = 0;
+            for (int ky = -p->nl; ky <= p->nl; ++ky)
+                for (int kx = 0; kx <= p->nl; ++kx) nI += !(kx == 0 && ky == 0);
+            p->nI = nI;
+            p->U_elems = size_t(nI) * p->sMt;
+            p->Z_elems = p->s0Mt;
+        } else if (p->D == 1) {
+            p->U_elems = size_t(p->nl) * p->sMt * p->sMt;
+            p->Z_elems = size_t(p->s0Mt) * p->s0Mt;
+        }
+        p->sigma_elems = p->Z_elems;
+    }
+    if ((st = dev_alloc(p, &p->grid_in, p->grid_in_elems * p->elem)) != SE_OK) return st;
+    if ((st = dev_alloc(p, &p->grid_out, p->grid_out_elems * p->elem)) != SE_OK) return st;
+    if (cudaMemset(p->grid_in, 0, p->grid_in_elems * p->elem) != cudaSuccess) return cuda_fail(cudaGetLastError(), "memset");
+    if ((st = dev_alloc(p, &p->spec, p->spec_elems * 2 * p->elem)) != SE_OK) return st;
+    if (p->U_elems && (st = dev_alloc(p, &p->U, p->U_elems * 2 * p->elem)) != SE_OK) return st;
+    if (p->Z_elems && (st = dev_alloc(p, &p->Z, p->Z_elems * 2 * p->elem)) != SE_OK) return st;
+    if (p->sigma_elems && (st = dev_alloc(p, &p->sigma_tab, p->sigma_elems * p->elem)) != SE_OK) return st;
+    if ((st = build_tables(p)) != SE_OK) return st;
+    if ((st = make_plans(p)) != SE_OK) return st;
+    if ((st = plan_set_fft_stream(p)) != SE_OK) return st;
+    return SE_OK;
+}
+
+se_status plan_reserve(se_plan_s *p, int64_t n)
+{
+    if (n <= p->cap) return SE_OK;
+    int64_t cap = (n + 1023) & ~int64_t(1023);
+    if (cap > (int64_t(1) << 31) - 1) return fail(SE_EINVAL, "more than 2^31 - 1 particles");
+    dev_free(p, (void **)&p->tile_rank);
+    dev_free(p, &p->prt.frac_q);
+    dev_free(p, (void **)&p->prt.idx_code);
+    p->cap = 0;
+    se_status st;
+    if ((st = dev_alloc(p, (void **)&p->tile_rank, sizeof(int2) * cap)) != SE_OK) return st;
+    if ((st = dev_alloc(p, &p->prt.frac_q, 4 * p->elem * cap)) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->prt.idx_code, sizeof(int2) * cap)) != SE_OK) return st;
+    p->cap = cap;
+    return SE_OK;
+}
+
+se_status plan_io_reserve(se_plan_s *p, int64_t n)
+{
+    const size_t need = size_t(n) * 8 * p->elem + 64;
+    if (need <= p->io_bytes) return SE_OK;
+    dev_free(p, &p->io_buf);
+    p->io_bytes = 0;
+    se_status st = dev_alloc(p, &p->io_buf, need);
+    if (st == SE_OK) p->io_bytes = need;
+    return st;
+}
+
+se_status plan_second_grid(se_plan_s *p)
+{
+    if (p->grid_in2) return SE_OK;
+    se_status st;
+    if ((st = dev_alloc(p, &p->grid_in2, p->grid_in_elems * p->elem)) != SE_OK) return st;
+    if ((st = dev_alloc(p, &p->grid_out2, p->grid_out_elems * p->elem)) != SE_OK) return st;
+    if (cudaMemset(p->grid_in2, 0, p->grid_in_elems * p->elem) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "memset");
+    return SE_OK;
+}
+
+void plan_release(se_plan_s *p)
+{
+    if (p->have_fwd) cufftDestroy(p->fwd);
+    if (p->have_inv) cufftDestroy(p->inv);
+    if (p->have_free_main) cufftDestroy(p->free_main);
+    if (p->have_free_I) cufftDestroy(p->free_I);
+    if (p->have_free_Z) cufftDestroy(p->free_Z);
+    p->have_fwd = p->have_inv = p->have_free_main = p->have_free_I = p->have_free_Z = false;
+    void **bufs[] = {&p->grid_in, &p->grid_out, &p->spec, &p->U, &p->Z, (void **)&p->I_lines, &p->tabs, &p->sigma_tab,
+                     &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
+                     (void **)&p->red, (void **)&p->err, (void **)&p->tile_rank, &p->prt.frac_q,
+                     (void **)&p->prt.idx_code, &p->io_buf, &p->grid_in2, &p->grid_out2};
+    for (void **b : bufs) dev_free(p, b);
+}
+
+}  // namespace se

@@ -1,0 +1,80 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every
+function declared in include/se_gb300.h, and validates arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import params as prm
+from paper_1712_04732_gb300 import _native as nat
+from paper_1712_04732_gb300 import build as bld
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "se_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bld.build()
+    return nat.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(se_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "se_potential" in names and "se_force" in names and "se_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(nat.EXPORTS) == names
+
+
+def test_status_names(lib):
+    for code, name in nat.STATUS.items():
+        assert lib.se_status_str(code).decode() == name
+
+
+@pytest.mark.parametrize("D,M,P,xi,box", [
+    (4, 32, 8, 8.0, 1.0),       # D out of range
+    (3, 31, 8, 8.0, 1.0),       # M odd
+    (3, 32, 7, 8.0, 1.0),       # P odd
+    (3, 8, 10, 8.0, 1.0),       # P > M
+    (3, 64, 18, 8.0, 1.0),      # P > 16
+    (3, 32, 8, -1.0, 1.0),      # xi <= 0
+    (3, 32, 8, 8.0, 0.0),       # empty box
+])
+def test_plan_create_rejects_bad_arguments(lib, D, M, P, xi, box):
+    h = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(box, box, box)
+    st = lib.se_plan_create(ctypes.byref(h), b, D, xi, M, P, nat.SE_WIN_PKB, nat.SE_F32, None)
+    assert st == 1 and not h.value
+    assert lib.se_last_error()
+
+
+def test_plan_create_rejects_non_cubic_box(lib):
+    h = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(1.0, 1.0, 2.0)
+    assert lib.se_plan_create(ctypes.byref(h), b, 3, 8.0, 32, 8, 1, 0, None) == 1
+
+
+def test_calls_reject_null_plan(lib):
+    assert lib.se_potential(None, 10, None, None, None, 0) == 1
+    assert lib.se_force(None, 10, None, None, None, None, None, 0) == 1
+    assert lib.se_plan_destroy(None) == 0
+
+
+@pytest.mark.parametrize("eps,xi,L,Q,win", [
+    (1e-5, 8.0, 1.0, 3.32e4, "pkb"), (1e-10, 8.0, 1.0, 3.32e4, "pkb"), (1e-3, 3.0, 10.0, 3.32e4, "pkb"),
+    (1e-8, 6.0, 5.0, 334.0, "gaussian"), (1e-12, 17.0, 3.0, 3.32e4, "pkb"),
+])
+def test_parameter_rules_agree_with_the_oracle(lib, eps, xi, L, Q, win):
+    """se_params_from_tolerance (C++) and the oracle's Sec. 6 rules (Python) are
+    written independently; they must give the same (M, P)."""
+    M, P = ctypes.c_int(), ctypes.c_int()
+    w = nat.SE_WIN_GAUSSIAN if win == "gaussian" else nat.SE_WIN_PKB
+    assert lib.se_params_from_tolerance(eps, xi, L, Q, w, ctypes.byref(M), ctypes.byref(P)) == 0
+    assert (M.value, P.value) == prm.from_tolerance(eps, xi, L, Q, win)

@@ -1,0 +1,333 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Oracle B runs the same discrete algorithm (Alg. 4) with the same parameters,
+so the FP64 path must agree with it to rounding; the FP32 path to its own
+rounding.  Sizes span several gridding tiles with ragged edges.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ewald as E
+from oracle import se_discrete as S
+from paper_1712_04732_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: (1e-11, 1e-10), torch.float32: (2e-6, 1e-5)}   # (phi, F) relative rms
+
+
+def _se():
+    import paper_1712_04732_gb300 as se
+    return se
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+
+
+def _oracle_for(plan, **kw):
+    info = plan.info()
+    o = S.SEOracle(plan.D, plan.L, plan.xi, plan.M, plan.P, plan.window, s_mt=info["s_mt"], nl=info["n_l"], **kw)
+    assert o.Mt == info["Mt"] and o.g["s0Mt"] == info["s0_mt"]
+    return o
+
+
+def _run(plan, x, q, **kw):
+    dev = plan.device
+    xt = torch.tensor(x, dtype=plan.dtype, device=dev)
+    qt = torch.tensor(q, dtype=plan.dtype, device=dev)
+    F, phi, En = plan.force(xt, qt, energy=True, **kw)
+    torch.cuda.synchronize()
+    return F.double().cpu().numpy(), phi.double().cpu().numpy(), En.item()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("window", ["pkb", "gaussian"])
+@pytest.mark.parametrize("D", [3, 2, 1, 0])
+def test_force_and_potential_match_discrete_oracle(D, window, dtype):
+    se = _se()
+    N, M, P = 700, 20, 8
+    x = wl.uniform_positions(N, 1.0, 11 + D)
+    q = wl.uniform_charges(N, 11 + D)
+    plan = se.Plan(D, 1.0, 6.0, M, P, window, dtype=dtype)
+    F, phi, En = _run(plan, x, q)
+    o = _oracle_for(plan)
+    pb, gb = o.potential(x, q, grad=True)
+    tp, tf = TOL[dtype]
+    assert _rel(phi, pb) < tp
+    assert _rel(F, -q[:, None] * gb) < tf
+    assert En == pytest.approx(0.5 * float(q @ pb), rel=10 * tp)
+
+
+@pytest.mark.parametrize("P", [2, 4, 6, 10, 12, 14, 16])
+def test_every_compiled_support(P):
+    se = _se()
+    D = [3, 2, 1, 0][P // 2 % 4]
+    N, M = 300, max(16, P + 4)
+    x = wl.uniform_positions(N, 1.0, 100 + P)
+    q = wl.uniform_charges(N, 100 + P)
+    plan = se.Plan(D, 1.0, 5.0, M, P, "pkb", dtype=torch.float64)
+    F, phi, _ = _run(plan, x, q)
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
+    assert _rel(F, -q[:, None] * gb) < 1e-10
+
+
+@pytest.mark.parametrize("D", [3, 1])
+def test_grid_not_divisible_by_the_tile(D):
+    """M = 28: the periodic tile edge becomes 7 (a divisor of M); free axes end ragged."""
+    se = _se()
+    x = wl.uniform_positions(500, 1.0, 5)
+    q = wl.uniform_charges(500, 5)
+    plan = se.Plan(D, 1.0, 6.5, 28, 6, "pkb", dtype=torch.float64)
+    assert 28 % plan.info()["tile"][0] == 0
+    F, phi, _ = _run(plan, x, q)
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
+    assert _rel(F, -q[:, None] * gb) < 1e-10
+
+
+@pytest.mark.parametrize("tile", [4, 16])
+def test_tile_edges(tile):
+    se = _se()
+    x = wl.uniform_positions(800, 1.0, 6)
+    q = wl.uniform_charges(800, 6)
+    plan = se.Plan(2, 1.0, 6.0, 32, 8, "pkb", dtype=torch.float64, tile=tile)
+    F, phi, _ = _run(plan, x, q)
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
+    assert _rel(F, -q[:, None] * gb) < 1e-10
+
+
+def test_positions_on_grid_lines_and_box_faces():
+    """Particles exactly on grid nodes, on tile boundaries and at x = 0."""
+    se = _se()
+    M = 24
+    h = 1.0 / M
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, M, size=(200, 3)) * h
+    x[:10] = 0.0
+    x[10:20, 0] = 8 * h
+    q = wl.uniform_charges(200, 9)
+    for D in (3, 2, 0):
+        plan = se.Plan(D, 1.0, 6.0, M, 6, "pkb", dtype=torch.float64)
+        F, phi, _ = _run(plan, x, q)
+        pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+        assert _rel(phi, pb) < 1e-11
+
+
+def test_periodic_coordinates_are_wrapped():
+    se = _se()
+    x = wl.uniform_positions(300, 1.0, 8)
+    q = wl.uniform_charges(300, 8)
+    plan = se.Plan(2, 1.0, 6.0, 24, 6, "pkb", dtype=torch.float64)
+    _, phi0, _ = _run(plan, x, q)
+    xs = x.copy()
+    xs[:, 0] += np.where(np.arange(300) % 2, 3.0, -2.0)
+    xs[:, 1] -= 1.0
+    _, phi1, _ = _run(plan, xs, q)
+    assert _rel(phi1, phi0) < 1e-12
+
+
+def test_all_particles_in_one_tile():
+    se = _se()
+    rng = np.random.default_rng(2)
+    x = 0.5 + 0.01 * rng.random((2000, 3))
+    q = wl.uniform_charges(2000, 2)
+    plan = se.Plan(0, 1.0, 6.0, 24, 8, "pkb", dtype=torch.float64)
+    F, phi, _ = _run(plan, x, q)
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
+    assert _rel(F, -q[:, None] * gb) < 1e-10
+
+
+def test_single_particle_and_empty_input():
+    se = _se()
+    plan = se.Plan(3, 1.0, 6.0, 16, 6, "pkb", dtype=torch.float64)
+    x = np.array([[0.3, 0.6, 0.9]])
+    q = np.array([1.0])
+    F, phi, _ = _run(plan, x, q)
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-12
+    e = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    out = plan.potential(e, torch.empty(0, dtype=torch.float64, device="cuda"))
+    assert out.shape == (0,)
+
+
+def test_self_term_flag():
+    se = _se()
+    x = wl.uniform_positions(200, 1.0, 1)
+    q = wl.uniform_charges(200, 1)
+    plan = se.Plan(3, 1.0, 6.0, 16, 6, "pkb", dtype=torch.float64)
+    _, p0, _ = _run(plan, x, q)
+    _, p1, _ = _run(plan, x, q, add_self=True)
+    assert np.allclose(p1 - p0, -2 * 6.0 / np.sqrt(np.pi) * q, rtol=1e-12, atol=1e-12)
+
+
+def test_host_io_path_equals_device_path():
+    se = _se()
+    x = wl.uniform_positions(1000, 1.0, 12)
+    q = wl.uniform_charges(1000, 12)
+    plan = se.Plan(1, 1.0, 6.0, 20, 6, "pkb", dtype=torch.float32)
+    F, phi, En = _run(plan, x, q)
+    xh = torch.tensor(x, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(q, dtype=torch.float32).pin_memory()
+    Fh = torch.empty((1000, 3), dtype=torch.float32).pin_memory()
+    ph = torch.empty(1000, dtype=torch.float32).pin_memory()
+    eh = torch.empty((), dtype=torch.float64).pin_memory()
+    plan.force_host(xh, qh, Fh, ph, eh)
+    assert _rel(ph.double().numpy(), phi) < 1e-6
+    assert _rel(Fh.double().numpy(), F) < 1e-6
+    assert eh.item() == pytest.approx(En, rel=1e-6)
+
+
+def test_vjp_matches_oracle_and_linearity():
+    """g_q = A g and g_x = g grad(A q) + q grad(A g) (operator symmetry)."""
+    se = _se()
+    N = 500
+    x = wl.uniform_positions(N, 1.0, 21)
+    q = wl.uniform_charges(N, 21)
+    g = wl.uniform_charges(N, 22)
+    for D in (3, 1):
+        plan = se.Plan(D, 1.0, 6.0, 20, 8, "pkb", dtype=torch.float64)
+        xt, qt, gt = (torch.tensor(a, device="cuda") for a in (x, q, g))
+        gx, gq = plan.vjp(xt, qt, gt)
+        o = _oracle_for(plan)
+        pg, dg = o.potential(x, g, grad=True)
+        _, dq = o.potential(x, q, grad=True)
+        assert _rel(gq.cpu().numpy(), pg) < 1e-11
+        ref = g[:, None] * dq + q[:, None] * dg
+        assert _rel(gx.cpu().numpy(), ref) < 1e-10
+
+
+def test_energy_autograd_against_finite_differences():
+    """E = 1/2 q.phi; dE/dx = -F and dE/dq = phi versus central differences (FP64,
+    h = 1e-6, 32 particles kept away from grid lines where the window shifts)."""
+    se = _se()
+    plan = se.Plan(0, 1.0, 6.0, 24, 8, "pkb", dtype=torch.float64)
+    h = 1.0 / 24
+    info = plan.info()
+    off = info["delta_L"] / 2
+    rng = np.random.default_rng(3)
+    x = []
+    while len(x) < 32:
+        c = rng.random(3)
+        fr = ((c + off) / h) % 1.0
+        if np.all((fr > 1e-3) & (fr < 1 - 1e-3)):
+            x.append(c)
+    x = torch.tensor(np.array(x), device="cuda", requires_grad=True)
+    q = torch.tensor(wl.uniform_charges(32, 3), device="cuda", requires_grad=True)
+    En = se.energy(plan, x, q)
+    En.backward()
+    eps = 1e-6
+    xd = x.detach()
+    for idx in [(0, 0), (5, 1), (17, 2), (31, 0)]:
+        xp = xd.clone(); xp[idx] += eps
+        xm = xd.clone(); xm[idx] -= eps
+        fd = (se.energy(plan, xp, q.detach()).item() - se.energy(plan, xm, q.detach()).item()) / (2 * eps)
+        assert x.grad[idx].item() == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    for i in [0, 9, 30]:
+        qp = q.detach().clone(); qp[i] += eps
+        qm = q.detach().clone(); qm[i] -= eps
+        fd = (se.energy(plan, xd, qp).item() - se.energy(plan, xd, qm).item()) / (2 * eps)
+        assert q.grad[i].item() == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_potential_autograd_gradcheck():
+    se = _se()
+    plan = se.Plan(3, 1.0, 5.0, 16, 6, "pkb", dtype=torch.float64)
+    rng = np.random.default_rng(5)
+    x = []
+    while len(x) < 12:
+        c = rng.random(3)
+        fr = (c * 16) % 1.0
+        if np.all((fr > 1e-2) & (fr < 1 - 1e-2)):
+            x.append(c)
+    x = torch.tensor(np.array(x), device="cuda", requires_grad=True)
+    q = torch.tensor(wl.uniform_charges(12, 5), device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda a, b: se.potential(plan, a, b), (x, q), eps=1e-6, atol=1e-5, rtol=1e-4)
+
+
+def test_neutrality_and_box_errors():
+    se = _se()
+    plan = se.Plan(2, 1.0, 6.0, 16, 6, "pkb", dtype=torch.float64)
+    x = torch.tensor(wl.uniform_positions(50, 1.0, 1), device="cuda")
+    q = torch.ones(50, dtype=torch.float64, device="cuda")
+    with pytest.raises(se.SEError) as ei:
+        plan.potential(x, q, check_neutral=True)
+    assert ei.value.name == "SE_ENONNEUTRAL"
+    xb = x.clone()
+    xb[3, 2] = 1.5                      # free direction, outside [0, L)
+    with pytest.raises(se.SEError) as ei:
+        plan.potential(xb, q - q.mean(), sync_check=True)
+    assert ei.value.name == "SE_EOUTOFBOX"
+    xn = x.clone()
+    xn[7, 0] = float("nan")
+    with pytest.raises(se.SEError) as ei:
+        plan.potential(xn, q - q.mean(), sync_check=True)
+    assert ei.value.name == "SE_ENOTFINITE"
+    plan.potential(x, q - q.mean(), sync_check=True)     # the plan stays usable
+
+
+def test_streams_and_repeatability():
+    se = _se()
+    x = torch.tensor(wl.uniform_positions(4000, 1.0, 1), device="cuda", dtype=torch.float32)
+    q = torch.tensor(wl.uniform_charges(4000, 1), device="cuda", dtype=torch.float32)
+    plan = se.Plan(3, 1.0, 8.0, 32, 8, "pkb", dtype=torch.float32)
+    p0 = plan.potential(x, q)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p1 = plan.potential(x, q)
+    s.synchronize()
+    assert torch.allclose(p0, p1, rtol=1e-5, atol=1e-6 * p0.abs().max().item())
+
+
+# ----------------------------------------------------- the named workloads at full size
+
+def _sample(n, k, seed=0):
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_free_space_workload_full_size(dtype):
+    """0P, N = 20000, M = 48, PKB P = 8, xi = 8 (the benchmark workload): the
+    GPU against the direct sum (oracle A) on 400 sampled targets (rms relative
+    error <= 1e-5 for phi and F) and against oracle B (same discretisation)."""
+    se = _se()
+    x, q, spec = wl.make("free_0p", seed=1)
+    plan = se.Plan(0, 1.0, 8.0, 48, 8, "pkb", dtype=dtype)
+    F, phi, En = _run(plan, x, q)
+    idx = _sample(len(q), 400)
+    pa, ga = E.fourier(0, x, q, 1.0, 8.0, xt=x[idx])
+    assert _rel(phi[idx], pa) < 1e-5
+    assert _rel(F[idx], -q[idx, None] * ga) < 1e-5
+    o = _oracle_for(plan)
+    pb, gb = o.potential(x, q, xt=x[idx], grad=True)
+    tp, tf = TOL[dtype]
+    assert _rel(phi[idx], pb) < tp
+    assert _rel(F[idx], -q[idx, None] * gb) < tf
+
+
+def test_lattice_workload_madelung():
+    """3P, NaCl cell (512 ions): SE k-space part (Gaussian P = 8 is accurate to
+    ~1e-5; P = 16 PKB to ~1e-14) plus the oracle's real-space and self terms
+    reproduces the Madelung constant."""
+    se = _se()
+    x, q = wl.nacl_cell(8, 1.0)
+    plan = se.Plan(3, 1.0, 8.0, 48, 16, "pkb", dtype=torch.float64)
+    _, phi, _ = _run(plan, x, q)
+    pr, _ = E.real(3, x, q, 1.0, 8.0, 6.5 / 8.0)
+    tot = phi + pr + E.self_term(q, 8.0)
+    assert np.allclose(-(tot * q) / 8.0, 1.7475645946, atol=1e-9)
+
+
+def test_lattice_workload_gaussian():
+    se = _se()
+    x, q, spec = wl.make("lattice_3p", seed=1)
+    plan = se.Plan(3, 1.0, 8.0, 32, 8, "gaussian", dtype=torch.float64)
+    F, phi, _ = _run(plan, x, q)
+    pa, ga = E.fourier(3, x, q, 1.0, 8.0)
+    assert _rel(phi, pa) < 3 * 2 * np.exp(-(np.pi / 2) * 8 * np.sqrt(0.91))   # Sec. 5.2 estimate
+    pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
