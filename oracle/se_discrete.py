@@ -118,18 +118,19 @@ class SEOracle:
         t = (np.asarray(x, dtype=np.float64) + np.array(self.off)) / self.h      # (N, 3)
         j = np.floor(t)[:, :, None] + np.arange(-P // 2 + 1, P // 2 + 1)[None, None, :]
         dist = (t[:, :, None] - j) * self.h                                      # (N, 3, P)
+        frac = t - np.floor(t)
         j = j.astype(np.int64)
         for a in range(3):
             if a < self.D:
                 j[:, a, :] %= self.n[a]
             elif j[:, a, :].min() < 0 or j[:, a, :].max() >= self.n[a]:
                 raise ValueError("support leaves the extended box in a free direction")
-        return j, dist
+        return j, dist, frac
 
     def grid_charges(self, x, q):
         """Eq. (gridding): H_j = sum_n q_n W(x_j - x_n)_* on the M^D x M~^(3-D) grid."""
-        j, dist = self._stencil(x)
-        w = self.win(dist)                                                       # (N, 3, P)
+        j, dist, frac = self._stencil(x)
+        w, _ = self.win.stencil(frac, dist)                                      # (N, 3, P)
         H = np.zeros(self.n)
         q = np.asarray(q, dtype=np.float64)
         P = self.P
@@ -224,9 +225,8 @@ class SEOracle:
     def gather(self, Ht, xt, grad: bool = False):
         """Eq. (complete_integral) by the trapezoidal rule, and with grad=True
         Eq. (force-method-1): the gradient with W' in place of W per axis."""
-        j, dist = self._stencil(xt)
-        w = self.win(dist)
-        dw = self.win.dx(dist) if grad else None
+        j, dist, frac = self._stencil(xt)
+        w, dw = self.win.stencil(frac, dist, grad)
         scale = 4.0 * math.pi * self.h ** 3
         P = self.P
         phi = np.zeros(j.shape[0])

@@ -101,6 +101,27 @@ class PKB:
             val = val * xb + j * c[..., j]
         return np.where(np.abs(x) <= self.w, val * 2.0 / self.h, 0.0)
 
+    def stencil(self, frac, k):
+        """Values at the P support points of a particle whose grid coordinate has
+        fractional part ``frac``: point k (counted from the lowest index) lies in
+        subinterval P-1-k at the common offset xbar = 2 frac - 1 (Sec. 4.1: all
+        evaluation points share one offset within their subintervals)."""
+        xb = 2.0 * np.asarray(frac, dtype=np.float64) - 1.0
+        c = self.coef[self.P - 1 - np.asarray(k)]
+        val = np.zeros(np.broadcast(xb, np.asarray(k)).shape)
+        for j in range(self.nu, -1, -1):
+            val = val * xb + c[..., j]
+        return val
+
+    def stencil_dx(self, frac, k):
+        """d/dx of :meth:`stencil` (d xbar / dx = 2/h)."""
+        xb = 2.0 * np.asarray(frac, dtype=np.float64) - 1.0
+        c = self.coef[self.P - 1 - np.asarray(k)]
+        val = np.zeros(np.broadcast(xb, np.asarray(k)).shape)
+        for j in range(self.nu, 0, -1):
+            val = val * xb + j * c[..., j]
+        return val * 2.0 / self.h
+
     def cond(self) -> float:
         """Condition number of the Vandermonde matrix at the Chebyshev points (Sec. 4.1)."""
         return float(np.linalg.cond(self.V))
@@ -130,6 +151,17 @@ class Window:
         if self.kind == "kb":
             return kaiser_dx(x, self.w, self.shape)
         return self.pkb.dx(x)
+
+    def stencil(self, frac, dist, grad=False):
+        """Window values (and x-derivatives) at the P support points of each
+        particle; ``frac`` (N, 3) fractional grid coordinates, ``dist`` (N, 3, P)
+        = x_m - x_j.  The PKB is evaluated per support point (Sec. 4.1); the
+        other windows are plain functions of the distance."""
+        if self.kind != "pkb":
+            return self(dist), (self.dx(dist) if grad else None)
+        k = np.arange(self.P)[None, None, :]
+        f = np.asarray(frac)[:, :, None]
+        return self.pkb.stencil(f, k), (self.pkb.stencil_dx(f, k) if grad else None)
 
     def hat(self, k):
         if self.kind == "gaussian":

@@ -104,6 +104,18 @@ def test_pkb_reproduces_polynomials_exactly():
     assert np.allclose(p.dx(x), poly.deriv()(x), rtol=1e-9, atol=1e-10)
 
 
+def test_pkb_stencil_evaluation_matches_the_piecewise_polynomial():
+    """Evaluating point k of the support in subinterval P-1-k at the common offset
+    xbar = 2 frac - 1 (Sec. 4.1) agrees with evaluating the piecewise polynomial at
+    the distance x_m - x_j = (frac + P/2 - 1 - k) h away from the joins."""
+    P, h, nu = 8, 1.0 / 24, 6
+    p = W.PKB(P, h, 2.5 * P, nu)
+    frac = np.linspace(0.01, 0.99, 23)[:, None]
+    k = np.arange(P)[None, :]
+    assert np.allclose(p.stencil(frac, k), p((frac + P / 2 - 1 - k) * h), rtol=1e-13, atol=1e-15)
+    assert np.allclose(p.stencil_dx(frac, k), p.dx((frac + P / 2 - 1 - k) * h), rtol=1e-11, atol=1e-12)
+
+
 def test_pkb_vandermonde_condition_number_law():
     """Sec. 4.1: cond ~ 0.6 * 10^(0.38 nu), 1.6e3 at nu = 9."""
     g = GOLDEN["vandermonde_condition"]
