@@ -4,7 +4,8 @@
 One step = one pass of the whole path (binning, gridding, FFT, scaling,
 inverse FFT, gathering of phi and F, FP64 energy) over the free-space
 workload: D = 0, N = 20000 charges uniform in [0,1)^3, q ~ U(-1,1) shifted to
-zero sum, xi = 8, M = 48 (M~ = 60, FFT (2 M~)^3 = 120^3), PKB window P = 8.
+zero sum, xi = 8, M = 48, extension lambda = 2 (M~ = 64, FFT (2 M~)^3 = 128^3),
+PKB window P = 8.
 `value` is the FP32 form (FP32 gridding/FFT/gathering, FP64 scaling tables and
 energy); the FP64 form is reported beside it.  Inputs are resident on the
 device when timing starts; L2 is flushed (256 MB write) before every timed step
@@ -140,7 +141,7 @@ def run_reference(a):
 
 def _config(spec):
     return {"workload": f"{WORKLOAD}: D={spec['D']} free space, N={spec['N']} uniform in [0,1)^3, "
-                        f"q~U(-1,1) neutralised, xi={spec['xi']}, M={spec['M']} (M~=60, FFT 120^3), "
+                        f"q~U(-1,1) neutralised, xi={spec['xi']}, M={spec['M']}, lambda={spec['lam']} (M~=64, FFT 128^3), "
                         f"PKB P={spec['P']}, phi+F+energy",
             "l2": "flushed (256 MB write) before every timed step", "timing": "CUDA graph replay, CUDA events"}
 
@@ -165,7 +166,8 @@ def run_ours(a):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def make_form(dtype):
-        plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"], dtype=dtype, device=dev)
+        plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"], dtype=dtype, device=dev,
+                       lam=spec.get("lam"))
         plan.reserve(N)
         x = torch.tensor(x_np, dtype=dtype, device=dev)
         q = torch.tensor(q_np, dtype=dtype, device=dev)
@@ -260,7 +262,7 @@ def run_ours(a):
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "traffic": None}
     # spread/gather GB/s on algorithmic bytes (16 B in per particle, 16 B out, grid once)
-    grid_bytes = 4 * 60 ** 3
+    grid_bytes = 4 * info["Mt"] ** 3
     sg_bytes = N * (16 + 16 + 8) + 2 * grid_bytes
     sg_gbs = sg_bytes / ((stage_ms["spread"] + stage_ms["merge"] + stage_ms["gather"]) * 1e-3) / 1e9
 

@@ -2,6 +2,7 @@
 // Included once by se_kern_f32.cu (T = float) and se_kern_f64.cu (T = double).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -18,16 +19,25 @@ namespace se {
         if (e_ != cudaSuccess) return cuda_fail(e_, where);         \
     } while (0)
 
-#define SE_DISPATCH_P(PV, ...)                                                  \
+// Dispatch on the window support P (compile-time) and the PKB degree: the
+// paper's degree nu_default(P) gets its exact instantiation, any other degree
+// the zero-padded generic one (kMaxNu).
+#define SE_CASE_P(PV, NUV, ...)                                                                \
+    case PV: {                                                                                 \
+        constexpr int PP = PV;                                                                 \
+        if ((NUV) == nu_default(PV)) { constexpr int NN = nu_default(PV); __VA_ARGS__; }        \
+        else { constexpr int NN = kMaxNu; __VA_ARGS__; }                                       \
+    } break;
+#define SE_DISPATCH_P(PV, NUV, ...)                                             \
     switch (PV) {                                                               \
-    case 2: { constexpr int PP = 2; __VA_ARGS__; } break;                       \
-    case 4: { constexpr int PP = 4; __VA_ARGS__; } break;                       \
-    case 6: { constexpr int PP = 6; __VA_ARGS__; } break;                       \
-    case 8: { constexpr int PP = 8; __VA_ARGS__; } break;                       \
-    case 10: { constexpr int PP = 10; __VA_ARGS__; } break;                     \
-    case 12: { constexpr int PP = 12; __VA_ARGS__; } break;                     \
-    case 14: { constexpr int PP = 14; __VA_ARGS__; } break;                     \
-    case 16: { constexpr int PP = 16; __VA_ARGS__; } break;                     \
+    SE_CASE_P(2, NUV, __VA_ARGS__)                                              \
+    SE_CASE_P(4, NUV, __VA_ARGS__)                                              \
+    SE_CASE_P(6, NUV, __VA_ARGS__)                                              \
+    SE_CASE_P(8, NUV, __VA_ARGS__)                                              \
+    SE_CASE_P(10, NUV, __VA_ARGS__)                                             \
+    SE_CASE_P(12, NUV, __VA_ARGS__)                                             \
+    SE_CASE_P(14, NUV, __VA_ARGS__)                                             \
+    SE_CASE_P(16, NUV, __VA_ARGS__)                                             \
     default: return fail(SE_EINVAL, "window support P not compiled in");        \
     }
 
@@ -72,19 +82,20 @@ static WindowArgs<T> window_args(const se_plan_s *p)
     return w;
 }
 
+// Dynamic shared memory: the extended block(s) plus per-warp window values
+// (at most 32 lanes x 3 values, or x 6 with derivatives).
 template <typename T>
 static size_t spread_smem(const se_plan_s *p)
 {
     const int nw = kThreads / 32;
-    return (al16(p->tg.blk) + al16((p->nu + 1) * p->P) + size_t(nw) * 3 * p->P) * sizeof(T);
+    return (al16(p->tg.blk) + size_t(nw) * 32 * 3) * sizeof(T);
 }
 
 template <typename T>
 static size_t gather_smem(const se_plan_s *p, int nblocks)
 {
     const int nw = kThreads / 32;
-    return (nblocks * al16(p->tg.blk) + al16((p->nu + 1) * p->P) + al16(p->nu * p->P) +
-            size_t(nw) * 6 * p->P) * sizeof(T);
+    return (nblocks * al16(p->tg.blk) + size_t(nw) * 32 * 6) * sizeof(T);
 }
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory; the attribute is
@@ -130,8 +141,9 @@ se_status Ops<T>::spread(se_plan_s *p, int64_t N, const T *g, void *dst)
     const size_t sm = spread_smem<T>(p);
     WindowArgs<T> wa = window_args<T>(p);
     const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
-    SE_DISPATCH_P(p->P, {
-        auto kern = k_spread<T, PP>;
+    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+    SE_DISPATCH_P(p->P, nu, {
+        auto kern = k_spread<T, PP, NN>;
         cudaError_t e = allow_smem(kern, sm);
         if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
         kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, g, wa,
@@ -139,10 +151,10 @@ se_status Ops<T>::spread(se_plan_s *p, int64_t N, const T *g, void *dst)
     });
     SE_LAUNCH_CHECK("spread");
     prof_mark(p, 2);
-    const int64_t ng = int64_t(p->tg.n[0]) * p->tg.n[1] * p->tg.n[2];
-    k_merge<T><<<blocks_for(ng, 256), 256, 0, p->stream>>>(p->tg, p->P, p->tile_off,
-                                                            reinterpret_cast<const T *>(p->scratch),
-                                                            reinterpret_cast<T *>(dst), p->gin);
+    const int t01 = p->tg.T[0] * p->tg.T[1];
+    dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
+    k_merge<T><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(p->scratch),
+                                         reinterpret_cast<T *>(dst), p->gin);
     SE_LAUNCH_CHECK("merge");
     prof_mark(p, 3);
     return SE_OK;
@@ -247,15 +259,16 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
     const T self = add_self ? T(-2.0 * p->xi / std::sqrt(M_PI)) : T(0);
     double *part = energy ? p->tile_part : nullptr;
     const T *grid = reinterpret_cast<const T *>(p->grid_out);
-    SE_DISPATCH_P(p->P, {
+    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+    SE_DISPATCH_P(p->P, nu, {
         if (grad) {
-            auto kern = k_gather<T, PP, true>;
+            auto kern = k_gather<T, PP, NN, true>;
             cudaError_t e = allow_smem(kern, sm);
             if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
             kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi, F,
                                                   part, T(p->inv_h), self);
         } else {
-            auto kern = k_gather<T, PP, false>;
+            auto kern = k_gather<T, PP, NN, false>;
             cudaError_t e = allow_smem(kern, sm);
             if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
             kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi,
@@ -282,8 +295,9 @@ se_status Ops<T>::gather_vjp(se_plan_s *p, int64_t N, const T *q, const T *g, co
     const size_t sm = gather_smem<T>(p, 2);
     WindowArgs<T> wa = window_args<T>(p);
     const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
-    SE_DISPATCH_P(p->P, {
-        auto kern = k_gather_vjp<T, PP>;
+    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+    SE_DISPATCH_P(p->P, nu, {
+        auto kern = k_gather_vjp<T, PP, NN>;
         cudaError_t e = allow_smem(kern, sm);
         if (e != cudaSuccess) return cuda_fail(e, "vjp smem attribute");
         kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa,

@@ -132,57 +132,60 @@ __global__ void k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, 
 }
 
 // ----------------------------------------------------------------- window
+// Lane layout of the tile kernels: a warp works on G = 32 / P particles at a
+// time; lane l serves particle l / P at stencil offset dx = l mod P (lanes past
+// G P idle).  Each lane evaluates the window at its own offset k = dx along all
+// three axes, so its PKB coefficients c[j][k] live in registers for the whole
+// kernel.
+template <int P>
+struct LaneMap {
+    static constexpr int G = 32 / P;
+    static constexpr int NP2 = P <= 2 ? 2 : P <= 4 ? 4 : P <= 8 ? 8 : 16;   // next power of two
+};
+
+// The paper's degree rule nu = min(P/2 + 2, 9) (Sec. 6); other degrees use the
+// zero-padded generic variant kMaxNu (exact: leading zero coefficients).
+__host__ __device__ constexpr int nu_default(int P) { return P / 2 + 2 < 9 ? P / 2 + 2 : 9; }
+
+template <typename T, int NU>
+struct LaneCoef {
+    T c[NU + 1];   // W  = sum_j c[j] xbar^j
+    T d[NU];       // dW/dt = sum_j d[j] xbar^j   (t = x / h)
+    __device__ __forceinline__ void load(const WindowArgs<T> &wa, int P, int k)
+    {
+#pragma unroll
+        for (int j = 0; j <= NU; ++j) c[j] = (j <= wa.nu) ? wa.c[j * P + k] : T(0);
+#pragma unroll
+        for (int j = 0; j < NU; ++j) d[j] = (j < wa.nu) ? wa.dc[j * P + k] : T(0);
+    }
+};
+
 // Value W(x_m - x_j) and derivative d/dt (t = x_m / h) at stencil point k for a
 // particle with fractional grid coordinate frac (Sec. 4): x_m - x_j =
 // (frac + P/2 - 1 - k) h.  PKB: Horner in xbar = 2 frac - 1 with the
 // coefficients of the subinterval point k falls in (Sec. 4.1).  Gaussian:
 // Eq. (gaussian) with x/w = 2 (frac + P/2 - 1 - k)/P.
-template <typename T, int P>
-__device__ __forceinline__ T win_val(int kind, int nu, T alpha, const T *sc, T frac, int k)
+template <typename T, int P, int NU, bool DER>
+__device__ __forceinline__ void win_eval(int kind, T alpha, const LaneCoef<T, NU> &cf, T frac, int k, T &w, T &dw)
 {
     if (kind == SE_WIN_PKB) {
-        T xb = T(2) * frac - T(1);
-        T v = sc[nu * P + k];
-        for (int j = nu - 1; j >= 0; --j) v = fma(v, xb, sc[j * P + k]);
-        return v;
-    }
-    T u = T(2) * (frac + T(P / 2 - 1 - k)) / T(P);
-    return dexp(-alpha * u * u);
-}
-
-template <typename T, int P>
-__device__ __forceinline__ T win_der(int kind, int nu, T alpha, const T *sdc, T frac, int k, T val)
-{
-    if (kind == SE_WIN_PKB) {
-        T xb = T(2) * frac - T(1);
-        T v = sdc[(nu - 1) * P + k];
-        for (int j = nu - 2; j >= 0; --j) v = fma(v, xb, sdc[j * P + k]);
-        return v;
-    }
-    T u = T(2) * (frac + T(P / 2 - 1 - k)) / T(P);
-    return T(-4) * alpha * u / T(P) * val;
-}
-
-// Per-lane share of the P x P (x, y) plane of one stencil: lane l owns the
-// points pp = l + 32 e, e = 0..NE-1, pp < P^2, at (pp mod P, pp div P).
-template <int P>
-struct PlaneShare {
-    static constexpr int NE = (P * P + 31) / 32;
-    int off[NE];
-    int dx[NE], dy[NE];
-    bool v[NE];
-    __device__ __forceinline__ void init(int lane, int BX)
-    {
+        const T xb = T(2) * frac - T(1);
+        T v = cf.c[NU];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) {
-            int pp = lane + 32 * e;
-            v[e] = pp < P * P;
-            dx[e] = v[e] ? pp % P : 0;
-            dy[e] = v[e] ? pp / P : 0;
-            off[e] = dy[e] * BX + dx[e];
+        for (int j = NU - 1; j >= 0; --j) v = fma(v, xb, cf.c[j]);
+        w = v;
+        if (DER) {
+            T u = cf.d[NU - 1];
+#pragma unroll
+            for (int j = NU - 2; j >= 0; --j) u = fma(u, xb, cf.d[j]);
+            dw = u;
         }
+    } else {
+        const T u = T(2) * (frac + T(P / 2 - 1 - k)) / T(P);
+        w = dexp(-alpha * u * u);
+        if (DER) dw = T(-4) * alpha * u / T(P) * w;
     }
-};
+}
 
 template <typename T>
 __device__ __forceinline__ size_t align_up_elems(size_t n)
@@ -190,59 +193,86 @@ __device__ __forceinline__ size_t align_up_elems(size_t n)
     return (n + 15) & ~size_t(15);
 }
 
+// Sum over the P lanes of one particle group; the total lands on offset 0.
+template <typename T, int P>
+__device__ __forceinline__ T group_sum(T v, int dx)
+{
+#pragma unroll
+    for (int o = LaneMap<P>::NP2 / 2; o >= 1; o >>= 1) {
+        const T t = __shfl_down_sync(0xffffffffu, v, o);
+        if (dx < o && dx + o < P) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int block_base(const TileGeom &tg, int code)
+{
+    return ((code >> 16) * tg.B[1] + ((code >> 8) & 255)) * tg.B[0] + (code & 255);
+}
+
 // ----------------------------------------------------------------- gridding
 // Eq. (gridding) for the particles of one tile: one CTA per tile, the tile's
-// extended block (T + P - 1)^3 accumulated in shared memory (one warp per
-// particle, each lane a share of the stencil plane, looping over z), then
-// written to the tile's slot in `scratch`.  When g != nullptr the charges are
-// taken from g (original particle order) instead of the sorted records (the
-// second spread of the adjoint).
-template <typename T, int P>
+// extended block (T + P - 1)^3 accumulated in shared memory, then written to
+// the tile's slot in `scratch`.  Lane (particle g, offset dx) adds
+// q W_x(dx) W_z(dz) W_y(dy) to the row (dy, dz) point dx for every dy, dz.
+// When g != nullptr the charges are taken from g (original particle order)
+// instead of the sorted records (the second gridding of the adjoint).
+template <typename T, int P, int NU>
 __global__ void __launch_bounds__(kThreads)
 k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
          const int2 *__restrict__ ic, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
 {
+    constexpr int G = LaneMap<P>::G;
     const int tile = blockIdx.x;
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *blk = reinterpret_cast<T *>(smraw);
     const int nblk = tg.blk;
-    T *sc = blk + align_up_elems<T>(nblk);
-    const int ncoef = (wa.nu + 1) * P;
-    T *wb = sc + align_up_elems<T>(ncoef);
+    T *wb = blk + align_up_elems<T>(nblk);          // [warp][G][3][P]
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) blk[i] = T(0);
-    if (wa.kind == SE_WIN_PKB)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
-    __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    T *w = wb + warp * 3 * P;
+    const int grp = lane / P, dx = lane - grp * P;
+    const bool lane_on = grp < G;
+    LaneCoef<T, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+    T *w = wb + (warp * G + (lane_on ? grp : 0)) * 3 * P;
     const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
-    PlaneShare<P> ps;
-    ps.init(lane, BX);
+    __syncthreads();
 
-    for (int p = beg + warp; p < end; p += nw) {
-        const typename Vec4<T>::type r = fq[p];
-        const int2 c = ic[p];
-        const T qv = g ? g[c.x] : r.w;
-        for (int j = lane; j < 3 * P; j += 32) {
-            const int a = j / P, k = j - a * P;
-            const T fr = a == 0 ? r.x : (a == 1 ? r.y : r.z);
-            w[j] = win_val<T, P>(wa.kind, wa.nu, wa.alpha, sc, fr, k);
+    for (int p0 = beg + warp * G; p0 < end; p0 += nw * G) {
+        const int p = p0 + grp;
+        const bool has = lane_on && p < end;
+        typename Vec4<T>::type r;
+        int2 c = make_int2(0, 0);
+        T qv = T(0);
+        if (has) {
+            r = fq[p];
+            c = ic[p];
+            qv = g ? g[c.x] : r.w;
+            T w0, w1, w2, dd;
+            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.x, dx, w0, dd);
+            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.y, dx, w1, dd);
+            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.z, dx, w2, dd);
+            w[dx] = w0;
+            w[P + dx] = w1;
+            w[2 * P + dx] = w2;
         }
         __syncwarp();
-        const int base = ((c.y >> 16) * tg.B[1] + ((c.y >> 8) & 255)) * BX + (c.y & 255);
-        T wxy[PlaneShare<P>::NE];
+        if (has) {
+            T wy[P];
 #pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) wxy[e] = qv * w[ps.dx[e]] * w[P + ps.dy[e]];
+            for (int j = 0; j < P; ++j) wy[j] = w[P + j];
+            const T wxq = qv * w[dx];
+            T *col = blk + block_base(tg, c.y) + dx;
 #pragma unroll
-        for (int dz = 0; dz < P; ++dz) {
-            const T wz = w[2 * P + dz];
-            T *row = blk + base + dz * BXY;
+            for (int dz = 0; dz < P; ++dz) {
+                const T t = wxq * w[2 * P + dz];
+                T *row = col + dz * BXY;
 #pragma unroll
-            for (int e = 0; e < PlaneShare<P>::NE; ++e)
-                if (ps.v[e]) atomicAdd(row + ps.off[e], wxy[e] * wz);
+                for (int dy = 0; dy < P; ++dy) atomicAdd(row + dy * BX, t * wy[dy]);
+            }
         }
         __syncwarp();
     }
@@ -251,46 +281,43 @@ k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) dst[i] = blk[i];
 }
 
-// Sum of the tile blocks covering each grid point, in a fixed order (tile
-// candidates along z, then y, then x), written to the forward-FFT input.
+// Sum of the tile blocks covering each grid point, in a fixed order, written
+// to the forward-FFT input.  One CTA per tile writes that tile's T0 x T1 x T2
+// points (threads laid out over x, y; loop over z); each point adds the blocks
+// of the tiles c - j (per axis, while the offset stays inside the block).
 // Tiles without particles hold no block and are skipped.  Periodic axes wrap
 // the tile index (their tile edge divides the grid); free axes never wrap.
 template <typename T>
-__global__ void k_merge(TileGeom tg, int P, const int *__restrict__ off, const T *__restrict__ scratch,
+__global__ void k_merge(TileGeom tg, const int *__restrict__ off, const T *__restrict__ scratch,
                         T *__restrict__ dst, GridView v)
 {
-    const int64_t n0 = tg.n[0], n1 = tg.n[1], n2 = tg.n[2];
-    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= n0 * n1 * n2) return;
-    const int g0 = int(i % n0), g1 = int((i / n0) % n1), g2 = int(i / (n0 * n1));
-    const int gg[3] = {g0, g1, g2};
-    int cand[3][6], offs[3][6], nc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        nc[a] = 0;
-        const int base = gg[a] / tg.T[a], o = gg[a] - base * tg.T[a];
-        for (int j = 0; j < 6; ++j) {
-            const int oo = o + j * tg.T[a];
-            if (oo >= tg.B[a]) break;
-            int cc = base - j;
-            if (cc < 0) {
-                if (!tg.periodic[a]) break;
-                cc = ((cc % tg.nt[a]) + tg.nt[a]) % tg.nt[a];
+    const int tile = blockIdx.x;
+    const int c0 = tile % tg.nt[0], c1 = (tile / tg.nt[0]) % tg.nt[1], c2 = tile / (tg.nt[0] * tg.nt[1]);
+    const int l0 = threadIdx.x, l1 = threadIdx.y;
+    const int g0 = c0 * tg.T[0] + l0, g1 = c1 * tg.T[1] + l1;
+    if (l0 >= tg.T[0] || l1 >= tg.T[1] || g0 >= tg.n[0] || g1 >= tg.n[1]) return;
+    for (int l2 = threadIdx.z; l2 < tg.T[2]; l2 += blockDim.z) {
+        const int g2 = c2 * tg.T[2] + l2;
+        if (g2 >= tg.n[2]) break;
+        T s = T(0);
+        for (int j2 = 0; l2 + j2 * tg.T[2] < tg.B[2]; ++j2) {
+            int t2 = c2 - j2;
+            if (t2 < 0) { if (!tg.periodic[2]) break; t2 = ((t2 % tg.nt[2]) + tg.nt[2]) % tg.nt[2]; }
+            for (int j1 = 0; l1 + j1 * tg.T[1] < tg.B[1]; ++j1) {
+                int t1 = c1 - j1;
+                if (t1 < 0) { if (!tg.periodic[1]) break; t1 = ((t1 % tg.nt[1]) + tg.nt[1]) % tg.nt[1]; }
+                for (int j0 = 0; l0 + j0 * tg.T[0] < tg.B[0]; ++j0) {
+                    int t0 = c0 - j0;
+                    if (t0 < 0) { if (!tg.periodic[0]) break; t0 = ((t0 % tg.nt[0]) + tg.nt[0]) % tg.nt[0]; }
+                    const int src = (t2 * tg.nt[1] + t1) * tg.nt[0] + t0;
+                    if (off[src + 1] == off[src]) continue;
+                    s += scratch[size_t(src) * tg.blk +
+                                 ((l2 + j2 * tg.T[2]) * tg.B[1] + (l1 + j1 * tg.T[1])) * tg.B[0] + l0 + j0 * tg.T[0]];
+                }
             }
-            cand[a][nc[a]] = cc;
-            offs[a][nc[a]] = oo;
-            ++nc[a];
         }
+        dst[g0 + g1 * v.s1 + g2 * v.s2] = s;
     }
-    T s = T(0);
-    for (int jz = 0; jz < nc[2]; ++jz)
-        for (int jy = 0; jy < nc[1]; ++jy)
-            for (int jx = 0; jx < nc[0]; ++jx) {
-                const int tile = (cand[2][jz] * tg.nt[1] + cand[1][jy]) * tg.nt[0] + cand[0][jx];
-                if (off[tile + 1] == off[tile]) continue;
-                s += scratch[size_t(tile) * tg.blk + (offs[2][jz] * tg.B[1] + offs[1][jy]) * tg.B[0] + offs[0][jx]];
-            }
-    dst[g0 + g1 * v.s1 + g2 * v.s2] = s;
 }
 
 // ----------------------------------------------------------------- scaling
@@ -416,30 +443,45 @@ __global__ void k_unpad_1p(int nl, int Mt, int sMt, int s0Mt, int row, typename 
 }
 
 // ----------------------------------------------------------------- gathering
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Stage the extended block of a tile from the real grid (periodic axes wrap;
-// points past a free axis' end are never used and are set to zero).
+// Stage the extended block of a tile from the real grid into shared memory
+// with asynchronous copies (one row per warp iteration, lanes along x;
+// periodic axes wrap, points past a free axis' end are never used and are set
+// to zero).  The caller waits (cp_async_wait_all) and synchronises.
 template <typename T>
 __device__ __forceinline__ void stage_block(const TileGeom &tg, int tile, const T *__restrict__ grid, GridView v,
                                             T *blk)
 {
     const int tx = tile % tg.nt[0], ty = (tile / tg.nt[0]) % tg.nt[1], tz = tile / (tg.nt[0] * tg.nt[1]);
     const int o0 = tx * tg.T[0], o1 = ty * tg.T[1], o2 = tz * tg.T[2];
-    for (int i = threadIdx.x; i < tg.blk; i += blockDim.x) {
-        const int b0 = i % tg.B[0], b1 = (i / tg.B[0]) % tg.B[1], b2 = i / (tg.B[0] * tg.B[1]);
-        int g0 = o0 + b0, g1 = o1 + b1, g2 = o2 + b2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int rows = tg.B[1] * tg.B[2];
+    for (int r = warp; r < rows; r += nw) {
+        const int b1 = r % tg.B[1], b2 = r / tg.B[1];
+        int g1 = o1 + b1, g2 = o2 + b2;
         bool ok = true;
-        if (g0 >= tg.n[0]) { if (tg.periodic[0]) g0 %= tg.n[0]; else ok = false; }
-        if (g1 >= tg.n[1]) { if (tg.periodic[1]) g1 %= tg.n[1]; else ok = false; }
-        if (g2 >= tg.n[2]) { if (tg.periodic[2]) g2 %= tg.n[2]; else ok = false; }
-        blk[i] = ok ? grid[g0 + g1 * v.s1 + g2 * v.s2] : T(0);
+        if (g1 >= tg.n[1]) { if (tg.periodic[1]) { while (g1 >= tg.n[1]) g1 -= tg.n[1]; } else ok = false; }
+        if (g2 >= tg.n[2]) { if (tg.periodic[2]) { while (g2 >= tg.n[2]) g2 -= tg.n[2]; } else ok = false; }
+        T *drow = blk + r * tg.B[0];
+        const T *srow = grid + g1 * v.s1 + g2 * v.s2;
+        for (int b0 = lane; b0 < tg.B[0]; b0 += 32) {
+            int g0 = o0 + b0;
+            bool okx = ok;
+            if (g0 >= tg.n[0]) { if (tg.periodic[0]) { while (g0 >= tg.n[0]) g0 -= tg.n[0]; } else okx = false; }
+            if (okx) cp_async_elem(drow + b0, srow + g0);
+            else drow[b0] = T(0);
+        }
     }
 }
 
@@ -447,14 +489,18 @@ __device__ __forceinline__ void stage_block(const TileGeom &tg, int tile, const 
 // inverse-FFT normalisation are folded into the scaling) and, with GRAD,
 // Eq. (force-method-1): grad phi = sum_j grad W(x_m - x_j) H~_j, the window
 // gradient being the exact derivative of the window used for gridding.
-// Outputs go to the particles' original positions: phi_m (+ self term),
-// F_m = -q_m grad phi_m, and per-tile partial sums of 1/2 q_m phi_m in FP64.
-template <typename T, int P, bool GRAD>
+// Lane (particle, dx) walks the P x P rows (dy, dz) at offset dx, summing over
+// dy in registers, then over dz; the P lanes of a particle are reduced by
+// shuffles.  Outputs go to the particles' original positions: phi_m (+ self
+// term), F_m = -q_m grad phi_m, and per-tile partial sums of 1/2 q_m phi_m in
+// FP64.
+template <typename T, int P, int NU, bool GRAD>
 __global__ void __launch_bounds__(kThreads)
 k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
          const int2 *__restrict__ ic, WindowArgs<T> wa, const T *__restrict__ grid, GridView v,
          T *__restrict__ phi, T *__restrict__ F, double *__restrict__ tile_part, T inv_h, T self_coef)
 {
+    constexpr int G = LaneMap<P>::G;
     const int tile = blockIdx.x;
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) {
@@ -463,71 +509,85 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
     }
     extern __shared__ __align__(16) unsigned char smraw[];
     T *blk = reinterpret_cast<T *>(smraw);
-    const int nblk = tg.blk;
-    T *sc = blk + align_up_elems<T>(nblk);
-    const int ncoef = (wa.nu + 1) * P;
-    T *sdc = sc + align_up_elems<T>(ncoef);
-    const int ndcoef = wa.nu * P;
-    T *wb = sdc + align_up_elems<T>(ndcoef);
+    T *wb = blk + align_up_elems<T>(tg.blk);        // [warp][G][6][P]: values x,y,z then derivatives
     __shared__ double epart[kThreads / 32];
     stage_block<T>(tg, tile, grid, v, blk);
-    if (wa.kind == SE_WIN_PKB) {
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
-        for (int i = threadIdx.x; i < ndcoef; i += blockDim.x) sdc[i] = wa.dc[i];
-    }
-    __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    T *w = wb + warp * 6 * P;     // [0, 3P): values, [3P, 6P): derivatives
+    const int grp = lane / P, dx = lane - grp * P;
+    const bool lane_on = grp < G;
+    LaneCoef<T, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+    T *w = wb + (warp * G + (lane_on ? grp : 0)) * 6 * P;
     const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
-    PlaneShare<P> ps;
-    ps.init(lane, BX);
     double esum = 0.0;
+    cp_async_wait_all();
+    __syncthreads();
 
-    for (int p = beg + warp; p < end; p += nw) {
-        const typename Vec4<T>::type r = fq[p];
-        const int2 c = ic[p];
-        for (int j = lane; j < 3 * P; j += 32) {
-            const int a = j / P, k = j - a * P;
-            const T fr = a == 0 ? r.x : (a == 1 ? r.y : r.z);
-            const T val = win_val<T, P>(wa.kind, wa.nu, wa.alpha, sc, fr, k);
-            w[j] = val;
-            if (GRAD) w[3 * P + j] = win_der<T, P>(wa.kind, wa.nu, wa.alpha, sdc, fr, k, val);
+    for (int p0 = beg + warp * G; p0 < end; p0 += nw * G) {
+        const int p = p0 + grp;
+        const bool has = lane_on && p < end;
+        typename Vec4<T>::type r;
+        int2 c = make_int2(0, 0);
+        if (has) {
+            r = fq[p];
+            c = ic[p];
+            T w0, w1, w2, d0, d1, d2;
+            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.x, dx, w0, d0);
+            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.y, dx, w1, d1);
+            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.z, dx, w2, d2);
+            w[dx] = w0;
+            w[P + dx] = w1;
+            w[2 * P + dx] = w2;
+            if (GRAD) {
+                w[3 * P + dx] = d0;
+                w[4 * P + dx] = d1;
+                w[5 * P + dx] = d2;
+            }
         }
         __syncwarp();
-        const int base = ((c.y >> 16) * tg.B[1] + ((c.y >> 8) & 255)) * BX + (c.y & 255);
-        T s0[PlaneShare<P>::NE], s1[PlaneShare<P>::NE];
+        T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
+        if (has) {
+            T wy[P], dwy[P];
 #pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) { s0[e] = T(0); s1[e] = T(0); }
+            for (int j = 0; j < P; ++j) {
+                wy[j] = w[P + j];
+                if (GRAD) dwy[j] = w[4 * P + j];
+            }
+            const T *col = blk + block_base(tg, c.y) + dx;
+            T sp = T(0), sgy = T(0), sgz = T(0);
 #pragma unroll
-        for (int dz = 0; dz < P; ++dz) {
-            const T wz = w[2 * P + dz];
-            const T dwz = GRAD ? w[5 * P + dz] : T(0);
-            const T *row = blk + base + dz * BXY;
+            for (int dz = 0; dz < P; ++dz) {
+                const T *row = col + dz * BXY;
+                T t0 = T(0), t1 = T(0);
 #pragma unroll
-            for (int e = 0; e < PlaneShare<P>::NE; ++e) {
-                if (ps.v[e]) {
-                    const T hv = row[ps.off[e]];
-                    s0[e] = fma(wz, hv, s0[e]);
-                    if (GRAD) s1[e] = fma(dwz, hv, s1[e]);
+                for (int dy = 0; dy < P; ++dy) {
+                    const T hv = row[dy * BX];
+                    t0 = fma(wy[dy], hv, t0);
+                    if (GRAD) t1 = fma(dwy[dy], hv, t1);
+                }
+                const T wz = w[2 * P + dz];
+                sp = fma(wz, t0, sp);
+                if (GRAD) {
+                    sgy = fma(wz, t1, sgy);
+                    sgz = fma(w[5 * P + dz], t0, sgz);
                 }
             }
-        }
-        T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
-#pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) {
-            if (!ps.v[e]) continue;
-            const T wx = w[ps.dx[e]], wy = w[P + ps.dy[e]];
-            ph = fma(wx * wy, s0[e], ph);
+            const T wx = w[dx];
+            ph = wx * sp;
             if (GRAD) {
-                gx = fma(w[3 * P + ps.dx[e]] * wy, s0[e], gx);
-                gy = fma(wx * w[4 * P + ps.dy[e]], s0[e], gy);
-                gz = fma(wx * wy, s1[e], gz);
+                gx = w[3 * P + dx] * sp;
+                gy = wx * sgy;
+                gz = wx * sgz;
             }
         }
-        ph = warp_sum(ph);
-        if (GRAD) { gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz); }
-        if (lane == 0) {
+        ph = group_sum<T, P>(ph, dx);
+        if (GRAD) {
+            gx = group_sum<T, P>(gx, dx);
+            gy = group_sum<T, P>(gy, dx);
+            gz = group_sum<T, P>(gz, dx);
+        }
+        if (has && dx == 0) {
             const T qv = r.w;
             const T phv = ph + self_coef * qv;
             const int64_t m = c.x;
@@ -543,6 +603,7 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
         __syncwarp();
     }
     if (tile_part) {
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
         if (lane == 0) epart[warp] = esum;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -558,87 +619,92 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
 //   g_q[m] = sum_j W(x_m - x_j) H~_g[j]                         (= (A g)_m)
 //   g_x[m] = g_m grad_m sum_j W H~_q[j] + q_m grad_m sum_j W H~_g[j].
 // Both blocks are staged in shared memory.
-template <typename T, int P>
+template <typename T, int P, int NU>
 __global__ void __launch_bounds__(kThreads)
 k_gather_vjp(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
              const int2 *__restrict__ ic, WindowArgs<T> wa, const T *__restrict__ grid_q,
-             const T *__restrict__ grid_g, GridView v, const T *__restrict__ g, T *__restrict__ gx,
-             T *__restrict__ gq, T inv_h)
+             const T *__restrict__ grid_g, GridView v, const T *__restrict__ g, T *__restrict__ gxo,
+             T *__restrict__ gqo, T inv_h)
 {
+    constexpr int G = LaneMap<P>::G;
     const int tile = blockIdx.x;
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *bq = reinterpret_cast<T *>(smraw);
-    const int nblk = tg.blk;
-    T *bg = bq + align_up_elems<T>(nblk);
-    T *sc = bg + align_up_elems<T>(nblk);
-    const int ncoef = (wa.nu + 1) * P;
-    T *sdc = sc + align_up_elems<T>(ncoef);
-    const int ndcoef = wa.nu * P;
-    T *wb = sdc + align_up_elems<T>(ndcoef);
+    T *bg = bq + align_up_elems<T>(tg.blk);
+    T *wb = bg + align_up_elems<T>(tg.blk);
     stage_block<T>(tg, tile, grid_q, v, bq);
     stage_block<T>(tg, tile, grid_g, v, bg);
-    if (wa.kind == SE_WIN_PKB) {
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
-        for (int i = threadIdx.x; i < ndcoef; i += blockDim.x) sdc[i] = wa.dc[i];
-    }
-    __syncthreads();
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    T *w = wb + warp * 6 * P;
+    const int grp = lane / P, dx = lane - grp * P;
+    const bool lane_on = grp < G;
+    LaneCoef<T, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+    T *w = wb + (warp * G + (lane_on ? grp : 0)) * 6 * P;
     const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
-    PlaneShare<P> ps;
-    ps.init(lane, BX);
-    for (int p = beg + warp; p < end; p += nw) {
-        const typename Vec4<T>::type r = fq[p];
-        const int2 c = ic[p];
-        for (int j = lane; j < 3 * P; j += 32) {
-            const int a = j / P, k = j - a * P;
-            const T fr = a == 0 ? r.x : (a == 1 ? r.y : r.z);
-            const T val = win_val<T, P>(wa.kind, wa.nu, wa.alpha, sc, fr, k);
-            w[j] = val;
-            w[3 * P + j] = win_der<T, P>(wa.kind, wa.nu, wa.alpha, sdc, fr, k, val);
+    cp_async_wait_all();
+    __syncthreads();
+
+    for (int p0 = beg + warp * G; p0 < end; p0 += nw * G) {
+        const int p = p0 + grp;
+        const bool has = lane_on && p < end;
+        typename Vec4<T>::type r;
+        int2 c = make_int2(0, 0);
+        T gm = T(0);
+        if (has) {
+            r = fq[p];
+            c = ic[p];
+            gm = g[c.x];
+            T w0, w1, w2, d0, d1, d2;
+            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.x, dx, w0, d0);
+            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.y, dx, w1, d1);
+            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.z, dx, w2, d2);
+            w[dx] = w0; w[P + dx] = w1; w[2 * P + dx] = w2;
+            w[3 * P + dx] = d0; w[4 * P + dx] = d1; w[5 * P + dx] = d2;
         }
         __syncwarp();
-        const int base = ((c.y >> 16) * tg.B[1] + ((c.y >> 8) & 255)) * BX + (c.y & 255);
-        const T gm = g[c.x], qm = r.w;
-        T s0[PlaneShare<P>::NE], s1[PlaneShare<P>::NE];
-#pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) { s0[e] = T(0); s1[e] = T(0); }
-        T t0[PlaneShare<P>::NE], t1[PlaneShare<P>::NE];
-#pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) { t0[e] = T(0); t1[e] = T(0); }
-#pragma unroll
-        for (int dz = 0; dz < P; ++dz) {
-            const T wz = w[2 * P + dz], dwz = w[5 * P + dz];
-            const int o = base + dz * BXY;
-#pragma unroll
-            for (int e = 0; e < PlaneShare<P>::NE; ++e) {
-                if (!ps.v[e]) continue;
-                // combined grid gm H~_q + qm H~_g for the position gradient
-                const T hq = bq[o + ps.off[e]], hg = bg[o + ps.off[e]];
-                const T hc = gm * hq + qm * hg;
-                s0[e] = fma(wz, hc, s0[e]);
-                s1[e] = fma(dwz, hc, s1[e]);
-                t0[e] = fma(wz, hg, t0[e]);
-            }
-        }
         T a0 = T(0), ax = T(0), ay = T(0), az = T(0);
+        if (has) {
+            const T qm = r.w;
+            T wy[P], dwy[P];
 #pragma unroll
-        for (int e = 0; e < PlaneShare<P>::NE; ++e) {
-            if (!ps.v[e]) continue;
-            const T wx = w[ps.dx[e]], wy = w[P + ps.dy[e]];
-            a0 = fma(wx * wy, t0[e], a0);
-            ax = fma(w[3 * P + ps.dx[e]] * wy, s0[e], ax);
-            ay = fma(wx * w[4 * P + ps.dy[e]], s0[e], ay);
-            az = fma(wx * wy, s1[e], az);
+            for (int j = 0; j < P; ++j) { wy[j] = w[P + j]; dwy[j] = w[4 * P + j]; }
+            const int b = block_base(tg, c.y) + dx;
+            T sp = T(0), sgy = T(0), sgz = T(0), sq = T(0);
+#pragma unroll
+            for (int dz = 0; dz < P; ++dz) {
+                T t0 = T(0), t1 = T(0), t2 = T(0);
+#pragma unroll
+                for (int dy = 0; dy < P; ++dy) {
+                    const int o = b + dz * BXY + dy * BX;
+                    const T hg = bg[o];
+                    const T hc = gm * bq[o] + qm * hg;     // grid of g_m H~_q + q_m H~_g
+                    t0 = fma(wy[dy], hc, t0);
+                    t1 = fma(dwy[dy], hc, t1);
+                    t2 = fma(wy[dy], hg, t2);
+                }
+                const T wz = w[2 * P + dz], dwz = w[5 * P + dz];
+                sp = fma(wz, t0, sp);
+                sgy = fma(wz, t1, sgy);
+                sgz = fma(dwz, t0, sgz);
+                sq = fma(wz, t2, sq);
+            }
+            const T wx = w[dx];
+            a0 = wx * sq;
+            ax = w[3 * P + dx] * sp;
+            ay = wx * sgy;
+            az = wx * sgz;
         }
-        (void)t1;
-        a0 = warp_sum(a0); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
-        if (lane == 0) {
+        a0 = group_sum<T, P>(a0, dx);
+        ax = group_sum<T, P>(ax, dx);
+        ay = group_sum<T, P>(ay, dx);
+        az = group_sum<T, P>(az, dx);
+        if (has && dx == 0) {
             const int64_t m = c.x;
-            if (gq) gq[m] = a0;
-            if (gx) { gx[3 * m] = ax * inv_h; gx[3 * m + 1] = ay * inv_h; gx[3 * m + 2] = az * inv_h; }
+            if (gqo) gqo[m] = a0;
+            if (gxo) { gxo[3 * m] = ax * inv_h; gxo[3 * m + 1] = ay * inv_h; gxo[3 * m + 2] = az * inv_h; }
         }
         __syncwarp();
     }

@@ -11,7 +11,8 @@ Named workloads (the sizes the tests and the benchmark use):
 * ``lattice_3p``    D = 3, N = 1000 uniform, alternating +-1 charges, xi = 8,
                     M = 32, truncated Gaussian P = 8, FP64 (plus the NaCl cell).
 * ``free_0p``       D = 0, N = 20000 uniform, q ~ U(-1,1) shifted to zero sum,
-                    M = 48, PKB P = 8, xi = 8, FP32 and FP64, phi + F.
+                    M = 48, PKB P = 8, xi = 8, extension lambda = 2 (M~ = 64,
+                    FFT 128^3), FP32 and FP64, phi + F.
 * ``slab_2p``       D = 2, N = 100000 uniform, M = 64, PKB P = 6 (FP32) and
                     P = 10 (FP64), xi = 16.
 * ``wire_1p``       D = 1, N = 1.2e6 (1e6 uniform + 2e5 in ten Gaussian blobs,
@@ -26,7 +27,7 @@ WORKLOADS = {
     "lattice_3p": dict(D=3, N=1000, L=1.0, xi=8.0, M=32, P=8, window="gaussian",
                        charges="alternating"),
     "free_0p": dict(D=0, N=20000, L=1.0, xi=8.0, M=48, P=8, window="pkb",
-                    charges="uniform"),
+                    charges="uniform", lam=2.0),
     "slab_2p": dict(D=2, N=100000, L=1.0, xi=16.0, M=64, P=6, window="pkb",
                     charges="uniform", P_fp64=10),
     "wire_1p": dict(D=1, N=1200000, L=1.0, xi=32.0, M=128, P=8, window="pkb",
