@@ -169,6 +169,27 @@ se_status se_vjp(se_plan_t plan, int64_t N, const void *x, const void *q, const 
 se_status se_plan_set_profiling(se_plan_t plan, int enable);
 se_status se_plan_get_profile(se_plan_t plan, double *ms, int64_t *calls, int64_t *launches);
 
+/* Potential of se_potential, computed without allocating device memory.
+ * The paper has no counterpart: this entry point serves callers that must not
+ * call cudaMalloc while they run (a fixed memory budget handed out at start-up,
+ * a loop where cudaMalloc's implicit device synchronisation is unacceptable, a
+ * framework whose allocator owns all device memory during a step).  Create the
+ * plan and call se_plan_reserve(plan, n_max) at set-up; afterwards this call
+ * allocates nothing.  The per-tile gridding blocks live in a fixed array of
+ * SE_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - The first call on a device looks up that array's device address (once per
+ *    device); make that first call before any CUDA stream capture.
+ *  - All calls share the array and it keeps the last call's contents; calls
+ *    whose work overlaps on the GPU (several streams or plans at once) race.
+ *  - Arguments as se_potential (device pointers; SE_ADD_SELF, SE_CHECK_NEUTRAL,
+ *    SE_SYNC_CHECK).  Errors: SE_ECAPACITY when N exceeds the reserved
+ *    capacity or the plan's gridding blocks exceed the fixed array;
+ *    SE_EINVAL for SE_HOST_IO (it needs staging memory) or bad arguments. */
+#define SE_NOALLOC_SCRATCH_BYTES (32u << 20)
+se_status se_potential_noalloc(se_plan_t plan, int64_t N, const void *x, const void *q, void *phi,
+                               unsigned flags);
+
 /* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
  * approximation-error estimates of Sec. 5.2, rounded up to even, with the
  * error-pollution rule of Eq. error_pollution) for an absolute rms tolerance

@@ -20,7 +20,7 @@ STATUS = {0: "SE_OK", 1: "SE_EINVAL", 2: "SE_ENONNEUTRAL", 3: "SE_EOUTOFBOX", 4:
 # every symbol declared in include/se_gb300.h
 EXPORTS = ["se_opts_default", "se_plan_create", "se_plan_destroy", "se_plan_set_stream", "se_plan_reserve",
            "se_plan_get_info", "se_plan_check", "se_potential", "se_force", "se_vjp",
-           "se_plan_set_profiling", "se_plan_get_profile",
+           "se_plan_set_profiling", "se_plan_get_profile", "se_potential_noalloc",
            "se_params_from_tolerance", "se_status_str", "se_last_error"]
 SE_N_STAGES = 8
 STAGES = ["bin", "spread", "merge", "fft_fwd", "scale", "fft_inv", "gather", "energy"]
@@ -80,6 +80,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "se_force": (ci, [vp, i64, vp, vp, vp, vp, vp, cu]),
         "se_vjp": (ci, [vp, i64, vp, vp, vp, vp, vp]),
         "se_plan_set_profiling": (ci, [vp, ci]),
+        "se_potential_noalloc": (ci, [vp, i64, vp, vp, vp, cu]),
         "se_plan_get_profile": (ci, [vp, ctypes.POINTER(cd), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "se_params_from_tolerance": (ci, [cd, cd, cd, cd, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "se_status_str": (ctypes.c_char_p, [ci]),

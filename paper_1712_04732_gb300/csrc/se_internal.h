@@ -168,6 +168,8 @@ struct Ops {
                                 const void *grid_g, T *gx, T *gq);
     // device reduction of sum q and sum |q| into p->red[0..1]
     static se_status charge_sums(se_plan_s *p, int64_t N, const T *q);
+    // as spread(), with the per-tile gridding blocks in caller-provided device memory
+    static se_status spread_with_scratch(se_plan_s *p, void *dst, void *scratch);
 };
 
 }  // namespace se

@@ -320,6 +320,32 @@ se_status Ops<T>::charge_sums(se_plan_s *p, int64_t N, const T *q)
     return SE_OK;
 }
 
+// Gridding with the per-tile blocks in caller-provided device memory of at least
+// n_tiles * block * sizeof(T) bytes (used by the allocation-free entry point).
+template <typename T>
+se_status Ops<T>::spread_with_scratch(se_plan_s *p, void *dst, void *scratch)
+{
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    const size_t sm = spread_smem<T>(p);
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+    SE_DISPATCH_P(p->P, nu, {
+        auto kern = k_spread<T, PP, NN>;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, nullptr, wa,
+                                              reinterpret_cast<T *>(scratch));
+    });
+    SE_LAUNCH_CHECK("spread");
+    const int t01 = p->tg.T[0] * p->tg.T[1];
+    dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
+    k_merge<T><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
+                                         reinterpret_cast<T *>(dst), p->gin);
+    SE_LAUNCH_CHECK("merge");
+    return SE_OK;
+}
+
 template struct Ops<T_INST>;
 
 }  // namespace se
