@@ -53,6 +53,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(v: float, device) -> float:
+    """Largest value of v over the ranks of the default process group (v itself
+    without one): the timing rule takes the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(n_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job particles per second: every rank processes its own replica."""
+    return world * n_per_rank / seconds
+
+
 def algorithmic_counts(P: int, nu: int, window: str):
     """Per-particle FMA counts of the tile kernels (PKB: Horner of degree nu for
     3P weights, their derivatives for the gradient):
@@ -210,12 +227,9 @@ def run_ours(a):
             e1.record()
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
-        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps, dev)
         if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             torch.distributed.barrier()
-            ms = t.item()
         return ms, wall
 
     # ---- FP32 form (the headline) -------------------------------------------------
@@ -224,7 +238,7 @@ def run_ours(a):
     clocks = Clocks(local)
     ms32, wall32 = timed(plan32, x32, q32, out32, g32, a.steps, a.warmup)
     clk = clocks.stop()
-    value = world * N / (ms32 * 1e-3)
+    value = aggregate_throughput(N, world, ms32 * 1e-3)
 
     # ---- FP64 form ---------------------------------------------------------------
     plan64, x64, q64, out64 = make_form(torch.float64)
@@ -280,21 +294,17 @@ def run_ours(a):
     t0 = time.perf_counter()
     for _ in range(ke):
         plan32.force_host(xh, qh, Fh, ph, eh)
-    e2e_s = (time.perf_counter() - t0) / ke
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = t.item()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ke, dev)
 
     line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(spec),
-            "fp64_form": {"value": world * N / (ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
+            "fp64_form": {"value": aggregate_throughput(N, world, ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
                           "steps": k64, "speedup_fp32_over_fp64": ms64 / ms32},
             "roofline": roof,
             "stage_ms": stage_ms,
             "spread_gather_gbs": sg_gbs,
-            "e2e": {"value": world * N / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": N * 16,
+            "e2e": {"value": aggregate_throughput(N, world, e2e_s), "unit": "particles/s", "h2d_bytes_per_step": N * 16,
                     "d2h_bytes_per_step": N * 16 + 8, "api": "se_force with SE_HOST_IO (pinned host buffers)"},
             "gpu_launches": int(round(launches_per_step * a.steps)),
             "gpu_launches_per_step": launches_per_step,

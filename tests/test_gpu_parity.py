@@ -103,9 +103,11 @@ def test_tile_edges(tile):
 
 
 def test_positions_on_grid_lines_and_box_faces():
-    """Particles exactly on grid nodes, on tile boundaries and at x = 0."""
+    """Particles exactly on grid nodes, on tile boundaries and at x = 0.  With a
+    dyadic spacing (M = 32) x / h is exact in both the kernel and the oracle, so
+    both place the support identically and agree to rounding."""
     se = _se()
-    M = 24
+    M = 32
     h = 1.0 / M
     rng = np.random.default_rng(4)
     x = rng.integers(0, M, size=(200, 3)) * h
@@ -117,6 +119,23 @@ def test_positions_on_grid_lines_and_box_faces():
         F, phi, _ = _run(plan, x, q)
         pb, gb = _oracle_for(plan).potential(x, q, grad=True)
         assert _rel(phi, pb) < 1e-11
+
+
+def test_positions_on_grid_lines_non_dyadic_spacing():
+    """With h = 1/24 a node coordinate x / h may round to either side of the
+    integer, which moves the support by one point; the truncated window's edge
+    value W(w) = 1/I0(beta) bounds the difference (Sec. 4: the KB window does
+    not vanish at |x| = w)."""
+    se = _se()
+    M = 24
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, M, size=(200, 3)) / M
+    q = wl.uniform_charges(200, 9)
+    plan = se.Plan(3, 1.0, 6.0, M, 6, "pkb", dtype=torch.float64)
+    F, phi, _ = _run(plan, x, q)
+    pb, _ = _oracle_for(plan).potential(x, q, grad=True)
+    from scipy.special import i0
+    assert _rel(phi, pb) < 20.0 / i0(2.5 * 6)
 
 
 def test_periodic_coordinates_are_wrapped():
