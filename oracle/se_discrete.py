@@ -137,10 +137,10 @@ class SEOracle:
         nx, ny, nz = self.n
         for a in range(P):
             for b in range(P):
-                for c in range(P):
-                    flat = (j[:, 0, a] * ny + j[:, 1, b]) * nz + j[:, 2, c]
-                    val = q * w[:, 0, a] * w[:, 1, b] * w[:, 2, c]
-                    H.reshape(-1)[:] += np.bincount(flat, weights=val, minlength=H.size)
+                # all P support points along z of the (a, b) column at once
+                flat = (j[:, 0, a, None] * ny + j[:, 1, b, None]) * nz + j[:, 2, :]
+                val = (q * w[:, 0, a] * w[:, 1, b])[:, None] * w[:, 2, :]
+                H.reshape(-1)[:] += np.bincount(flat.ravel(), weights=val.ravel(), minlength=H.size)
         return H
 
     # ---- steps 2-4 -------------------------------------------------------
