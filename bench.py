@@ -37,6 +37,10 @@ L2_FLUSH_BYTES = 256 << 20
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the tile kernels on this workload,
+# from one ncu --set full capture (profiles/free_0p_tile_kernels.md); reset to None whenever the
+# kernel changes
+NCU_TRAFFIC = {"spread": 659712, "gather": 1436160}
 
 
 def args_parse():
@@ -46,6 +50,7 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -163,6 +168,48 @@ def _config(spec):
             "l2": "flushed (256 MB write) before every timed step", "timing": "CUDA graph replay, CUDA events"}
 
 
+def run_batch(se, wl, dev, flush, steps):
+    """64 independent systems, N log-uniform in [1e3, 1e5], D alternating 3, 2,
+    xi = 8 (N/1e4)^(1/3), PKB, per-system M and P from the Sec. 6 rules at
+    relative tolerance 1e-5, FP32, phi + F: the batched graph against one plain
+    se_force call per system, both timed with CUDA events after an L2 flush."""
+    import numpy as np
+    import torch
+    sysl = wl.batch_systems(64, seed=1)
+    specs = [(len(q), D, 1.0, 8.0 * (len(q) / 1e4) ** (1.0 / 3.0)) for x, q, D in sysl]
+    x = torch.tensor(np.concatenate([s[0] for s in sysl]), dtype=torch.float32, device=dev)
+    q = torch.tensor(np.concatenate([s[1] for s in sysl]), dtype=torch.float32, device=dev)
+    ntot = x.shape[0]
+    t0 = time.perf_counter()
+    b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, device=dev)
+    out = (torch.empty((ntot, 3), device=dev), torch.empty(ntot, device=dev),
+           torch.empty(len(specs), dtype=torch.float64, device=dev))
+    b.force(x, q, out=out)                          # autotune + capture
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    res = {}
+    for name, each in (("graph", False), ("per_system", True)):
+        for _ in range(3):
+            b.force(x, q, out=out, each=each)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record()
+            b.force(x, q, out=out, each=each)
+            e1.record()
+        torch.cuda.synchronize(dev)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        res[name] = {"ms_per_step": ms, "value": ntot / (ms * 1e-3), "unit": "particles/s"}
+    Ms = [b.system_info(i)["M"] for i in range(len(specs))]
+    Ps = [b.system_info(i)["P"] for i in range(len(specs))]
+    b.close()
+    res.update({"systems": len(specs), "particles": ntot, "M_range": [min(Ms), max(Ms)],
+                "P_range": [min(Ps), max(Ps)], "setup_s_incl_autotune": setup_s,
+                "speedup_graph_over_per_system": res["per_system"]["ms_per_step"] / res["graph"]["ms_per_step"]})
+    return res
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -265,9 +312,9 @@ def run_ours(a):
     if dom in ("spread", "gather"):
         flop = 2.0 * counts[dom] * N
         ach = flop / (stage_ms[dom] * 1e-3) / 1e12
-        roof = {"kernel": "k_gather<float,8,true>" if dom == "gather" else "k_spread<float,8>",
+        roof = {"kernel": "k_gather_flat<float,8,6,true>" if dom == "gather" else "k_spread_cl<float,8>",
                 "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
                 "per_launch": f"{flop:.3e} flop ({counts[dom]} FMA/particle x {N})",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:
@@ -309,6 +356,10 @@ def run_ours(a):
             "gpu_launches": int(round(launches_per_step * a.steps)),
             "gpu_launches_per_step": launches_per_step,
             "clocks": clk, "wall_s_timed_region": wall32}
+
+    # ---- batched independent systems: one CUDA graph vs one se_force per system ---
+    if not a.no_batch:
+        line["batch_form"] = run_batch(se, wl, dev, flush, min(a.steps, 50))
 
     # ---- CPU baseline and accuracy (rank 0, one GPU only) -------------------------
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -82,6 +82,13 @@ typedef struct {
     double aft_eps;  /* [<= 0] relative tolerance in Eqs. (estimate-s), (estimate-nl):
                         1e-5 for SE_F32 plans, 1e-10 for SE_F64 plans */
     int    tile;     /* [<= 0] edge of the gridding tile in grid cells (4, 8 or 16) */
+    int    spread_mode; /* [<= 0] gridding kernel: 1 shared-memory atomics, one CTA per tile;
+                           2 the same split over a thread-block cluster of `split` CTAs whose
+                           blocks are summed through distributed shared memory; 3 per-warp
+                           private blocks without atomics (bit-reproducible) */
+    int    gather_mode; /* [<= 0] gathering kernel: 1 tile block staged in shared memory,
+                           `split` CTAs per tile; 2 direct reads of the grid */
+    int    split;       /* [<= 0] CTAs per tile for spread_mode 2 / gather_mode 1 (1..8) */
 } se_opts;
 
 /* Derived parameters of a plan (read-only report). */
@@ -189,6 +196,51 @@ se_status se_plan_get_profile(se_plan_t plan, double *ms, int64_t *calls, int64_
 #define SE_NOALLOC_SCRATCH_BYTES (32u << 20)
 se_status se_potential_noalloc(se_plan_t plan, int64_t N, const void *x, const void *q, void *phi,
                                unsigned flags);
+
+/* Real-space part of the Ewald sum, Eq. (real_space_ewald): phi^R_m = sum over
+ * images p in P_D (the plan's periodicity) and sources n, excluding n = m at
+ * p = 0, of q_n erfc(xi r)/r for r = |x_m - x_n + p| < rc, with the plan's xi,
+ * box and precision; F^R_m = -q_m grad phi^R_m.  Together with se_force and
+ * SE_ADD_SELF this gives the full potential of Eq. (potential_split).  Cell
+ * list of edge >= rc (rc < L/2 in periodic directions).  phi [N] and F [N][3]
+ * (device; either may be NULL) are overwritten, or added to with
+ * SE_ACCUMULATE.  The workspace grows on demand.  Errors: SE_EINVAL, SE_ENOMEM,
+ * SE_ECUDA; with SE_SYNC_CHECK also the latched input errors. */
+#define SE_ACCUMULATE 16u
+se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q, double rc, void *phi, void *F,
+                        unsigned flags);
+
+/* ---- Batched evaluation of many independent systems ------------------------
+ * nsys systems, system i with N[i] particles in a cubic box of side L[i],
+ * periodic in its first D[i] directions, splitting parameter xi[i].  Each
+ * system's grid M_i (Eq. KP_kinf) and support P_i (the approximation-error
+ * estimate of Sec. 5.2 with the error-pollution rule, Sec. 6) are chosen for
+ * the absolute tolerance eps_rel * B_i, B_i = sqrt(Q_i) f_c(xi_i L_i) / L_i
+ * (Eq. fc-expression; Q = NULL takes Q_i = N_i / 3, the mean for charges
+ * uniform in [-1, 1]); M_i is then rounded up to an FFT-friendly size.  The
+ * window is w for all systems.  Unless SE_BATCH_NO_AUTOTUNE is given, the first
+ * se_batch_force call times the gridding tile (4, 8, 16) and kernel variants
+ * per system on the real inputs and keeps the fastest.  Every call replays one
+ * CUDA graph (captured on first use and whenever the pointers change) whose
+ * parallel branches run the systems concurrently.
+ * Arrays x [sum N][3], q [sum N], F [sum N][3], phi [sum N] (may be NULL) are
+ * concatenated in system order (device pointers); energy [nsys] (device, may be
+ * NULL) receives E_i = 1/2 sum q phi per system.  The first call synchronises
+ * (autotuning); later calls are asynchronous on the batch stream. */
+#define SE_BATCH_NO_AUTOTUNE 1u
+typedef struct se_batch_s *se_batch_t;
+se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int *D, const double *L,
+                          const double *xi, const double *Q, double eps_rel, se_window w, se_dtype dt,
+                          unsigned flags);
+se_status se_batch_destroy(se_batch_t batch);
+se_status se_batch_set_stream(se_batch_t batch, void *stream);
+se_status se_batch_force(se_batch_t batch, const void *x, const void *q, void *F, void *phi, double *energy);
+/* The same result with one plain se_force call per system on the batch stream
+ * (no graph): the per-system baseline the batched form is measured against. */
+se_status se_batch_force_each(se_batch_t batch, const void *x, const void *q, void *F, void *phi,
+                              double *energy);
+/* Derived parameters of system i. */
+se_status se_batch_get_system(se_batch_t batch, int i, se_plan_info_t *info);
 
 /* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
  * approximation-error estimates of Sec. 5.2, rounded up to even, with the

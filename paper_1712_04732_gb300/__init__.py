@@ -20,7 +20,7 @@ import torch
 from . import _native as nat
 from ._native import SEError
 
-__all__ = ["Plan", "SEError", "potential", "energy", "params_from_tolerance"]
+__all__ = ["Plan", "Batch", "SEError", "potential", "energy", "params_from_tolerance"]
 
 _WINDOWS = {"gaussian": nat.SE_WIN_GAUSSIAN, "pkb": nat.SE_WIN_PKB}
 _DTYPES = {torch.float32: nat.SE_F32, torch.float64: nat.SE_F64}
@@ -37,12 +37,12 @@ class Plan:
     parameter; M: grid intervals per periodic direction; P: window support;
     window: "pkb" or "gaussian"; dtype: torch.float32 or torch.float64.
     Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
-    shape, aft_eps, tile.
+    shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants).
     """
 
     def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
                  dtype=torch.float32, device=None, lam=None, s0=None, s_mt=None, n_l=None, nu=None,
-                 shape=None, aft_eps=None, tile=None):
+                 shape=None, aft_eps=None, tile=None, spread_mode=None, gather_mode=None, split=None):
         self._lib = nat.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if self.device.type != "cuda":
@@ -59,6 +59,9 @@ class Plan:
         if shape is not None: o.shape = shape
         if aft_eps is not None: o.aft_eps = aft_eps
         if tile is not None: o.tile = tile
+        if spread_mode is not None: o.spread_mode = spread_mode
+        if gather_mode is not None: o.gather_mode = gather_mode
+        if split is not None: o.split = split
         box = (ctypes.c_double * 3)(L, L, L)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -164,12 +167,95 @@ class Plan:
         nat.check(self._lib.se_vjp(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(g), _ptr(gx), _ptr(gq)))
         return gx, gq
 
+    def real_space(self, x, q, rc, phi=None, F=None, accumulate=False):
+        """Real-space part phi^R (and F^R) with cut-off rc (``se_real_space``)."""
+        x, q = self._args(x, q)
+        n = x.shape[0]
+        if phi is None and F is None:
+            phi = torch.empty(n, dtype=self.dtype, device=self.device)
+            F = torch.empty((n, 3), dtype=self.dtype, device=self.device)
+        nat.check(self._lib.se_real_space(self._h, n, _ptr(x), _ptr(q), float(rc), _ptr(phi), _ptr(F),
+                                          nat.SE_ACCUMULATE if accumulate else 0))
+        return phi, F
+
+    def total(self, x, q, rc):
+        """Full Ewald potential and force, Eq. (potential_split): Fourier part with
+        the self term (se_force) plus the real-space part (se_real_space)."""
+        F, phi, _ = self.force(x, q, add_self=True)
+        self.real_space(x, q, rc, phi, F, accumulate=True)
+        return phi, F
+
     def force_host(self, x, q, F, phi=None, energy=None, add_self=False):
         """``se_force`` with SE_HOST_IO on pinned host tensors (copies inside the call)."""
         self._sync_stream()
         flags = nat.SE_HOST_IO | (nat.SE_ADD_SELF if add_self else 0)
         nat.check(self._lib.se_force(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(F), _ptr(phi), _ptr(energy),
                                      flags))
+
+
+class Batch:
+    """Many independent systems evaluated together (``se_batch_create``): per-system
+    M and P from the rules of Sec. 6 for relative tolerance ``eps_rel``, autotuned
+    kernel variants and one CUDA graph per call.  ``systems`` is a list of
+    (N, D, L, xi) tuples; ``Q`` optional per-system sums of q^2."""
+
+    def __init__(self, systems, eps_rel=1e-5, window="pkb", dtype=torch.float32, device=None, Q=None,
+                 autotune=True):
+        self._lib = nat.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.dtype = dtype
+        n = len(systems)
+        self.N = [int(s[0]) for s in systems]
+        Na = (ctypes.c_int64 * n)(*self.N)
+        Da = (ctypes.c_int * n)(*[int(s[1]) for s in systems])
+        La = (ctypes.c_double * n)(*[float(s[2]) for s in systems])
+        Xa = (ctypes.c_double * n)(*[float(s[3]) for s in systems])
+        Qa = (ctypes.c_double * n)(*Q) if Q is not None else None
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(self._lib.se_batch_create(ctypes.byref(h), n, Na, Da, La, Xa, Qa, float(eps_rel),
+                                                _WINDOWS[window], _DTYPES[dtype],
+                                                0 if autotune else nat.SE_BATCH_NO_AUTOTUNE))
+        self._h = h
+        self._stream = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.se_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def system_info(self, i):
+        inf = nat.Info()
+        nat.check(self._lib.se_batch_get_system(self._h, i, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in nat.Info._fields_}
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            nat.check(self._lib.se_batch_set_stream(self._h, ctypes.c_void_p(s)))
+            self._stream = s
+
+    def force(self, x, q, out=None, each=False):
+        """(F, phi, E[nsys]) for the concatenated systems; ``each`` runs one plain
+        se_force per system instead of the batched graph."""
+        self._sync_stream()
+        x = x.contiguous()
+        q = q.contiguous()
+        n = x.shape[0]
+        if out is None:
+            out = (torch.empty((n, 3), dtype=self.dtype, device=self.device),
+                   torch.empty(n, dtype=self.dtype, device=self.device),
+                   torch.empty(len(self.N), dtype=torch.float64, device=self.device))
+        F, phi, E = out
+        fn = self._lib.se_batch_force_each if each else self._lib.se_batch_force
+        nat.check(fn(self._h, _ptr(x), _ptr(q), _ptr(F), _ptr(phi), _ptr(E)))
+        return F, phi, E
 
 
 class _PotentialFn(torch.autograd.Function):

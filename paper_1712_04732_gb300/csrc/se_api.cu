@@ -22,6 +22,7 @@ se_status fail(se_status s, const std::string &msg)
 
 se_status cuda_fail(cudaError_t e, const char *where)
 {
+    cudaGetLastError();                       // do not let a reported error leak into a later check
     return fail(SE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -165,6 +166,9 @@ void se_opts_default(se_opts *o)
     o->shape = 0.0;
     o->aft_eps = 0.0;
     o->tile = 0;
+    o->spread_mode = 0;
+    o->gather_mode = 0;
+    o->split = 0;
 }
 
 se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P, se_window w,
@@ -192,6 +196,13 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     p->h = p->L / M;
     p->inv_h = M / p->L;
     p->tile_pref = o.tile;
+    p->spread_mode = o.spread_mode;
+    p->gather_mode = o.gather_mode;
+    p->split = o.split;
+    if (o.spread_mode > 3 || o.gather_mode > 2 || o.split > 8) {
+        delete p;
+        return fail(SE_EINVAL, "spread_mode must be 0..3, gather_mode 0..2, split 0..8");
+    }
     if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
     // Sec. 6: shape parameters and PKB degree
     p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
@@ -293,6 +304,7 @@ se_status se_plan_check(se_plan_t p)
 
 static se_status check_call(se_plan_t p, int64_t N, const void *x, const void *q)
 {
+    cudaGetLastError();                       // clear pending (non-sticky) errors of earlier, unrelated calls
     if (!p) return fail(SE_EINVAL, "plan is NULL");
     if (N < 0) return fail(SE_EINVAL, "N < 0");
     if (N > 0 && (!x || !q)) return fail(SE_EINVAL, "x or q is NULL");

@@ -1,0 +1,314 @@
+// Batched evaluation of many independent systems (se_batch_*): per-system
+// parameters from the rules of Sec. 6, a timing autotuner over the gridding
+// tile and kernel variants, and one CUDA graph whose parallel branches run the
+// systems' pipelines concurrently.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "se_internal.h"
+
+namespace {
+
+constexpr int kBranches = 8;   // concurrent graph branches (streams during capture)
+
+// Smallest even M' >= M whose prime factors are 2, 3, 5 (sizes cuFFT handles best).
+int fft_friendly(int M)
+{
+    for (int m = M + (M & 1);; m += 2) {
+        int r = m;
+        for (int f : {2, 3, 5})
+            while (r % f == 0) r /= f;
+        if (r == 1) return m;
+    }
+}
+
+struct Variant {
+    int tile, spread_mode, split, gather_mode;
+};
+
+}  // namespace
+
+struct se_batch_s {
+    int nsys = 0;
+    se_dtype dtype = SE_F32;
+    std::vector<int64_t> N, off;
+    std::vector<se_plan_t> plans;
+    std::vector<Variant> chosen;
+    cudaStream_t stream = nullptr;          // caller's stream: graph launches and tuning runs
+    cudaStream_t cap = nullptr;             // internal stream the graph is captured from
+    cudaStream_t branch[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *key[5] = {};          // pointers the graph was captured with
+    bool tuned = false, autotune = true;
+    int64_t graph_launches = 0;
+    se_window window = SE_WIN_PKB;
+    std::vector<double> L, xi;
+    std::vector<int> D, M, P;
+};
+
+namespace {
+
+se_status make_plan(se_batch_s *b, int i, const double L, int D, double xi, int M, int P, se_window w,
+                    const Variant &v, se_plan_t *out)
+{
+    se_opts o;
+    se_opts_default(&o);
+    o.tile = v.tile;
+    o.spread_mode = v.spread_mode;
+    o.split = v.split;
+    o.gather_mode = v.gather_mode;
+    const double box[3] = {L, L, L};
+    se_status st = se_plan_create(out, box, D, xi, M, P, w, b->dtype, &o);
+    if (st != SE_OK) return st;
+    if ((st = se_plan_reserve(*out, b->N[i])) != SE_OK) return st;
+    return SE_OK;
+}
+
+size_t elem(const se_batch_s *b) { return b->dtype == SE_F32 ? 4 : 8; }
+
+se_status run_system(se_batch_s *b, int i, const void *x, const void *q, void *F, void *phi, double *energy,
+                     cudaStream_t s)
+{
+    se_status st = se_plan_set_stream(b->plans[i], s);
+    if (st != SE_OK) return st;
+    const size_t e = elem(b);
+    const char *xb = static_cast<const char *>(x) + 3 * e * b->off[i];
+    const char *qb = static_cast<const char *>(q) + e * b->off[i];
+    char *Fb = static_cast<char *>(F) + 3 * e * b->off[i];
+    char *pb = phi ? static_cast<char *>(phi) + e * b->off[i] : nullptr;
+    double *eb = energy ? energy + i : nullptr;
+    return se_force(b->plans[i], b->N[i], xb, qb, Fb, pb, eb, 0);
+}
+
+void release_graph(se_batch_s *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Autotuner: for every system time each candidate variant (median of a few
+// calls on the real inputs) and keep the fastest plan.
+se_status autotune(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy,
+                   const std::vector<double> &L, const std::vector<int> &D, const std::vector<double> &xi,
+                   const std::vector<int> &M, const std::vector<int> &P, se_window w)
+{
+    const Variant cand[] = {{8, 1, 1, 2}, {8, 2, 4, 2}, {4, 1, 1, 2}, {16, 1, 1, 2}, {8, 1, 1, 1}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int i = 0; i < b->nsys; ++i) {
+        float best = 1e30f;
+        for (const Variant &v : cand) {
+            se_plan_t p = nullptr;
+            if (make_plan(b, i, L[i], D[i], xi[i], M[i], P[i], w, v, &p) != SE_OK) {
+                se_plan_destroy(p);
+                continue;                                 // variant not available for this grid
+            }
+            se_plan_t keep = b->plans[i];
+            b->plans[i] = p;
+            float t[3];
+            se_status st = SE_OK;
+            for (int r = 0; r < 4 && st == SE_OK; ++r) {
+                cudaEventRecord(e0, b->stream);
+                st = run_system(b, i, x, q, F, phi, energy, b->stream);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+            }
+            b->plans[i] = keep;
+            if (st != SE_OK) {
+                se_plan_destroy(p);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best) {
+                best = t[1];
+                se_plan_destroy(b->plans[i]);
+                b->plans[i] = p;
+                b->chosen[i] = v;
+            } else {
+                se_plan_destroy(p);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned = true;
+    return SE_OK;
+}
+
+se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    release_graph(b);
+    // capture from an internal stream (the caller's may be the legacy stream,
+    // which cannot be captured); the graph is launched on the caller's stream
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return se::cuda_fail(e, "begin capture");
+    se_status st = SE_OK;
+    cudaEventRecord(b->fork, b->cap);
+    for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+    // systems dealt round-robin, largest first, onto the branches
+    std::vector<int> order(b->nsys);
+    for (int i = 0; i < b->nsys; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int u, int v) { return b->N[u] > b->N[v]; });
+    for (int r = 0; r < b->nsys && st == SE_OK; ++r) {
+        const int i = order[r];
+        st = run_system(b, i, x, q, F, phi, energy, b->branch[r % kBranches]);
+    }
+    for (int k = 0; k < kBranches; ++k) {
+        cudaEventRecord(b->join[k], b->branch[k]);
+        cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != SE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return se::cuda_fail(e, "end capture");
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return se::cuda_fail(e, "graph instantiate");
+    b->key[0] = x;
+    b->key[1] = q;
+    b->key[2] = F;
+    b->key[3] = phi;
+    b->key[4] = energy;
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int *D, const double *L,
+                          const double *xi, const double *Q, double eps_rel, se_window w, se_dtype dt,
+                          unsigned flags)
+{
+    if (!out) return se::fail(SE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nsys <= 0 || !N || !D || !L || !xi) return se::fail(SE_EINVAL, "nsys > 0 and N, D, L, xi are required");
+    if (!(eps_rel > 0) || eps_rel >= 1) return se::fail(SE_EINVAL, "eps_rel must lie in (0, 1)");
+    se_batch_s *b = new se_batch_s();
+    b->nsys = nsys;
+    b->dtype = dt;
+    b->autotune = !(flags & SE_BATCH_NO_AUTOTUNE);
+    b->N.assign(N, N + nsys);
+    b->off.resize(nsys + 1, 0);
+    for (int i = 0; i < nsys; ++i) {
+        if (N[i] <= 0) { delete b; return se::fail(SE_EINVAL, "every system needs N > 0"); }
+        b->off[i + 1] = b->off[i] + N[i];
+    }
+    b->plans.assign(nsys, nullptr);
+    b->chosen.assign(nsys, Variant{8, 0, 0, 0});
+    b->window = w;
+    b->L.assign(L, L + nsys);
+    b->xi.assign(xi, xi + nsys);
+    b->D.assign(D, D + nsys);
+    b->M.assign(nsys, 0);
+    b->P.assign(nsys, 0);
+    se_status st = SE_OK;
+    for (int i = 0; i < nsys && st == SE_OK; ++i) {
+        // Sec. 6: M from Eq. (KP_kinf) and P from the approximation error for eps = eps_rel * B
+        const double Qi = Q ? Q[i] : N[i] / 3.0;
+        const double xl = xi[i] * L[i];
+        const double B = std::sqrt(Qi) * std::exp(-12.62 / (xl * xl)) * (0.8909 + 0.01411 * xl + 4.315e-5 * xl * xl) / L[i];
+        int M = 0, P = 0;
+        st = se_params_from_tolerance(eps_rel * B, xi[i], L[i], Qi, w, &M, &P);
+        if (st != SE_OK) break;
+        P = std::min(std::max(P, 2), 16);
+        M = fft_friendly(std::max(M, P));
+        b->M[i] = M;
+        b->P[i] = P;
+        Variant v{8, 0, 0, 0};
+        st = make_plan(b, i, L[i], D[i], xi[i], M, P, w, v, &b->plans[i]);
+    }
+    if (st == SE_OK) {
+        cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        for (int k = 0; k < kBranches && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) st = se::cuda_fail(e, "batch streams");
+    }
+    if (st != SE_OK) {
+        se_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SE_OK;
+}
+
+se_status se_batch_destroy(se_batch_t b)
+{
+    if (!b) return SE_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+    release_graph(b);
+    for (se_plan_t p : b->plans) se_plan_destroy(p);
+    for (int k = 0; k < kBranches; ++k) {
+        if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return SE_OK;
+}
+
+se_status se_batch_set_stream(se_batch_t b, void *stream)
+{
+    if (!b) return se::fail(SE_EINVAL, "batch is NULL");
+    if (static_cast<cudaStream_t>(stream) != b->stream) release_graph(b);
+    b->stream = static_cast<cudaStream_t>(stream);
+    return SE_OK;
+}
+
+se_status se_batch_force(se_batch_t b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    if (!b) return se::fail(SE_EINVAL, "batch is NULL");
+    cudaGetLastError();                       // pending errors of earlier, unrelated calls
+    if (!x || !q || !F) return se::fail(SE_EINVAL, "x, q and F are required");
+    se_status st;
+    if (b->autotune && !b->tuned) {
+        release_graph(b);
+        // tuning needs the real inputs; it runs each system eagerly a few times
+        if ((st = autotune(b, x, q, F, phi, energy, b->L, b->D, b->xi, b->M, b->P, b->window)) != SE_OK) return st;
+    }
+    const void *k[5] = {x, q, F, phi, energy};
+    bool same = b->exec != nullptr;
+    for (int i = 0; i < 5; ++i) same = same && k[i] == b->key[i];
+    if (!same && (st = capture(b, x, q, F, phi, energy)) != SE_OK) return st;
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return se::cuda_fail(e, "graph launch");
+    ++b->graph_launches;
+    return SE_OK;
+}
+
+se_status se_batch_force_each(se_batch_t b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    if (!b) return se::fail(SE_EINVAL, "batch is NULL");
+    if (!x || !q || !F) return se::fail(SE_EINVAL, "x, q and F are required");
+    for (int i = 0; i < b->nsys; ++i) {
+        se_status st = run_system(b, i, x, q, F, phi, energy, b->stream);
+        if (st != SE_OK) return st;
+    }
+    return SE_OK;
+}
+
+se_status se_batch_get_system(se_batch_t b, int i, se_plan_info_t *info)
+{
+    if (!b || !info || i < 0 || i >= b->nsys) return se::fail(SE_EINVAL, "bad batch, index or info");
+    return se_plan_get_info(b->plans[i], info);
+}
+
+}  // extern "C"

@@ -14,6 +14,7 @@ namespace se {
 constexpr int kMaxP = 16;       // largest window support compiled in
 constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
+constexpr int kMergeJ = 6;      // most tiles per axis whose blocks overlap one grid point
 
 // Window description passed by value to the tile kernels.  For the PKB the
 // coefficient c[j][k] multiplies xbar^j at stencil point k (k = 0..P-1 counted
@@ -36,7 +37,9 @@ struct TileGeom {
     int T[3];      // tile edge
     int nt[3];     // tiles per axis
     int B[3];      // extended block edge T + P - 1
-    int blk;       // B0 * B1 * B2
+    int blk;       // B0 * B1 * B2 (compact block, the layout in global scratch)
+    int pitch;     // row pitch of a block in shared memory (>= B0, chosen against bank conflicts)
+    int sblk;      // pitch * B1 * B2 (shared-memory block)
 };
 
 // Grid accessor: element (i, j, k) of a real grid lives at
@@ -47,7 +50,7 @@ struct GridView {
 
 struct Particles {   // sorted-by-tile particle records
     void *frac_q;    // float4 / double4: fractional grid coordinate per axis, charge
-    int2 *idx_code;  // original index, packed local anchor (8 bits per axis)
+    int4 *idx_anc;   // original index, lowest support index per axis (the anchor)
 };
 
 // Per-axis scaling factors of one spectral box: sigma = norm * f0 f1 f2 / (k0 + k1 + k2)
@@ -74,6 +77,8 @@ struct se_plan_s {
     std::vector<double> coef, dcoef;     // PKB coefficients in stencil order (FP64 master copy)
     int dev = 0;
     int tile_pref = 0;
+    int spread_warps = 8;                // warps (private blocks) per gridding CTA (spread_mode 3)
+    int spread_mode = 0, gather_mode = 0, split = 0;   // kernel variants (0: chosen per call)
     cudaStream_t stream = nullptr;
 
     // ---- device memory ----
@@ -83,6 +88,7 @@ struct se_plan_s {
     se::GridView gin{}, gout{};
     size_t grid_in_elems = 0, grid_out_elems = 0;
     void *spec = nullptr;                // complex spectrum of the main transform
+    void *spec_pad = nullptr;            // D = 0: 2D spectra of the non-zero z-planes (z-padded with zeros)
     size_t spec_elems = 0;
     void *U = nullptr;                   // D = 1, 2: padded lines / planes of the set I
     size_t U_elems = 0;
@@ -100,9 +106,11 @@ struct se_plan_s {
     size_t scratch_bytes = 0;
     int *tile_cnt = nullptr;             // n_tiles + 1
     int *tile_off = nullptr;             // n_tiles + 1
-    double *tile_part = nullptr;         // per-tile FP64 partial sums (energy, neutrality)
+    double *tile_part = nullptr;         // per-tile / per-CTA FP64 partial sums (energy, neutrality)
+    size_t tile_part_elems = 0;
     double *red = nullptr;               // small FP64 reduction outputs
     int *err = nullptr;                  // latched device-side input errors
+    int *counters = nullptr;             // completion counters of the last-CTA reductions (zero between calls)
     // particle workspace
     int64_t cap = 0;
     int2 *tile_rank = nullptr;           // (tile, rank) per input particle
@@ -113,7 +121,7 @@ struct se_plan_s {
     void *grid_in2 = nullptr, *grid_out2 = nullptr;
     // FFT plans
     cufftHandle fwd = 0, inv = 0;        // main real <-> complex transform
-    cufftHandle free_main = 0;           // D = 1, 2: in-place free-direction transform of spec
+    cufftHandle free_main = 0;           // D = 1, 2: in-place free-direction transform of spec; D = 0: z-transform
     cufftHandle free_I = 0, free_Z = 0;  // D = 1, 2: transforms of U and Z
     bool have_fwd = false, have_inv = false, have_free_main = false, have_free_I = false, have_free_Z = false;
     int64_t device_bytes = 0;
@@ -123,6 +131,7 @@ struct se_plan_s {
     double prof_ms[SE_N_STAGES] = {};
     int64_t prof_calls = 0;
     int64_t launches = 0;
+    void *real_ws = nullptr;             // workspace of the real-space sum (se_real.cu)
 };
 
 namespace se {
@@ -149,6 +158,7 @@ se_status plan_io_reserve(se_plan_s *p, int64_t n);
 se_status plan_second_grid(se_plan_s *p);
 se_status plan_set_fft_stream(se_plan_s *p);
 void plan_release(se_plan_s *p);
+void real_release(se_plan_s *p);         // se_real.cu
 
 // per-precision launchers (se_kern_f32.cu / se_kern_f64.cu)
 template <typename T>

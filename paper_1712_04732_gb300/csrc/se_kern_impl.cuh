@@ -82,20 +82,24 @@ static WindowArgs<T> window_args(const se_plan_s *p)
     return w;
 }
 
-// Dynamic shared memory: the extended block(s) plus per-warp window values
-// (at most 32 lanes x 3 values, or x 6 with derivatives).
+static inline size_t al32(size_t n) { return (n + 31) & ~size_t(31); }
+
+// Dynamic shared memory of the gridding kernel: one private block per warp,
+// the PKB coefficients and per-warp window values.
 template <typename T>
 static size_t spread_smem(const se_plan_s *p)
 {
-    const int nw = kThreads / 32;
-    return (al16(p->tg.blk) + size_t(nw) * 32 * 3) * sizeof(T);
+    const int nw = p->spread_warps;
+    return (size_t(nw) * al32(p->tg.sblk) + al32((kMaxNu + 1) * p->P) + size_t(nw) * 3 * p->P) * sizeof(T);
 }
 
+// ... of the staged gathering kernels: the staged block(s) plus per-warp
+// window values (at most 32 lanes x 6 values).
 template <typename T>
 static size_t gather_smem(const se_plan_s *p, int nblocks)
 {
     const int nw = kThreads / 32;
-    return (nblocks * al16(p->tg.blk) + size_t(nw) * 32 * 6) * sizeof(T);
+    return (nblocks * al32(p->tg.sblk) + size_t(nw) * 32 * 6) * sizeof(T);
 }
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory; the attribute is
@@ -121,43 +125,104 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     cudaError_t e = cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * (nt + 1), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
     BinArgs<T> a = bin_args<T>(p);
-    k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err);
+    k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
+                                                               p->tile_off, p->counters);
     SE_LAUNCH_CHECK("bin_count");
-    k_scan<<<1, 1024, 0, p->stream>>>(nt, p->tile_cnt, p->tile_off);
-    SE_LAUNCH_CHECK("scan");
     k_bin_scatter<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(
         a, N, x, q, p->tile_off, p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
-        p->prt.idx_code);
+        p->prt.idx_anc);
     SE_LAUNCH_CHECK("bin_scatter");
     prof_mark(p, 1);
+    return SE_OK;
+}
+
+#define SE_DISPATCH_P_ONLY(PV, ...)                                             \
+    switch (PV) {                                                               \
+    case 2: { constexpr int PP = 2; __VA_ARGS__; } break;                       \
+    case 4: { constexpr int PP = 4; __VA_ARGS__; } break;                       \
+    case 6: { constexpr int PP = 6; __VA_ARGS__; } break;                       \
+    case 8: { constexpr int PP = 8; __VA_ARGS__; } break;                       \
+    case 10: { constexpr int PP = 10; __VA_ARGS__; } break;                     \
+    case 12: { constexpr int PP = 12; __VA_ARGS__; } break;                     \
+    case 14: { constexpr int PP = 14; __VA_ARGS__; } break;                     \
+    case 16: { constexpr int PP = 16; __VA_ARGS__; } break;                     \
+    default: return fail(SE_EINVAL, "window support P not compiled in");        \
+    }
+
+// CTAs per tile when a tile's particles are split (spread_mode 2, staged
+// gathering): 4 unless the tiles hold fewer than 4 particles on average
+// (measured on GB300 with one warp per particle: 4 was best or within 7 % of
+// best for 20 000 to 1.2e6 particles).
+static int split_for(const se_plan_s *p, int64_t N)
+{
+    if (p->split > 0) return p->split;
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    return N >= int64_t(4) * nt ? 4 : 1;
+}
+
+// Gridding (per-tile blocks into `scratch`) followed by the block merge into dst.
+template <typename T>
+static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, void *scratch)
+{
+    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    const int mode = p->spread_mode > 0 ? p->spread_mode : 2;   // 2 with split 1 is mode 1
+    if (mode == 3) {
+        const size_t sm = spread_smem<T>(p);
+        SE_DISPATCH_P_ONLY(p->P, {
+            auto kern = k_spread<T, PP>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+            kern<<<nt, 32 * p->spread_warps, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_anc, g, wa,
+                                                              reinterpret_cast<T *>(scratch));
+        });
+    } else {
+        const int CL = mode == 1 ? 1 : split_for(p, N);
+        const size_t sm = (al32(p->tg.sblk) + al32((kMaxNu + 1) * p->P) + size_t(kThreads / 32) * 3 * p->P) *
+                          sizeof(T);
+        SE_DISPATCH_P_ONLY(p->P, {
+            auto kern = k_spread_cl<T, PP>;
+            cudaError_t e = allow_smem(kern, sm);
+            if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(unsigned(nt * CL));
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = p->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = unsigned(CL);
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, kern, p->tg, (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g,
+                                   wa, reinterpret_cast<T *>(scratch));
+            if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+        });
+    }
+    SE_LAUNCH_CHECK("spread");
+    prof_mark(p, 2);
+    const int t01 = p->tg.T[0] * p->tg.T[1];
+    dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
+    bool two = true;                                  // at most two tiles overlap a point per axis
+    for (int a = 0; a < 3; ++a) two = two && (p->tg.B[a] - 1) / p->tg.T[a] + 1 <= 2;
+    if (two)
+        k_merge<T, 2><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
+                                                reinterpret_cast<T *>(dst), p->gin);
+    else
+        k_merge<T, kMergeJ><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
+                                                      reinterpret_cast<T *>(dst), p->gin);
+    SE_LAUNCH_CHECK("merge");
+    prof_mark(p, 3);
     return SE_OK;
 }
 
 template <typename T>
 se_status Ops<T>::spread(se_plan_s *p, int64_t N, const T *g, void *dst)
 {
-    (void)N;
-    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
-    const size_t sm = spread_smem<T>(p);
-    WindowArgs<T> wa = window_args<T>(p);
-    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
-    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
-    SE_DISPATCH_P(p->P, nu, {
-        auto kern = k_spread<T, PP, NN>;
-        cudaError_t e = allow_smem(kern, sm);
-        if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
-        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, g, wa,
-                                              reinterpret_cast<T *>(p->scratch));
-    });
-    SE_LAUNCH_CHECK("spread");
-    prof_mark(p, 2);
-    const int t01 = p->tg.T[0] * p->tg.T[1];
-    dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
-    k_merge<T><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(p->scratch),
-                                         reinterpret_cast<T *>(dst), p->gin);
-    SE_LAUNCH_CHECK("merge");
-    prof_mark(p, 3);
-    return SE_OK;
+    return spread_impl<T>(p, N, g, dst, p->scratch);
 }
 
 // cuFFT wrappers per precision
@@ -167,6 +232,8 @@ static inline cufftResult fft_c2r(cufftHandle h, cufftComplex *in, float *out) {
 static inline cufftResult fft_c2r(cufftHandle h, cufftDoubleComplex *in, double *out) { return cufftExecZ2D(h, in, out); }
 static inline cufftResult fft_c2c(cufftHandle h, cufftComplex *d, int dir) { return cufftExecC2C(h, d, d, dir); }
 static inline cufftResult fft_c2c(cufftHandle h, cufftDoubleComplex *d, int dir) { return cufftExecZ2Z(h, d, d, dir); }
+static inline cufftResult fft_c2c_oop(cufftHandle h, cufftComplex *i, cufftComplex *o, int dir) { return cufftExecC2C(h, i, o, dir); }
+static inline cufftResult fft_c2c_oop(cufftHandle h, cufftDoubleComplex *i, cufftDoubleComplex *o, int dir) { return cufftExecZ2Z(h, i, o, dir); }
 
 template <typename T> static const ScaleBox<T> &sb_spec(const se_plan_s *p);
 template <> const ScaleBox<float> &sb_spec<float>(const se_plan_s *p) { return p->sb_spec_f; }
@@ -180,17 +247,30 @@ se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
 {
     using C = typename Cplx<T>::type;
     C *spec = reinterpret_cast<C *>(p->spec);
-    cufftResult r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec);
+    cufftResult r;
+    if (p->D == 0) {
+        // forward: 2D R2C of the M~ non-zero z-planes into the zero-padded buffer,
+        // z-transform into spec; scaling; inverse z-transform in place, 2D C2R of
+        // the M~ z-planes that are read back
+        C *pad = reinterpret_cast<C *>(p->spec_pad);
+        if ((r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), pad)) != CUFFT_SUCCESS) return cufft_fail(r, "forward xy");
+        if ((r = fft_c2c_oop(p->free_main, pad, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "forward z");
+        prof_mark(p, 4);
+        k_scale_tab<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(
+            int64_t(p->spec_elems), reinterpret_cast<const T *>(p->sigma_tab), spec);
+        SE_LAUNCH_CHECK("scale");
+        prof_mark(p, 5);
+        if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse z");
+        if ((r = fft_c2r(p->inv, spec, reinterpret_cast<T *>(gout))) != CUFFT_SUCCESS) return cufft_fail(r, "inverse xy");
+        prof_mark(p, 6);
+        return SE_OK;
+    }
+    r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec);
     if (r != CUFFT_SUCCESS) return cufft_fail(r, "forward transform");
-    if (p->D == 3 || p->D == 0) prof_mark(p, 4);
+    if (p->D == 3) prof_mark(p, 4);
     if (p->D == 3) {
         const ScaleBox<T> &sb = sb_spec<T>(p);
         k_scale_box<T><<<blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256), 256, 0, p->stream>>>(sb, spec);
-        SE_LAUNCH_CHECK("scale");
-        prof_mark(p, 5);
-    } else if (p->D == 0) {
-        k_scale_tab<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(
-            int64_t(p->spec_elems), reinterpret_cast<const T *>(p->sigma_tab), spec);
         SE_LAUNCH_CHECK("scale");
         prof_mark(p, 5);
     } else {
@@ -250,37 +330,56 @@ template <typename T>
 se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, double *energy, bool add_self,
                          bool grad)
 {
-    (void)N;
     (void)q;
     const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
-    const size_t sm = gather_smem<T>(p, 1);
     WindowArgs<T> wa = window_args<T>(p);
     const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
     const T self = add_self ? T(-2.0 * p->xi / std::sqrt(M_PI)) : T(0);
     double *part = energy ? p->tile_part : nullptr;
     const T *grid = reinterpret_cast<const T *>(p->grid_out);
     const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
-    SE_DISPATCH_P(p->P, nu, {
-        if (grad) {
-            auto kern = k_gather<T, PP, NN, true>;
-            cudaError_t e = allow_smem(kern, sm);
-            if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
-            kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi, F,
-                                                  part, T(p->inv_h), self);
-        } else {
-            auto kern = k_gather<T, PP, NN, false>;
-            cudaError_t e = allow_smem(kern, sm);
-            if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
-            kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa, grid, p->gout, phi,
-                                                  nullptr, part, T(p->inv_h), self);
-        }
-    });
-    SE_LAUNCH_CHECK("gather");
-    prof_mark(p, 7);
-    if (energy) {
-        k_sum_fixed<<<1, 256, 0, p->stream>>>(nt, p->tile_part, energy);
-        SE_LAUNCH_CHECK("energy");
+    // sparsely filled tiles: read the grid directly; otherwise stage each tile's block
+    const bool flat = p->gather_mode != 1;
+    const int split = flat ? 1 : split_for(p, N);
+    int nparts = nt * split;
+    if (flat) {
+        SE_DISPATCH_P(p->P, nu, {
+            constexpr int G = LaneMap<PP>::G;
+            const int64_t per_cta = int64_t(kThreads / 32) * G;
+            const unsigned nb = unsigned((N + per_cta - 1) / per_cta);
+            nparts = int(nb);
+            if (grad)
+                k_gather_flat<T, PP, NN, true><<<nb, kThreads, 0, p->stream>>>(
+                    N, p->tg, fq, p->prt.idx_anc, wa, grid, p->gout, phi, F, part, energy, p->counters + 1,
+                    T(p->inv_h), self);
+            else
+                k_gather_flat<T, PP, NN, false><<<nb, kThreads, 0, p->stream>>>(
+                    N, p->tg, fq, p->prt.idx_anc, wa, grid, p->gout, phi, nullptr, part, energy, p->counters + 1,
+                    T(p->inv_h), self);
+        });
+    } else {
+        const size_t sm = gather_smem<T>(p, 1);
+        SE_DISPATCH_P(p->P, nu, {
+            if (grad) {
+                auto kern = k_gather<T, PP, NN, true>;
+                cudaError_t e = allow_smem(kern, sm);
+                if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                kern<<<nt * split, kThreads, sm, p->stream>>>(p->tg, split, p->tile_off, fq, p->prt.idx_anc, wa, grid,
+                                                              p->gout, phi, F, part, energy, p->counters + 1,
+                                                              T(p->inv_h), self);
+            } else {
+                auto kern = k_gather<T, PP, NN, false>;
+                cudaError_t e = allow_smem(kern, sm);
+                if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                kern<<<nt * split, kThreads, sm, p->stream>>>(p->tg, split, p->tile_off, fq, p->prt.idx_anc, wa, grid,
+                                                              p->gout, phi, nullptr, part, energy, p->counters + 1,
+                                                              T(p->inv_h), self);
+            }
+        });
     }
+    SE_LAUNCH_CHECK("gather");
+    (void)nparts;
+    prof_mark(p, 7);
     prof_mark(p, 8);
     return SE_OK;
 }
@@ -300,7 +399,7 @@ se_status Ops<T>::gather_vjp(se_plan_s *p, int64_t N, const T *q, const T *g, co
         auto kern = k_gather_vjp<T, PP, NN>;
         cudaError_t e = allow_smem(kern, sm);
         if (e != cudaSuccess) return cuda_fail(e, "vjp smem attribute");
-        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, wa,
+        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_anc, wa,
                                               reinterpret_cast<const T *>(grid_q), reinterpret_cast<const T *>(grid_g),
                                               p->gout, g, gx, gq, T(p->inv_h));
     });
@@ -325,25 +424,7 @@ se_status Ops<T>::charge_sums(se_plan_s *p, int64_t N, const T *q)
 template <typename T>
 se_status Ops<T>::spread_with_scratch(se_plan_s *p, void *dst, void *scratch)
 {
-    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
-    const size_t sm = spread_smem<T>(p);
-    WindowArgs<T> wa = window_args<T>(p);
-    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
-    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
-    SE_DISPATCH_P(p->P, nu, {
-        auto kern = k_spread<T, PP, NN>;
-        cudaError_t e = allow_smem(kern, sm);
-        if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
-        kern<<<nt, kThreads, sm, p->stream>>>(p->tg, p->tile_off, fq, p->prt.idx_code, nullptr, wa,
-                                              reinterpret_cast<T *>(scratch));
-    });
-    SE_LAUNCH_CHECK("spread");
-    const int t01 = p->tg.T[0] * p->tg.T[1];
-    dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
-    k_merge<T><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
-                                         reinterpret_cast<T *>(dst), p->gin);
-    SE_LAUNCH_CHECK("merge");
-    return SE_OK;
+    return spread_impl<T>(p, p->cap, nullptr, dst, scratch);
 }
 
 template struct Ops<T_INST>;

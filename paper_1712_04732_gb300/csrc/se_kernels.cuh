@@ -3,6 +3,8 @@
 // window support P.  Included by se_kern_f32.cu and se_kern_f64.cu only.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "se_internal.h"
 
 namespace se {
@@ -68,52 +70,65 @@ __device__ __forceinline__ bool locate(const BinArgs<T> &a, const T *xp, T &qv, 
     return ok;
 }
 
-template <typename T>
-__global__ void k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
-                            int *__restrict__ cnt, int2 *__restrict__ tile_rank, int *err)
+// Exclusive prefix sum of n counts by one CTA (off[n] receives the total).
+__device__ __forceinline__ void block_scan(int n, const int *cnt, int *off, int *part, int *carry)
 {
-    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= N) return;
-    T xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-    T qv = q[i];
-    int anc[3];
-    T frac[3];
-    locate(a, xp, qv, anc, frac, err);
-    int tile = ((anc[2] / a.T[2]) * a.nt[1] + anc[1] / a.T[1]) * a.nt[0] + anc[0] / a.T[0];
-    int r = atomicAdd(&cnt[tile], 1);
-    tile_rank[i] = make_int2(tile, r);
-}
-
-// Exclusive prefix sum of the tile counts (one CTA; n_tiles is small).
-static __global__ void k_scan(int n, const int *__restrict__ cnt, int *__restrict__ off)
-{
-    __shared__ int part[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    if (threadIdx.x == 0) *carry = 0;
     __syncthreads();
     for (int base = 0; base < n; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = (i < n) ? cnt[i] : 0;
+        const int i = base + threadIdx.x;
+        const int v = (i < n) ? __ldcg(cnt + i) : 0;
         part[threadIdx.x] = v;
         __syncthreads();
         for (int s = 1; s < blockDim.x; s <<= 1) {
-            int t = (threadIdx.x >= s) ? part[threadIdx.x - s] : 0;
+            const int t = (threadIdx.x >= s) ? part[threadIdx.x - s] : 0;
             __syncthreads();
             part[threadIdx.x] += t;
             __syncthreads();
         }
-        if (i < n) off[i] = carry + part[threadIdx.x] - v;
+        if (i < n) off[i] = *carry + part[threadIdx.x] - v;
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+        if (threadIdx.x == blockDim.x - 1) *carry += part[threadIdx.x];
         __syncthreads();
     }
-    if (threadIdx.x == 0) off[n] = carry;
+    if (threadIdx.x == 0) off[n] = *carry;
+}
+
+// Tile of every particle (counting pass of the counting sort) and, in the CTA
+// that finishes last, the exclusive scan of the tile counts into tile offsets.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q, int *__restrict__ cnt,
+            int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done)
+{
+    __shared__ int part[256];
+    __shared__ int carry;
+    __shared__ bool last;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i < N) {
+        T xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        T qv = q[i];
+        int anc[3];
+        T frac[3];
+        locate(a, xp, qv, anc, frac, err);
+        const int tile = ((anc[2] / a.T[2]) * a.nt[1] + anc[1] / a.T[1]) * a.nt[0] + anc[0] / a.T[0];
+        const int r = atomicAdd(&cnt[tile], 1);
+        tile_rank[i] = make_int2(tile, r);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    block_scan(ntiles, cnt, off, part, &carry);
+    if (threadIdx.x == 0) *done = 0;
 }
 
 template <typename T>
 __global__ void k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
                               const int *__restrict__ off, const int2 *__restrict__ tile_rank,
-                              typename Vec4<T>::type *__restrict__ fq, int2 *__restrict__ ic)
+                              typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia)
 {
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= N) return;
@@ -127,16 +142,14 @@ __global__ void k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, 
     typename Vec4<T>::type r;
     r.x = frac[0]; r.y = frac[1]; r.z = frac[2]; r.w = qv;
     fq[pos] = r;
-    int code = (anc[0] % a.T[0]) | ((anc[1] % a.T[1]) << 8) | ((anc[2] % a.T[2]) << 16);
-    ic[pos] = make_int2(int(i), code);
+    ia[pos] = make_int4(int(i), anc[0], anc[1], anc[2]);
 }
 
 // ----------------------------------------------------------------- window
-// Lane layout of the tile kernels: a warp works on G = 32 / P particles at a
-// time; lane l serves particle l / P at stencil offset dx = l mod P (lanes past
-// G P idle).  Each lane evaluates the window at its own offset k = dx along all
-// three axes, so its PKB coefficients c[j][k] live in registers for the whole
-// kernel.
+// Lane layout of the gathering kernels: a warp works on G = 32 / P particles
+// at a time; lane l serves particle l / P at stencil offset dx = l mod P (lanes
+// past G P idle).  Each lane evaluates the window at its own offset k = dx
+// along all three axes, so its PKB coefficients c[j][k] live in registers.
 template <int P>
 struct LaneMap {
     static constexpr int G = 32 / P;
@@ -187,10 +200,25 @@ __device__ __forceinline__ void win_eval(int kind, T alpha, const LaneCoef<T, NU
     }
 }
 
+// The same window value with the coefficients read from shared memory
+// (sc[j P + k], j = 0..nu): used where a lane's stencil offset varies.
+template <typename T, int P>
+__device__ __forceinline__ T win_val_smem(int kind, int nu, T alpha, const T *sc, T frac, int k)
+{
+    if (kind == SE_WIN_PKB) {
+        const T xb = T(2) * frac - T(1);
+        T v = sc[nu * P + k];
+        for (int j = nu - 1; j >= 0; --j) v = fma(v, xb, sc[j * P + k]);
+        return v;
+    }
+    const T u = T(2) * (frac + T(P / 2 - 1 - k)) / T(P);
+    return dexp(-alpha * u * u);
+}
+
 template <typename T>
 __device__ __forceinline__ size_t align_up_elems(size_t n)
 {
-    return (n + 15) & ~size_t(15);
+    return (n + 31) & ~size_t(31);
 }
 
 // Sum over the P lanes of one particle group; the total lands on offset 0.
@@ -205,117 +233,257 @@ __device__ __forceinline__ T group_sum(T v, int dx)
     return v;
 }
 
-__device__ __forceinline__ int block_base(const TileGeom &tg, int code)
+__device__ __forceinline__ void tile_origin(const TileGeom &tg, int tile, int o[3])
 {
-    return ((code >> 16) * tg.B[1] + ((code >> 8) & 255)) * tg.B[0] + (code & 255);
+    o[0] = (tile % tg.nt[0]) * tg.T[0];
+    o[1] = ((tile / tg.nt[0]) % tg.nt[1]) * tg.T[1];
+    o[2] = (tile / (tg.nt[0] * tg.nt[1])) * tg.T[2];
+}
+
+// Offset of a particle's lowest support point inside its tile's shared-memory block.
+__device__ __forceinline__ int block_base(const TileGeom &tg, const int o[3], int4 a)
+{
+    return ((a.w - o[2]) * tg.B[1] + (a.z - o[1])) * tg.pitch + (a.y - o[0]);
 }
 
 // ----------------------------------------------------------------- gridding
-// Eq. (gridding) for the particles of one tile: one CTA per tile, the tile's
-// extended block (T + P - 1)^3 accumulated in shared memory, then written to
-// the tile's slot in `scratch`.  Lane (particle g, offset dx) adds
-// q W_x(dx) W_z(dz) W_y(dy) to the row (dy, dz) point dx for every dy, dz.
-// When g != nullptr the charges are taken from g (original particle order)
-// instead of the sorted records (the second gridding of the adjoint).
-template <typename T, int P, int NU>
+// Eq. (gridding) for the particles of one tile: one CTA per tile.  Every warp
+// owns a private copy of the tile's extended block (T + P - 1)^3 in shared
+// memory and adds its particles to it one at a time with plain read-modify-
+// write: the lanes cover distinct (x, y) points of the stencil plane and walk
+// z, so no two lanes touch the same word and no atomics are needed.  The
+// copies are then summed in warp order into the tile's slot of `scratch`
+// (compact layout).  With the particle order fixed, the result is
+// bit-reproducible.  When g != nullptr the charges are taken from g (original
+// particle order; the second gridding of the adjoint).
+template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
 k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
-         const int2 *__restrict__ ic, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
+         const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
 {
-    constexpr int G = LaneMap<P>::G;
+    constexpr int NE = (P * P + 31) / 32;
     const int tile = blockIdx.x;
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *blk = reinterpret_cast<T *>(smraw);
-    const int nblk = tg.blk;
-    T *wb = blk + align_up_elems<T>(nblk);          // [warp][G][3][P]
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) blk[i] = T(0);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int grp = lane / P, dx = lane - grp * P;
-    const bool lane_on = grp < G;
-    LaneCoef<T, NU> cf;
-    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
-    T *w = wb + (warp * G + (lane_on ? grp : 0)) * 3 * P;
-    const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sblk = int(align_up_elems<T>(tg.sblk));
+    T *blocks = reinterpret_cast<T *>(smraw);
+    T *sc = blocks + size_t(nw) * sblk;                       // PKB coefficients
+    const int ncoef = (wa.nu + 1) * P;
+    T *wb = sc + align_up_elems<T>(ncoef);                    // [warp][3P] window values
+    for (int i = threadIdx.x; i < nw * sblk; i += blockDim.x) blocks[i] = T(0);
+    if (wa.kind == SE_WIN_PKB)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
+    int o[3];
+    tile_origin(tg, tile, o);
+    T *blk = blocks + size_t(warp) * sblk;
+    T *w = wb + warp * 3 * P;
+    const int pitch = tg.pitch, plane = tg.B[1] * tg.pitch;
+    int poff[NE];
+    bool pv[NE];
+    int pdx[NE], pdy[NE];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        const int pp = lane + 32 * e;
+        pv[e] = pp < P * P;
+        pdx[e] = pv[e] ? pp % P : 0;
+        pdy[e] = pv[e] ? pp / P : 0;
+        poff[e] = pdy[e] * pitch + pdx[e];
+    }
     __syncthreads();
 
-    for (int p0 = beg + warp * G; p0 < end; p0 += nw * G) {
-        const int p = p0 + grp;
-        const bool has = lane_on && p < end;
-        typename Vec4<T>::type r;
-        int2 c = make_int2(0, 0);
-        T qv = T(0);
-        if (has) {
-            r = fq[p];
-            c = ic[p];
-            qv = g ? g[c.x] : r.w;
-            T w0, w1, w2, dd;
-            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.x, dx, w0, dd);
-            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.y, dx, w1, dd);
-            win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf, r.z, dx, w2, dd);
-            w[dx] = w0;
-            w[P + dx] = w1;
-            w[2 * P + dx] = w2;
+    for (int p = beg + warp; p < end; p += nw) {
+        const typename Vec4<T>::type r = fq[p];
+        const int4 a = ia[p];
+        const T qv = g ? g[a.x] : r.w;
+        for (int j = lane; j < 3 * P; j += 32) {
+            const int ax = j / P, k = j - ax * P;
+            w[j] = win_val_smem<T, P>(wa.kind, wa.nu, wa.alpha, sc, ax == 0 ? r.x : (ax == 1 ? r.y : r.z), k);
         }
         __syncwarp();
-        if (has) {
-            T wy[P];
+        T wxy[NE];
 #pragma unroll
-            for (int j = 0; j < P; ++j) wy[j] = w[P + j];
-            const T wxq = qv * w[dx];
-            T *col = blk + block_base(tg, c.y) + dx;
+        for (int e = 0; e < NE; ++e) wxy[e] = qv * w[pdx[e]] * w[P + pdy[e]];
+        T *base = blk + block_base(tg, o, a);
 #pragma unroll
-            for (int dz = 0; dz < P; ++dz) {
-                const T t = wxq * w[2 * P + dz];
-                T *row = col + dz * BXY;
+        for (int dz = 0; dz < P; ++dz) {
+            const T wz = w[2 * P + dz];
+            T *row = base + dz * plane;
 #pragma unroll
-                for (int dy = 0; dy < P; ++dy) atomicAdd(row + dy * BX, t * wy[dy]);
-            }
+            for (int e = 0; e < NE; ++e)
+                if (pv[e]) row[poff[e]] = fma(wxy[e], wz, row[poff[e]]);
         }
         __syncwarp();
     }
     __syncthreads();
-    T *dst = scratch + size_t(tile) * nblk;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) dst[i] = blk[i];
+    // fixed-order sum of the private copies into the compact block
+    T *dst = scratch + size_t(tile) * tg.blk;
+    const int B0 = tg.B[0], B1 = tg.B[1];
+    for (int i = threadIdx.x; i < tg.blk; i += blockDim.x) {
+        const int b0 = i % B0, r1 = i / B0;
+        const int b1 = r1 % B1, b2 = r1 / B1;
+        const int si = (b2 * B1 + b1) * pitch + b0;
+        T s = T(0);
+        for (int k = 0; k < nw; ++k) s += blocks[size_t(k) * sblk + si];
+        dst[i] = s;
+    }
+}
+
+// Eq. (gridding) with shared-memory atomics, one tile per thread-block cluster
+// of CL CTAs (CL = 1: one CTA per tile).  Each CTA adds a 1/CL share of the
+// tile's particles to its own copy of the extended block, one particle per warp
+// at a time: the lanes own distinct (x, y) points of the stencil plane
+// (pp = lane + 32 e -> (pp mod P, pp div P)) and walk z, so an atomic
+// instruction never carries two updates of one word and the row pitch keeps
+// the lanes on distinct banks.  The cluster then sums the copies through
+// distributed shared memory, each CTA writing a slice of the compact block to
+// `scratch`.  When g != nullptr the charges are taken from g (original
+// particle order).
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
+            const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int NE = (P * P + 31) / 32;
+    const int CL = int(cluster.num_blocks()), rank = int(cluster.block_rank());
+    const int tile = blockIdx.x / CL;
+    const int beg = off[tile], end = off[tile + 1];
+    if (beg == end) return;                               // the same for every CTA of the cluster
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *blk = reinterpret_cast<T *>(smraw);
+    T *sc = blk + align_up_elems<T>(tg.sblk);             // PKB coefficients
+    const int ncoef = (wa.nu + 1) * P;
+    T *wb = sc + align_up_elems<T>(ncoef);                // [warp][3P]
+    for (int i = threadIdx.x; i < tg.sblk; i += blockDim.x) blk[i] = T(0);
+    if (wa.kind == SE_WIN_PKB)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T *w = wb + warp * 3 * P;
+    int o[3];
+    tile_origin(tg, tile, o);
+    const int pitch = tg.pitch, plane = tg.B[1] * tg.pitch;
+    int poff[NE], pdx[NE], pdy[NE];
+    bool pv[NE];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        const int pp = lane + 32 * e;
+        pv[e] = pp < P * P;
+        pdx[e] = pv[e] ? pp % P : 0;
+        pdy[e] = pv[e] ? pp / P : 0;
+        poff[e] = pdy[e] * pitch + pdx[e];
+    }
+    __syncthreads();
+
+    for (int p = beg + rank * nw + warp; p < end; p += CL * nw) {
+        const typename Vec4<T>::type r = fq[p];
+        const int4 a = ia[p];
+        const T qv = g ? g[a.x] : r.w;
+        for (int j = lane; j < 3 * P; j += 32) {
+            const int ax = j / P, k = j - ax * P;
+            w[j] = win_val_smem<T, P>(wa.kind, wa.nu, wa.alpha, sc, ax == 0 ? r.x : (ax == 1 ? r.y : r.z), k);
+        }
+        __syncwarp();
+        T wxy[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) wxy[e] = qv * w[pdx[e]] * w[P + pdy[e]];
+        T *base = blk + block_base(tg, o, a);
+#pragma unroll
+        for (int dz = 0; dz < P; ++dz) {
+            const T wz = w[2 * P + dz];
+            T *row = base + dz * plane;
+#pragma unroll
+            for (int e = 0; e < NE; ++e)
+                if (pv[e]) atomicAdd(row + poff[e], wxy[e] * wz);
+        }
+        __syncwarp();
+    }
+    cluster.sync();                                       // every copy complete and visible to the cluster
+    T *dst = scratch + size_t(tile) * tg.blk;
+    const int chunk = (tg.blk + CL - 1) / CL;
+    const int lo = rank * chunk, hi = min(tg.blk, lo + chunk);
+    const int B0 = tg.B[0];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int si = (i / B0) * pitch + i % B0;
+        T s = T(0);
+        for (int j = 0; j < CL; ++j) s += cluster.map_shared_rank(blk, j)[si];
+        dst[i] = s;
+    }
+    cluster.sync();                                       // no CTA leaves while its block is still read
 }
 
 // Sum of the tile blocks covering each grid point, in a fixed order, written
 // to the forward-FFT input.  One CTA per tile writes that tile's T0 x T1 x T2
-// points (threads laid out over x, y; loop over z); each point adds the blocks
-// of the tiles c - j (per axis, while the offset stays inside the block).
-// Tiles without particles hold no block and are skipped.  Periodic axes wrap
-// the tile index (their tile edge divides the grid); free axes never wrap.
-template <typename T>
+// points (threads over x, y; loop over z); each point adds the blocks of the
+// tiles c - j (per axis, while the offset stays inside the block).  Which of
+// those tiles hold particles (tiles without particles hold no block) is read
+// once per CTA into shared memory.  Periodic axes wrap the tile index (their
+// tile edge divides the grid); free axes never wrap.
+template <typename T, int J>
 __global__ void k_merge(TileGeom tg, const int *__restrict__ off, const T *__restrict__ scratch,
                         T *__restrict__ dst, GridView v)
 {
+    __shared__ int src_tile[J][J][J];
     const int tile = blockIdx.x;
-    const int c0 = tile % tg.nt[0], c1 = (tile / tg.nt[0]) % tg.nt[1], c2 = tile / (tg.nt[0] * tg.nt[1]);
-    const int l0 = threadIdx.x, l1 = threadIdx.y;
-    const int g0 = c0 * tg.T[0] + l0, g1 = c1 * tg.T[1] + l1;
-    if (l0 >= tg.T[0] || l1 >= tg.T[1] || g0 >= tg.n[0] || g1 >= tg.n[1]) return;
-    for (int l2 = threadIdx.z; l2 < tg.T[2]; l2 += blockDim.z) {
-        const int g2 = c2 * tg.T[2] + l2;
-        if (g2 >= tg.n[2]) break;
-        T s = T(0);
-        for (int j2 = 0; l2 + j2 * tg.T[2] < tg.B[2]; ++j2) {
-            int t2 = c2 - j2;
-            if (t2 < 0) { if (!tg.periodic[2]) break; t2 = ((t2 % tg.nt[2]) + tg.nt[2]) % tg.nt[2]; }
-            for (int j1 = 0; l1 + j1 * tg.T[1] < tg.B[1]; ++j1) {
-                int t1 = c1 - j1;
-                if (t1 < 0) { if (!tg.periodic[1]) break; t1 = ((t1 % tg.nt[1]) + tg.nt[1]) % tg.nt[1]; }
-                for (int j0 = 0; l0 + j0 * tg.T[0] < tg.B[0]; ++j0) {
-                    int t0 = c0 - j0;
-                    if (t0 < 0) { if (!tg.periodic[0]) break; t0 = ((t0 % tg.nt[0]) + tg.nt[0]) % tg.nt[0]; }
-                    const int src = (t2 * tg.nt[1] + t1) * tg.nt[0] + t0;
-                    if (off[src + 1] == off[src]) continue;
-                    s += scratch[size_t(src) * tg.blk +
-                                 ((l2 + j2 * tg.T[2]) * tg.B[1] + (l1 + j1 * tg.T[1])) * tg.B[0] + l0 + j0 * tg.T[0]];
-                }
+    int c[3];
+    c[0] = tile % tg.nt[0];
+    c[1] = (tile / tg.nt[0]) % tg.nt[1];
+    c[2] = tile / (tg.nt[0] * tg.nt[1]);
+    int nj[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nj[a] = min(J, (tg.B[a] - 1) / tg.T[a] + 1);
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    for (int q = tid; q < J * J * J; q += nthr) {
+        const int j0 = q % J, j1 = (q / J) % J, j2 = q / (J * J);
+        const int jj[3] = {j0, j1, j2};
+        int t[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t[a] = c[a] - jj[a];
+            if (jj[a] >= nj[a]) ok = false;
+            else if (t[a] < 0) {
+                if (!tg.periodic[a]) ok = false;
+                else t[a] = ((t[a] % tg.nt[a]) + tg.nt[a]) % tg.nt[a];
             }
         }
+        int s = -1;
+        if (ok) {
+            const int id = (t[2] * tg.nt[1] + t[1]) * tg.nt[0] + t[0];
+            if (off[id + 1] != off[id]) s = id;
+        }
+        src_tile[j2][j1][j0] = s;
+    }
+    __syncthreads();
+    const int l0 = threadIdx.x, l1 = threadIdx.y;
+    const int g0 = c[0] * tg.T[0] + l0, g1 = c[1] * tg.T[1] + l1;
+    if (l0 >= tg.T[0] || l1 >= tg.T[1] || g0 >= tg.n[0] || g1 >= tg.n[1]) return;
+    for (int l2 = threadIdx.z; l2 < tg.T[2]; l2 += blockDim.z) {
+        const int g2 = c[2] * tg.T[2] + l2;
+        if (g2 >= tg.n[2]) break;
+        // all candidate loads first (unrolled), then the fixed-order sum
+        T val[J][J][J];
+#pragma unroll
+        for (int j2 = 0; j2 < J; ++j2)
+#pragma unroll
+            for (int j1 = 0; j1 < J; ++j1)
+#pragma unroll
+                for (int j0 = 0; j0 < J; ++j0) {
+                    const int o2 = l2 + j2 * tg.T[2], o1 = l1 + j1 * tg.T[1], o0 = l0 + j0 * tg.T[0];
+                    const int src = src_tile[j2][j1][j0];
+                    const bool use = src >= 0 && o2 < tg.B[2] && o1 < tg.B[1] && o0 < tg.B[0];
+                    val[j2][j1][j0] = use ? scratch[size_t(src) * tg.blk + (o2 * tg.B[1] + o1) * tg.B[0] + o0] : T(0);
+                }
+        T s = T(0);
+#pragma unroll
+        for (int j2 = 0; j2 < J; ++j2)
+#pragma unroll
+            for (int j1 = 0; j1 < J; ++j1)
+#pragma unroll
+                for (int j0 = 0; j0 < J; ++j0) s += val[j2][j1][j0];
         dst[g0 + g1 * v.s1 + g2 * v.s2] = s;
     }
 }
@@ -443,6 +611,32 @@ __global__ void k_unpad_1p(int nl, int Mt, int sMt, int s0Mt, int row, typename 
 }
 
 // ----------------------------------------------------------------- gathering
+// Energy E = sum of the per-CTA partial sums part[0..n), added in index order by
+// the CTA that finishes last (the others have published their partials).
+__device__ __forceinline__ void finish_energy(double *part, int n, double *energy, int *done)
+{
+    __shared__ bool last;
+    __shared__ double red[256];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *energy = red[0];
+        *done = 0;
+    }
+}
+
 __device__ __forceinline__ void cp_async_elem(float *dst, const float *src)
 {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
@@ -455,33 +649,92 @@ __device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Stage the extended block of a tile from the real grid into shared memory
-// with asynchronous copies (one row per warp iteration, lanes along x;
-// periodic axes wrap, points past a free axis' end are never used and are set
-// to zero).  The caller waits (cp_async_wait_all) and synchronises.
+// Stage the extended block of a tile (tile origin o) from the real grid into
+// shared memory (row pitch tg.pitch) with asynchronous copies: warps take rows
+// (y, z), lanes run along x.  Periodic axes wrap; points past a free axis' end
+// are never used and are set to zero.  The caller waits (cp_async_wait_all)
+// and synchronises.
 template <typename T>
-__device__ __forceinline__ void stage_block(const TileGeom &tg, int tile, const T *__restrict__ grid, GridView v,
-                                            T *blk)
+__device__ __forceinline__ void stage_block(const TileGeom &tg, const int o[3], const T *__restrict__ grid,
+                                            GridView v, T *blk)
 {
-    const int tx = tile % tg.nt[0], ty = (tile / tg.nt[0]) % tg.nt[1], tz = tile / (tg.nt[0] * tg.nt[1]);
-    const int o0 = tx * tg.T[0], o1 = ty * tg.T[1], o2 = tz * tg.T[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int rows = tg.B[1] * tg.B[2];
+    const int B1 = tg.B[1], rows = tg.B[1] * tg.B[2];
+    int b1 = warp % B1, b2 = warp / B1;
     for (int r = warp; r < rows; r += nw) {
-        const int b1 = r % tg.B[1], b2 = r / tg.B[1];
-        int g1 = o1 + b1, g2 = o2 + b2;
+        int g1 = o[1] + b1, g2 = o[2] + b2;
         bool ok = true;
         if (g1 >= tg.n[1]) { if (tg.periodic[1]) { while (g1 >= tg.n[1]) g1 -= tg.n[1]; } else ok = false; }
         if (g2 >= tg.n[2]) { if (tg.periodic[2]) { while (g2 >= tg.n[2]) g2 -= tg.n[2]; } else ok = false; }
-        T *drow = blk + r * tg.B[0];
+        T *drow = blk + r * tg.pitch;
         const T *srow = grid + g1 * v.s1 + g2 * v.s2;
         for (int b0 = lane; b0 < tg.B[0]; b0 += 32) {
-            int g0 = o0 + b0;
+            int g0 = o[0] + b0;
             bool okx = ok;
             if (g0 >= tg.n[0]) { if (tg.periodic[0]) { while (g0 >= tg.n[0]) g0 -= tg.n[0]; } else okx = false; }
             if (okx) cp_async_elem(drow + b0, srow + g0);
             else drow[b0] = T(0);
         }
+        b1 += nw;
+        while (b1 >= B1) { b1 -= B1; ++b2; }
+    }
+}
+
+// Weights of one particle group at this lane's offset dx along the three axes,
+// stored to the group's slot w[6P] (values x, y, z, then derivatives).
+template <typename T, int P, int NU, bool GRAD>
+__device__ __forceinline__ void group_weights(const WindowArgs<T> &wa, const LaneCoef<T, NU> &cf,
+                                              const typename Vec4<T>::type &r, int dx, T *w)
+{
+    T w0, w1, w2, d0 = T(0), d1 = T(0), d2 = T(0);
+    win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.x, dx, w0, d0);
+    win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.y, dx, w1, d1);
+    win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.z, dx, w2, d2);
+    w[dx] = w0;
+    w[P + dx] = w1;
+    w[2 * P + dx] = w2;
+    if (GRAD) {
+        w[3 * P + dx] = d0;
+        w[4 * P + dx] = d1;
+        w[5 * P + dx] = d2;
+    }
+}
+
+// Contraction of one particle's P^3 stencil with the grid (through `at`, which
+// maps (dy, dz) to the row base for this lane's dx): phi and its gradient
+// factors for this lane, Eq. (complete_integral) and Eq. (force-method-1).
+template <typename T, int P, bool GRAD, class RowAt>
+__device__ __forceinline__ void group_contract(const T *w, int dx, RowAt at, T &ph, T &gx, T &gy, T &gz)
+{
+    T wy[P], dwy[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        wy[j] = w[P + j];
+        dwy[j] = GRAD ? w[4 * P + j] : T(0);
+    }
+    T sp = T(0), sgy = T(0), sgz = T(0);
+#pragma unroll
+    for (int dz = 0; dz < P; ++dz) {
+        T t0 = T(0), t1 = T(0);
+#pragma unroll
+        for (int dy = 0; dy < P; ++dy) {
+            const T hv = at(dy, dz);
+            t0 = fma(wy[dy], hv, t0);
+            if (GRAD) t1 = fma(dwy[dy], hv, t1);
+        }
+        const T wz = w[2 * P + dz];
+        sp = fma(wz, t0, sp);
+        if (GRAD) {
+            sgy = fma(wz, t1, sgy);
+            sgz = fma(w[5 * P + dz], t0, sgz);
+        }
+    }
+    const T wx = w[dx];
+    ph = wx * sp;
+    if (GRAD) {
+        gx = w[3 * P + dx] * sp;
+        gy = wx * sgy;
+        gz = wx * sgz;
     }
 }
 
@@ -489,29 +742,35 @@ __device__ __forceinline__ void stage_block(const TileGeom &tg, int tile, const 
 // inverse-FFT normalisation are folded into the scaling) and, with GRAD,
 // Eq. (force-method-1): grad phi = sum_j grad W(x_m - x_j) H~_j, the window
 // gradient being the exact derivative of the window used for gridding.
-// Lane (particle, dx) walks the P x P rows (dy, dz) at offset dx, summing over
-// dy in registers, then over dz; the P lanes of a particle are reduced by
-// shuffles.  Outputs go to the particles' original positions: phi_m (+ self
-// term), F_m = -q_m grad phi_m, and per-tile partial sums of 1/2 q_m phi_m in
-// FP64.
+// One CTA per tile with the tile's block staged in shared memory; lane
+// (particle, dx) walks the P x P rows (dy, dz) at offset dx, summing over dy in
+// registers, then over dz; the P lanes of a particle are reduced by shuffles.
+// Outputs go to the particles' original positions: phi_m (+ self term),
+// F_m = -q_m grad phi_m, and per-CTA partial sums of 1/2 q_m phi_m in FP64.
 template <typename T, int P, int NU, bool GRAD>
 __global__ void __launch_bounds__(kThreads)
-k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
-         const int2 *__restrict__ ic, WindowArgs<T> wa, const T *__restrict__ grid, GridView v,
-         T *__restrict__ phi, T *__restrict__ F, double *__restrict__ tile_part, T inv_h, T self_coef)
+k_gather(TileGeom tg, int split, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
+         const int4 *__restrict__ ia, WindowArgs<T> wa, const T *__restrict__ grid, GridView v,
+         T *__restrict__ phi, T *__restrict__ F, double *__restrict__ part, double *energy, int *done, T inv_h,
+         T self_coef)
 {
     constexpr int G = LaneMap<P>::G;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x / split, rank = blockIdx.x - tile * split;
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) {
-        if (tile_part && threadIdx.x == 0) tile_part[tile] = 0.0;
+        if (part) {
+            if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+            finish_energy(part, gridDim.x, energy, done);
+        }
         return;
     }
     extern __shared__ __align__(16) unsigned char smraw[];
     T *blk = reinterpret_cast<T *>(smraw);
-    T *wb = blk + align_up_elems<T>(tg.blk);        // [warp][G][6][P]: values x,y,z then derivatives
+    T *wb = blk + align_up_elems<T>(tg.sblk);          // [warp][G][6P]
     __shared__ double epart[kThreads / 32];
-    stage_block<T>(tg, tile, grid, v, blk);
+    int o[3];
+    tile_origin(tg, tile, o);
+    stage_block<T>(tg, o, grid, v, blk);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int grp = lane / P, dx = lane - grp * P;
@@ -519,67 +778,27 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
     LaneCoef<T, NU> cf;
     if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
     T *w = wb + (warp * G + (lane_on ? grp : 0)) * 6 * P;
-    const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
+    const int pitch = tg.pitch, plane = tg.B[1] * tg.pitch;
     double esum = 0.0;
     cp_async_wait_all();
     __syncthreads();
 
-    for (int p0 = beg + warp * G; p0 < end; p0 += nw * G) {
+    for (int p0 = beg + (rank * nw + warp) * G; p0 < end; p0 += split * nw * G) {
         const int p = p0 + grp;
         const bool has = lane_on && p < end;
         typename Vec4<T>::type r;
-        int2 c = make_int2(0, 0);
+        int4 a = make_int4(0, 0, 0, 0);
         if (has) {
             r = fq[p];
-            c = ic[p];
-            T w0, w1, w2, d0, d1, d2;
-            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.x, dx, w0, d0);
-            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.y, dx, w1, d1);
-            win_eval<T, P, NU, GRAD>(wa.kind, wa.alpha, cf, r.z, dx, w2, d2);
-            w[dx] = w0;
-            w[P + dx] = w1;
-            w[2 * P + dx] = w2;
-            if (GRAD) {
-                w[3 * P + dx] = d0;
-                w[4 * P + dx] = d1;
-                w[5 * P + dx] = d2;
-            }
+            a = ia[p];
+            group_weights<T, P, NU, GRAD>(wa, cf, r, dx, w);
         }
         __syncwarp();
         T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
         if (has) {
-            T wy[P], dwy[P];
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                wy[j] = w[P + j];
-                if (GRAD) dwy[j] = w[4 * P + j];
-            }
-            const T *col = blk + block_base(tg, c.y) + dx;
-            T sp = T(0), sgy = T(0), sgz = T(0);
-#pragma unroll
-            for (int dz = 0; dz < P; ++dz) {
-                const T *row = col + dz * BXY;
-                T t0 = T(0), t1 = T(0);
-#pragma unroll
-                for (int dy = 0; dy < P; ++dy) {
-                    const T hv = row[dy * BX];
-                    t0 = fma(wy[dy], hv, t0);
-                    if (GRAD) t1 = fma(dwy[dy], hv, t1);
-                }
-                const T wz = w[2 * P + dz];
-                sp = fma(wz, t0, sp);
-                if (GRAD) {
-                    sgy = fma(wz, t1, sgy);
-                    sgz = fma(w[5 * P + dz], t0, sgz);
-                }
-            }
-            const T wx = w[dx];
-            ph = wx * sp;
-            if (GRAD) {
-                gx = w[3 * P + dx] * sp;
-                gy = wx * sgy;
-                gz = wx * sgz;
-            }
+            const T *col = blk + block_base(tg, o, a) + dx;
+            group_contract<T, P, GRAD>(w, dx, [&](int dy, int dz) { return col[dz * plane + dy * pitch]; },
+                                       ph, gx, gy, gz);
         }
         ph = group_sum<T, P>(ph, dx);
         if (GRAD) {
@@ -590,7 +809,7 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
         if (has && dx == 0) {
             const T qv = r.w;
             const T phv = ph + self_coef * qv;
-            const int64_t m = c.x;
+            const int64_t m = a.x;
             if (phi) phi[m] = phv;
             if (GRAD && F) {
                 const T s = -qv * inv_h;
@@ -602,15 +821,95 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
         }
         __syncwarp();
     }
-    if (tile_part) {
-        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+    if (part) {
+        for (int s = 16; s > 0; s >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, s);
         if (lane == 0) epart[warp] = esum;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
             for (int i = 0; i < nw; ++i) s += epart[i];
-            tile_part[tile] = s;
+            part[blockIdx.x] = s;
         }
+        finish_energy(part, gridDim.x, energy, done);
+    }
+}
+
+// The same gathering without tiles or staging, for sparsely filled tiles:
+// warps take consecutive groups of G sorted particles and read the grid
+// directly (the sorted order keeps neighbouring stencils in L1).  Per-CTA
+// partial energies go to part[blockIdx.x].
+template <typename T, int P, int NU, bool GRAD>
+__global__ void __launch_bounds__(kThreads)
+k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__ fq, const int4 *__restrict__ ia,
+              WindowArgs<T> wa, const T *__restrict__ grid, GridView v, T *__restrict__ phi, T *__restrict__ F,
+              double *__restrict__ part, double *energy, int *done, T inv_h, T self_coef)
+{
+    constexpr int G = LaneMap<P>::G;
+    __shared__ T wbs[kThreads / 32][32 * 6];
+    __shared__ double epart[kThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int grp = lane / P, dx = lane - grp * P;
+    const bool lane_on = grp < G;
+    LaneCoef<T, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+    T *w = &wbs[warp][(lane_on ? grp : 0) * 6 * P];
+    const int64_t p = (int64_t(blockIdx.x) * nw + warp) * G + grp;
+    const bool has = lane_on && p < N;
+    typename Vec4<T>::type r;
+    int4 a = make_int4(0, 0, 0, 0);
+    if (has) {
+        r = fq[p];
+        a = ia[p];
+        group_weights<T, P, NU, GRAD>(wa, cf, r, dx, w);
+    }
+    __syncwarp();
+    T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
+    if (has) {
+        int g0 = a.y + dx;
+        if (g0 >= tg.n[0]) g0 -= tg.n[0];
+        int yo[P], zo[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            int y = a.z + j, z = a.w + j;
+            if (y >= tg.n[1]) y -= tg.n[1];
+            if (z >= tg.n[2]) z -= tg.n[2];
+            yo[j] = int(y * v.s1);
+            zo[j] = int(z * v.s2);
+        }
+        const T *col = grid + g0;
+        group_contract<T, P, GRAD>(w, dx, [&](int dy, int dz) { return __ldg(col + yo[dy] + zo[dz]); },
+                                   ph, gx, gy, gz);
+    }
+    ph = group_sum<T, P>(ph, dx);
+    if (GRAD) {
+        gx = group_sum<T, P>(gx, dx);
+        gy = group_sum<T, P>(gy, dx);
+        gz = group_sum<T, P>(gz, dx);
+    }
+    double esum = 0.0;
+    if (has && dx == 0) {
+        const T qv = r.w;
+        const T phv = ph + self_coef * qv;
+        const int64_t m = a.x;
+        if (phi) phi[m] = phv;
+        if (GRAD && F) {
+            const T s = -qv * inv_h;
+            F[3 * m] = s * gx;
+            F[3 * m + 1] = s * gy;
+            F[3 * m + 2] = s * gz;
+        }
+        esum = 0.5 * double(qv) * double(phv);
+    }
+    if (part) {
+        for (int s = 16; s > 0; s >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, s);
+        if (lane == 0) epart[warp] = esum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < nw; ++i) s += epart[i];
+            part[blockIdx.x] = s;
+        }
+        finish_energy(part, gridDim.x, energy, done);
     }
 }
 
@@ -622,7 +921,7 @@ k_gather(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
 template <typename T, int P, int NU>
 __global__ void __launch_bounds__(kThreads)
 k_gather_vjp(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
-             const int2 *__restrict__ ic, WindowArgs<T> wa, const T *__restrict__ grid_q,
+             const int4 *__restrict__ ia, WindowArgs<T> wa, const T *__restrict__ grid_q,
              const T *__restrict__ grid_g, GridView v, const T *__restrict__ g, T *__restrict__ gxo,
              T *__restrict__ gqo, T inv_h)
 {
@@ -632,10 +931,12 @@ k_gather_vjp(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::t
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *bq = reinterpret_cast<T *>(smraw);
-    T *bg = bq + align_up_elems<T>(tg.blk);
-    T *wb = bg + align_up_elems<T>(tg.blk);
-    stage_block<T>(tg, tile, grid_q, v, bq);
-    stage_block<T>(tg, tile, grid_g, v, bg);
+    T *bg = bq + align_up_elems<T>(tg.sblk);
+    T *wb = bg + align_up_elems<T>(tg.sblk);
+    int o[3];
+    tile_origin(tg, tile, o);
+    stage_block<T>(tg, o, grid_q, v, bq);
+    stage_block<T>(tg, o, grid_g, v, bg);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int grp = lane / P, dx = lane - grp * P;
@@ -643,7 +944,7 @@ k_gather_vjp(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::t
     LaneCoef<T, NU> cf;
     if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
     T *w = wb + (warp * G + (lane_on ? grp : 0)) * 6 * P;
-    const int BX = tg.B[0], BXY = tg.B[0] * tg.B[1];
+    const int pitch = tg.pitch, plane = tg.B[1] * tg.pitch;
     cp_async_wait_all();
     __syncthreads();
 
@@ -651,58 +952,34 @@ k_gather_vjp(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::t
         const int p = p0 + grp;
         const bool has = lane_on && p < end;
         typename Vec4<T>::type r;
-        int2 c = make_int2(0, 0);
+        int4 a = make_int4(0, 0, 0, 0);
         T gm = T(0);
         if (has) {
             r = fq[p];
-            c = ic[p];
-            gm = g[c.x];
-            T w0, w1, w2, d0, d1, d2;
-            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.x, dx, w0, d0);
-            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.y, dx, w1, d1);
-            win_eval<T, P, NU, true>(wa.kind, wa.alpha, cf, r.z, dx, w2, d2);
-            w[dx] = w0; w[P + dx] = w1; w[2 * P + dx] = w2;
-            w[3 * P + dx] = d0; w[4 * P + dx] = d1; w[5 * P + dx] = d2;
+            a = ia[p];
+            gm = g[a.x];
+            group_weights<T, P, NU, true>(wa, cf, r, dx, w);
         }
         __syncwarp();
         T a0 = T(0), ax = T(0), ay = T(0), az = T(0);
         if (has) {
             const T qm = r.w;
-            T wy[P], dwy[P];
-#pragma unroll
-            for (int j = 0; j < P; ++j) { wy[j] = w[P + j]; dwy[j] = w[4 * P + j]; }
-            const int b = block_base(tg, c.y) + dx;
-            T sp = T(0), sgy = T(0), sgz = T(0), sq = T(0);
-#pragma unroll
-            for (int dz = 0; dz < P; ++dz) {
-                T t0 = T(0), t1 = T(0), t2 = T(0);
-#pragma unroll
-                for (int dy = 0; dy < P; ++dy) {
-                    const int o = b + dz * BXY + dy * BX;
-                    const T hg = bg[o];
-                    const T hc = gm * bq[o] + qm * hg;     // grid of g_m H~_q + q_m H~_g
-                    t0 = fma(wy[dy], hc, t0);
-                    t1 = fma(dwy[dy], hc, t1);
-                    t2 = fma(wy[dy], hg, t2);
-                }
-                const T wz = w[2 * P + dz], dwz = w[5 * P + dz];
-                sp = fma(wz, t0, sp);
-                sgy = fma(wz, t1, sgy);
-                sgz = fma(dwz, t0, sgz);
-                sq = fma(wz, t2, sq);
-            }
-            const T wx = w[dx];
-            a0 = wx * sq;
-            ax = w[3 * P + dx] * sp;
-            ay = wx * sgy;
-            az = wx * sgz;
+            const int b = block_base(tg, o, a) + dx;
+            // grid of g_m H~_q + q_m H~_g for the position gradient, H~_g for g_q
+            T dummy0, dummy1, dummy2;
+            group_contract<T, P, true>(w, dx, [&](int dy, int dz) {
+                const int idx = b + dz * plane + dy * pitch;
+                return gm * bq[idx] + qm * bg[idx];
+            }, dummy0, ax, ay, az);
+            group_contract<T, P, false>(w, dx, [&](int dy, int dz) { return bg[b + dz * plane + dy * pitch]; },
+                                        a0, dummy0, dummy1, dummy2);
         }
         a0 = group_sum<T, P>(a0, dx);
         ax = group_sum<T, P>(ax, dx);
         ay = group_sum<T, P>(ay, dx);
         az = group_sum<T, P>(az, dx);
         if (has && dx == 0) {
-            const int64_t m = c.x;
+            const int64_t m = a.x;
             if (gqo) gqo[m] = a0;
             if (gxo) { gxo[3 * m] = ax * inv_h; gxo[3 * m + 1] = ay * inv_h; gxo[3 * m + 2] = az * inv_h; }
         }

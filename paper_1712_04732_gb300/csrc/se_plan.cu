@@ -2,6 +2,7 @@
 // (Sec. 4.1), the scaling tables of Eq. (scale) with the truncated Green's
 // functions, the FP64 precomputation of Alg. 3 (D = 0), device buffers and
 // cuFFT plans.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -420,9 +421,17 @@ static se_status make_plans(se_plan_s *p)
         SE_PLAN(cufftPlan3d(&p->fwd, M, M, M, R2C), p->have_fwd, "plan fwd");
         SE_PLAN(cufftPlan3d(&p->inv, M, M, M, C2R), p->have_inv, "plan inv");
     } else if (p->D == 0) {
+        // (2 M~)^3 transform of a grid that is zero outside its M~^3 corner: 2D
+        // transforms of the M~ non-zero z-planes, then one strided z-transform
+        // over all (x', y) columns; the inverse mirrors it and keeps z < M~.
         const int n2 = 2 * Mt;
-        SE_PLAN(cufftPlan3d(&p->fwd, n2, n2, n2, R2C), p->have_fwd, "plan fwd");
-        SE_PLAN(cufftPlan3d(&p->inv, n2, n2, n2, C2R), p->have_inv, "plan inv");
+        int n[2] = {n2, n2};
+        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt), p->have_inv, "plan inv");
+        int nz[1] = {n2};
+        const int col = n2 * (Mt + 1);
+        SE_PLAN(cufftPlanMany(&p->free_main, 1, nz, nz, col, 1, nz, col, 1, C2C, col), p->have_free_main,
+                "plan z");
     } else if (p->D == 2) {
         int n[2] = {M, M};
         SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt), p->have_fwd, "plan fwd");
@@ -467,6 +476,32 @@ se_status plan_set_fft_stream(se_plan_s *p)
 
 // ------------------------------------------------------------ build / reserve / release
 
+// Row pitch (elements) of a block in shared memory: the smallest pitch >= B0
+// for which the gridding kernel's access pattern -- rows of P consecutive lanes
+// stacked 32 / P deep -- touches the fewest bank wavefronts.
+static int choose_pitch(int B0, int P, int elem)
+{
+    int best = B0, best_cost = 1 << 30;
+    for (int pitch = B0; pitch < B0 + 32; ++pitch) {
+        int cost = 0;
+        // a warp instruction moves 32 elements; 8-byte elements go out as two half-warps
+        const int per_wave = elem == 8 ? 16 : 32;
+        for (int h = 0; h < 32 / per_wave; ++h) {
+            int banks[32] = {0};
+            for (int l = h * per_wave; l < (h + 1) * per_wave; ++l) {
+                const int r = l / P, c = l % P;
+                const long word = (long(r) * pitch + c) * (elem / 4);
+                for (int w = 0; w < elem / 4; ++w) banks[(word + w) % 32]++;
+            }
+            int worst = 0;
+            for (int b = 0; b < 32; ++b) worst = std::max(worst, banks[b]);
+            cost += worst;
+        }
+        if (cost < best_cost) { best_cost = cost; best = pitch; }
+    }
+    return best;
+}
+
 static int choose_tile(int n, bool periodic, int pref)
 {
     if (!periodic) return pref;
@@ -491,7 +526,7 @@ se_status plan_build(se_plan_s *p)
         p->off[a] = per ? 0.0 : p->dL / 2.0;
     }
     if (p->window == SE_WIN_PKB) fit_pkb(p);
-    // tiles: pick the edge so that the extended block fits in shared memory
+    // tiles: pick the edge so that the extended blocks fit in shared memory
     int pref = p->tile_pref > 0 ? p->tile_pref : 8;
     for (;;) {
         int blk = 1;
@@ -502,19 +537,31 @@ se_status plan_build(se_plan_s *p)
             blk *= p->tg.B[a];
         }
         p->tg.blk = blk;
-        const size_t need = (2 * ((size_t(blk) + 15) & ~size_t(15)) + 512 + (kThreads / 32) * 6 * p->P) * p->elem;
-        if (need <= 220 * 1024) break;
-        if (pref <= 4) return fail(SE_EINVAL, "gridding block does not fit in shared memory");
+        p->tg.pitch = choose_pitch(p->tg.B[0], p->P, int(p->elem));
+        p->tg.sblk = p->tg.pitch * p->tg.B[1] * p->tg.B[2];
+        const size_t sblk = (size_t(p->tg.sblk) + 31) & ~size_t(31);
+        // gridding: one private block per warp (up to 8), within ~200 KB of shared memory
+        const size_t budget = 200 * 1024 / p->elem - 2 * 32 * 3 * kMaxP;
+        p->spread_warps = int(std::min<size_t>(8, budget / sblk));
+        // adjoint gathering stages two blocks
+        const size_t need_vjp = (2 * sblk + (kThreads / 32) * 32 * 6) * p->elem;
+        bool fits = p->spread_warps >= 1 && need_vjp <= 220 * 1024;
+        for (int a = 0; a < 3; ++a) fits = fits && (p->tg.B[a] - 1) / p->tg.T[a] + 1 <= kMergeJ;
+        if (fits) break;
+        if (pref <= 4) return fail(SE_EINVAL, "gridding block does not fit in shared memory (grid size M has no suitable tile edge)");
         pref /= 2;
     }
     const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
     se_status st;
     if ((st = dev_alloc(p, (void **)&p->tile_cnt, sizeof(int) * (nt + 1))) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->tile_off, sizeof(int) * (nt + 1))) != SE_OK) return st;
-    if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * std::max(nt, 256))) != SE_OK) return st;
+    p->tile_part_elems = size_t(std::max(8 * nt, 256));
+    if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * p->tile_part_elems)) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->red, sizeof(double) * 8)) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->err, sizeof(int))) != SE_OK) return st;
     if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return cuda_fail(cudaGetLastError(), "memset");
+    if ((st = dev_alloc(p, (void **)&p->counters, 4 * sizeof(int))) != SE_OK) return st;
+    if (cudaMemset(p->counters, 0, 4 * sizeof(int)) != cudaSuccess) return cuda_fail(cudaGetLastError(), "memset");
     p->scratch_bytes = size_t(nt) * p->tg.blk * p->elem;
     if ((st = dev_alloc(p, &p->scratch, p->scratch_bytes)) != SE_OK) return st;
     // grids and spectra
@@ -522,7 +569,7 @@ se_status plan_build(se_plan_s *p)
     const int64_t nlog = int64_t(p->tg.n[0]) * p->tg.n[1] * p->tg.n[2];
     if (p->D == 0) {
         const int64_t n2 = 2 * int64_t(Mt);
-        p->grid_in_elems = p->grid_out_elems = size_t(n2 * n2 * n2);
+        p->grid_in_elems = p->grid_out_elems = size_t(Mt * n2 * n2);     // the M~ non-zero z-planes
         p->gin.s1 = p->gout.s1 = n2;
         p->gin.s2 = p->gout.s2 = n2 * n2;
         p->spec_elems = size_t(n2 * n2 * (Mt + 1));
@@ -549,6 +596,12 @@ se_status plan_build(se_plan_s *p)
     if ((st = dev_alloc(p, &p->grid_out, p->grid_out_elems * p->elem)) != SE_OK) return st;
     if (cudaMemset(p->grid_in, 0, p->grid_in_elems * p->elem) != cudaSuccess) return cuda_fail(cudaGetLastError(), "memset");
     if ((st = dev_alloc(p, &p->spec, p->spec_elems * 2 * p->elem)) != SE_OK) return st;
+    if (p->D == 0) {
+        // 2D spectra of the non-zero z-planes; the upper M~ planes stay zero
+        if ((st = dev_alloc(p, &p->spec_pad, p->spec_elems * 2 * p->elem)) != SE_OK) return st;
+        if (cudaMemset(p->spec_pad, 0, p->spec_elems * 2 * p->elem) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "memset");
+    }
     if (p->U_elems && (st = dev_alloc(p, &p->U, p->U_elems * 2 * p->elem)) != SE_OK) return st;
     if (p->Z_elems && (st = dev_alloc(p, &p->Z, p->Z_elems * 2 * p->elem)) != SE_OK) return st;
     if (p->sigma_elems && (st = dev_alloc(p, &p->sigma_tab, p->sigma_elems * p->elem)) != SE_OK) return st;
@@ -565,12 +618,20 @@ se_status plan_reserve(se_plan_s *p, int64_t n)
     if (cap > (int64_t(1) << 31) - 1) return fail(SE_EINVAL, "more than 2^31 - 1 particles");
     dev_free(p, (void **)&p->tile_rank);
     dev_free(p, &p->prt.frac_q);
-    dev_free(p, (void **)&p->prt.idx_code);
+    dev_free(p, (void **)&p->prt.idx_anc);
     p->cap = 0;
     se_status st;
     if ((st = dev_alloc(p, (void **)&p->tile_rank, sizeof(int2) * cap)) != SE_OK) return st;
     if ((st = dev_alloc(p, &p->prt.frac_q, 4 * p->elem * cap)) != SE_OK) return st;
-    if ((st = dev_alloc(p, (void **)&p->prt.idx_code, sizeof(int2) * cap)) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->prt.idx_anc, sizeof(int4) * cap)) != SE_OK) return st;
+    // per-CTA partial sums of the direct gathering: one per 8 warps x (32 / P) particles
+    const size_t nparts = std::max<size_t>(p->tile_part_elems, size_t(cap / 16 + 256));
+    if (nparts > p->tile_part_elems) {
+        dev_free(p, (void **)&p->tile_part);
+        p->tile_part_elems = 0;
+        if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * nparts)) != SE_OK) return st;
+        p->tile_part_elems = nparts;
+    }
     p->cap = cap;
     return SE_OK;
 }
@@ -599,16 +660,17 @@ se_status plan_second_grid(se_plan_s *p)
 
 void plan_release(se_plan_s *p)
 {
+    real_release(p);
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
     if (p->have_free_main) cufftDestroy(p->free_main);
     if (p->have_free_I) cufftDestroy(p->free_I);
     if (p->have_free_Z) cufftDestroy(p->free_Z);
     p->have_fwd = p->have_inv = p->have_free_main = p->have_free_I = p->have_free_Z = false;
-    void **bufs[] = {&p->grid_in, &p->grid_out, &p->spec, &p->U, &p->Z, (void **)&p->I_lines, &p->tabs, &p->sigma_tab,
+    void **bufs[] = {&p->grid_in, &p->grid_out, &p->spec, &p->spec_pad, &p->U, &p->Z, (void **)&p->I_lines, &p->tabs, &p->sigma_tab,
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
-                     (void **)&p->red, (void **)&p->err, (void **)&p->tile_rank, &p->prt.frac_q,
-                     (void **)&p->prt.idx_code, &p->io_buf, &p->grid_in2, &p->grid_out2};
+                     (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
+                     (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2};
     for (void **b : bufs) dev_free(p, b);
 }
 

@@ -62,6 +62,28 @@ def test_force_and_potential_match_discrete_oracle(D, window, dtype):
     assert En == pytest.approx(0.5 * float(q @ pb), rel=10 * tp)
 
 
+@pytest.mark.parametrize("spread_mode,gather_mode,split", [
+    (1, 1, 1), (2, 1, 2), (2, 1, 4), (2, 2, 8), (3, 1, 1), (3, 2, 1), (1, 2, 3)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_every_kernel_variant(spread_mode, gather_mode, split, dtype):
+    """Gridding variants (shared atomics, cluster-split atomics, per-warp private
+    blocks) and gathering variants (staged with split CTAs, direct reads) give the
+    same potential and forces."""
+    se = _se()
+    N, M = 3000, 24
+    x = wl.uniform_positions(N, 1.0, 41)
+    q = wl.uniform_charges(N, 41)
+    for D in (3, 2):
+        plan = se.Plan(D, 1.0, 6.0, M, 8, "pkb", dtype=dtype, spread_mode=spread_mode,
+                       gather_mode=gather_mode, split=split)
+        F, phi, En = _run(plan, x, q)
+        pb, gb = _oracle_for(plan).potential(x, q, grad=True)
+        tp, tf = TOL[dtype]
+        assert _rel(phi, pb) < tp
+        assert _rel(F, -q[:, None] * gb) < tf
+        assert En == pytest.approx(0.5 * float(q @ pb), rel=10 * tp)
+
+
 @pytest.mark.parametrize("P", [2, 4, 6, 10, 12, 14, 16])
 def test_every_compiled_support(P):
     se = _se()
@@ -352,3 +374,59 @@ def test_lattice_workload_gaussian():
     assert _rel(phi, pa) < 3 * 2 * np.exp(-(np.pi / 2) * 8 * np.sqrt(0.91))   # Sec. 5.2 estimate
     pb, gb = _oracle_for(plan).potential(x, q, grad=True)
     assert _rel(phi, pb) < 1e-11
+
+
+@pytest.mark.parametrize("dtype,P", [(torch.float32, 6), (torch.float64, 10)])
+def test_slab_workload_full_size(dtype, P):
+    """2P, N = 100000, M = 64, xi = 16, PKB P = 6 (FP32) / 10 (FP64): the GPU
+    against oracle B (same discretisation) on 300 sampled targets at full size."""
+    se = _se()
+    x, q, spec = wl.make("slab_2p", seed=1)
+    plan = se.Plan(2, 1.0, spec["xi"], spec["M"], P, "pkb", dtype=dtype)
+    F, phi, _ = _run(plan, x, q)
+    idx = _sample(len(q), 300, 1)
+    pb, gb = _oracle_for(plan).potential(x, q, xt=x[idx], grad=True)
+    tp, tf = TOL[dtype]
+    assert _rel(phi[idx], pb) < tp
+    assert _rel(F[idx], -q[idx, None] * gb) < tf
+
+
+@pytest.mark.parametrize("dtype,P,tol_phi,tol_F", [(torch.float32, 6, 1e-5, 3e-4), (torch.float32, 8, 1e-5, 1e-5),
+                                                   (torch.float64, 10, 1e-9, 2e-8)])
+def test_slab_parameters_accuracy_against_direct_sum(dtype, P, tol_phi, tol_F):
+    """The slab grid (M = 64, xi = 16) against the closed forms Eqs. (2pno0), (2p0)
+    on 2000 particles (200 sampled targets); forces need P + 2 for the
+    potential's accuracy (Sec. 7.2)."""
+    se = _se()
+    x, q, spec = wl.make("slab_2p", seed=3, N=2000)
+    plan = se.Plan(2, 1.0, spec["xi"], spec["M"], P, "pkb", dtype=dtype)
+    F, phi, _ = _run(plan, x, q)
+    idx = _sample(len(q), 200, 4)
+    pa, ga = E.fourier(2, x, q, 1.0, spec["xi"], xt=x[idx])
+    assert _rel(phi[idx], pa) < tol_phi
+    assert _rel(F[idx], -q[idx, None] * ga) < tol_F
+
+
+def test_wire_workload_full_size():
+    """1P, N = 1.2e6 (a sixth of them in ten Gaussian clouds), M = 128, xi = 32,
+    PKB P = 8, FP32: the GPU against oracle B on 200 sampled targets at full size."""
+    se = _se()
+    x, q, spec = wl.make("wire_1p", seed=1)
+    plan = se.Plan(1, 1.0, spec["xi"], spec["M"], spec["P"], "pkb", dtype=torch.float32)
+    F, phi, _ = _run(plan, x, q)
+    idx = _sample(len(q), 200, 2)
+    pb, gb = _oracle_for(plan).potential(x, q, xt=x[idx], grad=True)
+    assert _rel(phi[idx], pb) < TOL[torch.float32][0]
+    assert _rel(F[idx], -q[idx, None] * gb) < TOL[torch.float32][1]
+
+
+def test_wire_parameters_accuracy_against_direct_sum():
+    """The wire grid (M = 128, xi = 32, P = 8) against the 1P sum through
+    xi-independence (Sec. 2) on 3000 particles (clouds included)."""
+    se = _se()
+    x, q, spec = wl.make("wire_1p", seed=5, N=3000)
+    plan = se.Plan(1, 1.0, spec["xi"], spec["M"], spec["P"], "pkb", dtype=torch.float32)
+    F, phi, _ = _run(plan, x, q)
+    pa, ga = E.fourier_xi_route(1, x, q, 1.0, spec["xi"])
+    assert _rel(phi, pa) < 1e-5
+    assert _rel(F, -q[:, None] * ga) < 1e-5
