@@ -12,6 +12,12 @@ plain array code in the order of Alg. 4:
   4. IFFT / AIFT (Alg. 2, truncating to M~ in each free direction);
   5. gathering, Eq. (complete_integral) by the trapezoidal rule, and its
      gradient, Eq. (force-method-1).
+Forces by method 2 of Sec. 7.2: the scaling of step 3 is multiplied by i k_a
+for each direction a, steps 4-5 run once per direction, and the gathering uses
+W itself.  At the Nyquist index of an even-length transform the factor i k_a
+is set to zero: it is the odd part of a real signal that the real-valued
+inverse transform cannot represent (taking the real part of the complex
+inverse transform removes exactly this term).
 
 Discrete scaling (derived from Def. 1 with the trapezoidal rule; the paper
 does not print it): with an unnormalised forward DFT and a 1/n inverse over
@@ -33,6 +39,15 @@ from scipy.special import j0, j1
 
 from . import params as prm
 from .windows import Window
+
+
+def ik_factor(n: int, d: float):
+    """i k for the n-point DFT with spacing d: k = 2 pi m / (n d) at signed index m,
+    zero at the Nyquist index m = -n/2 of an even n (method 2 of Sec. 7.2)."""
+    k = 2.0 * np.pi * np.fft.fftfreq(n, d=d)
+    if n % 2 == 0:
+        k[n // 2] = 0.0
+    return 1j * k
 
 
 def green(D: int, R: float, kper2, kap):
@@ -152,14 +167,18 @@ class SEOracle:
         what = kvecs_hat * kap_hats
         return np.exp(-tot / (4.0 * xi * xi)) / what ** 2 * green(self.D, self.g["R"], kper2, kap)
 
-    def convolve(self, H):
-        """Steps 2-4 of Alg. 4: returns H~ on the same grid as H."""
+    def convolve(self, H, deriv=None):
+        """Steps 2-4 of Alg. 4: returns H~ on the same grid as H.  With deriv = a
+        (0, 1, 2) the scaling also multiplies by i k_a (method 2 of Sec. 7.2),
+        which gives the derivative of H~ along direction a."""
         D, h, M, Mt = self.D, self.h, self.M, self.Mt
         hat = self.win.hat
         if D == 3:
             k = 2.0 * np.pi * np.fft.fftfreq(M, d=h)
             kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
             sig = self._sigma(kx ** 2 + ky ** 2 + kz ** 2, hat(kx) * hat(ky) * hat(kz), 0.0, 1.0)
+            if deriv is not None:
+                sig = sig * self._ik_along(deriv, [M, M, M])
             return np.fft.ifftn(sig * np.fft.fftn(H)).real
         if D == 0:
             n2 = 2 * Mt
@@ -169,8 +188,17 @@ class SEOracle:
             kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
             sig = np.exp(-(kx ** 2 + ky ** 2 + kz ** 2) / (4.0 * self.xi ** 2)) \
                 / (hat(kx) * hat(ky) * hat(kz)) ** 2 * self.GR
+            if deriv is not None:
+                sig = sig * self._ik_along(deriv, [n2, n2, n2])
             return np.fft.ifftn(sig * np.fft.fftn(Hp)).real[:Mt, :Mt, :Mt]
-        return self._aft_scale_aift(H)
+        return self._aft_scale_aift(H, deriv)
+
+    def _ik_along(self, a, shape):
+        """i k_a on a transform grid of the given per-axis lengths (spacing h)."""
+        f = ik_factor(shape[a], self.h)
+        sh = [1, 1, 1]
+        sh[a] = shape[a]
+        return f.reshape(sh)
 
     def _classes(self):
         """Periodic-mode classes of Sec. 3.4: zero mode, I (Eq. I: a box
@@ -185,8 +213,8 @@ class SEOracle:
         outer = ~zero & ~inner
         return [(zero, self.g["s0Mt"]), (inner, self.g["sMt"]), (outer, self.Mt)]
 
-    def _aft_scale_aift(self, H):
-        """Alg. 1 (AFT), scaling, Alg. 2 (AIFT) for D = 1, 2."""
+    def _aft_scale_aift(self, H, deriv=None):
+        """Alg. 1 (AFT), scaling, Alg. 2 (AIFT) for D = 1, 2; deriv as in convolve."""
         D, h, M, Mt = self.D, self.h, self.M, self.Mt
         hat = self.win.hat
         per_axes = tuple(range(D))
@@ -217,6 +245,14 @@ class SEOracle:
             kper2 = kper2_all[mask].reshape((-1,) + (1,) * free_axes_n)
             khat = khat_all[mask].reshape((-1,) + (1,) * free_axes_n)
             sig = self._sigma(kper2, khat, kap, kaph)
+            if deriv is not None and deriv < D:                  # periodic direction
+                ikp = ik_factor(M, h)
+                ika = np.meshgrid(*([ikp if ax == deriv else np.ones(M) for ax in range(D)]), indexing="ij")
+                sig = sig * np.prod(ika, axis=0)[mask].reshape((-1,) + (1,) * free_axes_n)
+            elif deriv is not None:                              # free direction deriv - D of the class grid
+                shp = [1] * (1 + free_axes_n)
+                shp[1 + deriv - D] = nf
+                sig = sig * ik_factor(nf, h).reshape(shp)
             back = np.fft.ifftn(sig * Fk, axes=fax)               # Alg. 2 steps 1-3
             out[mask] = back[sl]                                 # truncate to M~, merge (step 4)
         return np.fft.ifftn(out, axes=per_axes).real             # Alg. 2 step 5
@@ -245,10 +281,19 @@ class SEOracle:
             g *= scale
         return phi, g
 
-    def potential(self, x, q, xt=None, grad: bool = False):
+    def potential(self, x, q, xt=None, grad: bool = False, force_method: int = 1):
         """phi~^{DP,F} (Eq. fourier_space_ewald) at the targets (default: the
-        sources) and, with grad=True, its gradient with respect to the target."""
+        sources) and, with grad=True, its gradient with respect to the target:
+        method 1 (Eq. force-method-1, W' in the gathering) or method 2 of
+        Sec. 7.2 (i k in the scaling, one inverse transform and one gathering
+        with W per direction)."""
         H = self.grid_charges(x, q)
         Ht = self.convolve(H)
-        return self.gather(Ht, x if xt is None else xt, grad)
-
+        xt = x if xt is None else xt
+        if not grad or force_method == 1:
+            return self.gather(Ht, xt, grad)
+        if force_method != 2:
+            raise ValueError("force_method is 1 or 2")
+        phi, _ = self.gather(Ht, xt)
+        g = np.stack([self.gather(self.convolve(H, deriv=a), xt)[0] for a in range(3)], axis=1)
+        return phi, g

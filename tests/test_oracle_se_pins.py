@@ -231,3 +231,65 @@ def test_se_oracle_linear_and_translation_covariant_3p():
     p0, _ = o.potential(x, q)
     p1, _ = o.potential((x + 5 * o.h) % 1.0, q)
     assert np.allclose(p0, p1, rtol=1e-12, atol=1e-12 * np.abs(p0).max())
+
+
+# ------------------------------------------------------ forces by method 2 (Sec. 7.2)
+
+def test_ik_factor_differentiates_pure_modes():
+    """i k on an n-point grid: d/dx of sin(2 pi m x / L) is (2 pi m / L) cos(2 pi m x / L)
+    for |m| < n/2; the Nyquist mode (sampled as cos(pi j)) has no derivative."""
+    n, L = 12, 0.75
+    d = L / n
+    xs = np.arange(n) * d
+    for m in range(1, n // 2):
+        f = np.sin(2 * np.pi * m * xs / L)
+        df = np.fft.ifft(S.ik_factor(n, d) * np.fft.fft(f))
+        np.testing.assert_allclose(df.real, 2 * np.pi * m / L * np.cos(2 * np.pi * m * xs / L), atol=1e-12)
+        assert np.max(np.abs(df.imag)) < 1e-12
+    nyq = np.cos(np.pi * np.arange(n))
+    assert np.max(np.abs(np.fft.ifft(S.ik_factor(n, d) * np.fft.fft(nyq)))) < 1e-14
+
+
+@pytest.mark.parametrize("D", [3, 2, 1, 0])
+def test_method2_force_matches_continuum(D):
+    """Method 2 (i k in the scaling) against oracle A's analytic gradients."""
+    x, q = _system(N=80, seed=5)
+    o = S.SEOracle(D, 1.0, 4.0, 32, 16, "pkb")
+    _, g2 = o.potential(x, q, grad=True, force_method=2)
+    _, ga = E.fourier(D, x, q, 1.0, 4.0)
+    assert _rel(g2, ga) < (1e-6 if D == 0 else 1e-9)
+
+
+@pytest.mark.parametrize("D", [3, 2, 1, 0])
+def test_method2_conserves_momentum(D):
+    """With the same window for gridding and gathering and an odd, purely
+    imaginary multiplier, sum_m F_m = -sum_j H_j (dH~)_j vanishes: the operator
+    of i k sigma is antisymmetric.  Method 1 has no such identity."""
+    x, q = _system(N=100, seed=6)
+    o = S.SEOracle(D, 1.0, 6.0, 24, 6, "pkb")
+    _, g2 = o.potential(x, q, grad=True, force_method=2)
+    _, g1 = o.potential(x, q, grad=True, force_method=1)
+    F2, F1 = -q[:, None] * g2, -q[:, None] * g1
+    assert np.max(np.abs(F2.sum(axis=0))) < 1e-13 * np.abs(F2).sum()
+    assert np.max(np.abs(F1.sum(axis=0))) > 1e-9 * np.abs(F1).sum()
+
+
+def test_method2_error_tracks_the_potential_and_method1_needs_two_more_points():
+    """Sec. 7.2 (Fig. force, 3P, PKB, xi = 8, M = 64): method 2 has the error
+    curve of the potential; method 1 is offset and needs P + 2 to reach the
+    error of method 2 at P."""
+    x, q = _system(N=200, seed=2)
+    _, ga = E.fourier(3, x, q, 1.0, 8.0)
+    pa, _ = E.fourier(3, x, q, 1.0, 8.0)
+    err = {}
+    for P in (4, 6, 8, 10):
+        o = S.SEOracle(3, 1.0, 8.0, 64, P, "pkb")
+        phi, g1 = o.potential(x, q, grad=True, force_method=1)
+        _, g2 = o.potential(x, q, grad=True, force_method=2)
+        err[P] = (_rel(phi, pa), _rel(g1, ga), _rel(g2, ga))
+    for P in (4, 6, 8, 10):
+        ephi, e1, e2 = err[P]
+        assert e2 < 2.0 * ephi and ephi < 2.0 * e2
+        assert e1 > 10.0 * e2
+    for P in (4, 6, 8):
+        assert err[P + 2][1] < err[P][2]
