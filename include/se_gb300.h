@@ -89,6 +89,11 @@ typedef struct {
     int    gather_mode; /* [<= 0] gathering kernel: 1 tile block staged in shared memory,
                            `split` CTAs per tile; 2 direct reads of the grid */
     int    split;       /* [<= 0] CTAs per tile for spread_mode 2 / gather_mode 1 (1..8) */
+    int    force_method; /* [<= 0 -> 1] how se_force differentiates (Sec. 7.2): 1 gathers with
+                           the window's derivative, Eq. (force-method-1); 2 multiplies the
+                           scaling by i k per direction and runs the inverse transform and a
+                           gathering with W three more times (the plan then holds three more
+                           spectra and grids).  se_potential and se_vjp are unaffected. */
 } se_opts;
 
 /* Derived parameters of a plan (read-only report). */
@@ -141,9 +146,12 @@ se_status se_plan_check(se_plan_t plan);
 se_status se_potential(se_plan_t plan, int64_t N, const void *x, const void *q, void *phi,
                        unsigned flags);
 
-/* Fourier-space forces F_m = -q_m grad phi~(x_m) (Sec. 7.2, method 1,
- * Eq. force-method-1: one inverse transform, gradient gather with the exact
- * derivative of the window).  F [N][3] out; phi [N] out if non-NULL;
+/* Fourier-space forces F_m = -q_m grad phi~(x_m) (Sec. 7.2).  Method 1 (the
+ * default, Eq. force-method-1): one inverse transform, gradient gather with the
+ * exact derivative of the window.  Method 2 (se_opts.force_method = 2): the
+ * scaled spectrum times i k_a for a = x, y, z, four inverse transforms, and a
+ * gathering of the four grids with W; i k_a is zero at the Nyquist index of an
+ * even-length transform.  F [N][3] out; phi [N] out if non-NULL;
  * energy (DEVICE pointer to one double, may be NULL) receives
  * E = 1/2 sum_m q_m phi_m accumulated in FP64 (with SE_ADD_SELF the self
  * term is part of phi and of E).  Flags and errors as se_potential. */

@@ -37,12 +37,14 @@ class Plan:
     parameter; M: grid intervals per periodic direction; P: window support;
     window: "pkb" or "gaussian"; dtype: torch.float32 or torch.float64.
     Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
-    shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants).
+    shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants),
+    force_method (1: gradient of the window, 2: i k in the scaling; Sec. 7.2).
     """
 
     def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
                  dtype=torch.float32, device=None, lam=None, s0=None, s_mt=None, n_l=None, nu=None,
-                 shape=None, aft_eps=None, tile=None, spread_mode=None, gather_mode=None, split=None):
+                 shape=None, aft_eps=None, tile=None, spread_mode=None, gather_mode=None, split=None,
+                 force_method=None):
         self._lib = nat.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if self.device.type != "cuda":
@@ -62,6 +64,7 @@ class Plan:
         if spread_mode is not None: o.spread_mode = spread_mode
         if gather_mode is not None: o.gather_mode = gather_mode
         if split is not None: o.split = split
+        if force_method is not None: o.force_method = force_method
         box = (ctypes.c_double * 3)(L, L, L)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("s0", ctypes.c_double), ("s_mt", ctypes.c_int),
                 ("n_l", ctypes.c_int), ("nu", ctypes.c_int), ("shape", ctypes.c_double),
                 ("aft_eps", ctypes.c_double), ("tile", ctypes.c_int), ("spread_mode", ctypes.c_int),
-                ("gather_mode", ctypes.c_int), ("split", ctypes.c_int)]
+                ("gather_mode", ctypes.c_int), ("split", ctypes.c_int),
+                ("force_method", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

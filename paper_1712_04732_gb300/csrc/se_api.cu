@@ -92,8 +92,14 @@ static se_status run(se_plan_s *p, int64_t N, const void *x, const void *q, void
     prof_mark(p, 0);
     if ((st = Ops<T>::bin(p, N, dx, dq)) != SE_OK) return st;
     if ((st = Ops<T>::spread(p, N, nullptr, p->grid_in)) != SE_OK) return st;
-    if ((st = Ops<T>::convolve(p, p->grid_in, p->grid_out)) != SE_OK) return st;
-    if ((st = Ops<T>::gather(p, N, dq, dphi, dF, den, flags & SE_ADD_SELF, grad)) != SE_OK) return st;
+    if (grad && p->force_method == 2) {
+        // Sec. 7.2, method 2: i k in the scaling, four inverse transforms, gathering with W
+        if ((st = Ops<T>::convolve_ik(p, p->grid_in)) != SE_OK) return st;
+        if ((st = Ops<T>::gather_m2(p, N, dphi, dF, den, flags & SE_ADD_SELF)) != SE_OK) return st;
+    } else {
+        if ((st = Ops<T>::convolve(p, p->grid_in, p->grid_out)) != SE_OK) return st;
+        if ((st = Ops<T>::gather(p, N, dq, dphi, dF, den, flags & SE_ADD_SELF, grad)) != SE_OK) return st;
+    }
     if (p->prof) {
         if ((e = cudaEventSynchronize(p->ev[SE_N_STAGES])) != cudaSuccess) return cuda_fail(e, "profile sync");
         for (int i = 0; i < SE_N_STAGES; ++i) {
@@ -169,6 +175,7 @@ void se_opts_default(se_opts *o)
     o->spread_mode = 0;
     o->gather_mode = 0;
     o->split = 0;
+    o->force_method = 0;
 }
 
 se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P, se_window w,
@@ -204,6 +211,8 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
         return fail(SE_EINVAL, "spread_mode must be 0..3, gather_mode 0..2, split 0..8");
     }
     if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
+    if (o.force_method > 2) { delete p; return fail(SE_EINVAL, "force_method must be 1 or 2 (Sec. 7.2)"); }
+    p->force_method = o.force_method == 2 ? 2 : 1;
     // Sec. 6: shape parameters and PKB degree
     p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
     p->nu = o.nu > 0 ? o.nu : std::min(P / 2 + 2, 9);

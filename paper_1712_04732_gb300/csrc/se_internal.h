@@ -64,6 +64,18 @@ struct ScaleBox {
     int nl;
 };
 
+// Factor i k_a of method 2 (Sec. 7.2) for each element of a spectrum buffer of
+// n0 x n1 x n2 complex values (i0 fastest): k_a = k[a][i_dim[a]] with i_dim the
+// element's index along box dimension dim[a]; dim[a] < 0 means k_a = 0 on the
+// whole buffer.  The three products go to dst + a * stride.
+template <typename T>
+struct IkBox {
+    int n0, n1, n2;
+    const T *k[3];
+    int dim[3];
+    int64_t stride;
+};
+
 }  // namespace se
 
 struct se_plan_s {
@@ -79,6 +91,7 @@ struct se_plan_s {
     int tile_pref = 0;
     int spread_warps = 8;                // warps (private blocks) per gridding CTA (spread_mode 3)
     int spread_mode = 0, gather_mode = 0, split = 0;   // kernel variants (0: chosen per call)
+    int force_method = 1;                // Sec. 7.2: 1 derivative of the window, 2 i k in the scaling
     cudaStream_t stream = nullptr;
 
     // ---- device memory ----
@@ -132,6 +145,10 @@ struct se_plan_s {
     int64_t prof_calls = 0;
     int64_t launches = 0;
     void *real_ws = nullptr;             // workspace of the real-space sum (se_real.cu)
+    // method 2 forces: the three i k_a copies of spec / U / Z and the three gradient grids
+    void *spec_d = nullptr, *U_d = nullptr, *Z_d = nullptr, *grid_d = nullptr;
+    se::IkBox<float> ib_spec_f{}, ib_U_f{}, ib_Z_f{};
+    se::IkBox<double> ib_spec_d{}, ib_U_d{}, ib_Z_d{};
 };
 
 namespace se {
@@ -170,6 +187,10 @@ struct Ops {
     static se_status spread(se_plan_s *p, int64_t N, const T *g, void *dst);
     // forward transform, scaling and inverse transform: grid_in -> grid_out
     static se_status convolve(se_plan_s *p, void *gin, void *gout);
+    // method 2 (Sec. 7.2): grid_in -> grid_out and the three gradient grids grid_d
+    static se_status convolve_ik(se_plan_s *p, void *gin);
+    // gather phi and the three gradient grids at the sorted particles (method 2)
+    static se_status gather_m2(se_plan_s *p, int64_t N, T *phi, T *F, double *energy, bool add_self);
     // gather phi (and grad) from grid_out at the sorted particles
     static se_status gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, double *energy,
                             bool add_self, bool grad);

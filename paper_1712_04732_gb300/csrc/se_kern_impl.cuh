@@ -242,69 +242,110 @@ template <typename T> static const ScaleBox<T> &sb_U(const se_plan_s *p);
 template <> const ScaleBox<float> &sb_U<float>(const se_plan_s *p) { return p->sb_U_f; }
 template <> const ScaleBox<double> &sb_U<double>(const se_plan_s *p) { return p->sb_U_d; }
 
+template <typename T> static const IkBox<T> &ib_spec(const se_plan_s *p);
+template <> const IkBox<float> &ib_spec<float>(const se_plan_s *p) { return p->ib_spec_f; }
+template <> const IkBox<double> &ib_spec<double>(const se_plan_s *p) { return p->ib_spec_d; }
+template <typename T> static const IkBox<T> &ib_U(const se_plan_s *p);
+template <> const IkBox<float> &ib_U<float>(const se_plan_s *p) { return p->ib_U_f; }
+template <> const IkBox<double> &ib_U<double>(const se_plan_s *p) { return p->ib_U_d; }
+template <typename T> static const IkBox<T> &ib_Z(const se_plan_s *p);
+template <> const IkBox<float> &ib_Z<float>(const se_plan_s *p) { return p->ib_Z_f; }
+template <> const IkBox<double> &ib_Z<double>(const se_plan_s *p) { return p->ib_Z_d; }
+
+// Alg. 4 step 2: forward FFT (D = 3, 0) or AFT (Alg. 1, D = 1, 2) of gin into
+// spec (and U, Z).
 template <typename T>
-se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
+static se_status forward(se_plan_s *p, void *gin)
 {
     using C = typename Cplx<T>::type;
     C *spec = reinterpret_cast<C *>(p->spec);
     cufftResult r;
     if (p->D == 0) {
-        // forward: 2D R2C of the M~ non-zero z-planes into the zero-padded buffer,
-        // z-transform into spec; scaling; inverse z-transform in place, 2D C2R of
-        // the M~ z-planes that are read back
+        // 2D R2C of the M~ non-zero z-planes into the zero-padded buffer, z-transform into spec
         C *pad = reinterpret_cast<C *>(p->spec_pad);
         if ((r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), pad)) != CUFFT_SUCCESS) return cufft_fail(r, "forward xy");
         if ((r = fft_c2c_oop(p->free_main, pad, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "forward z");
-        prof_mark(p, 4);
-        k_scale_tab<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(
-            int64_t(p->spec_elems), reinterpret_cast<const T *>(p->sigma_tab), spec);
-        SE_LAUNCH_CHECK("scale");
-        prof_mark(p, 5);
-        if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse z");
-        if ((r = fft_c2r(p->inv, spec, reinterpret_cast<T *>(gout))) != CUFFT_SUCCESS) return cufft_fail(r, "inverse xy");
-        prof_mark(p, 6);
         return SE_OK;
     }
-    r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec);
-    if (r != CUFFT_SUCCESS) return cufft_fail(r, "forward transform");
-    if (p->D == 3) prof_mark(p, 4);
-    if (p->D == 3) {
-        const ScaleBox<T> &sb = sb_spec<T>(p);
-        k_scale_box<T><<<blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256), 256, 0, p->stream>>>(sb, spec);
-        SE_LAUNCH_CHECK("scale");
-        prof_mark(p, 5);
+    if ((r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec)) != CUFFT_SUCCESS) return cufft_fail(r, "forward transform");
+    if (p->D == 3) return SE_OK;
+    C *U = reinterpret_cast<C *>(p->U);
+    C *Z = reinterpret_cast<C *>(p->Z);
+    const int row = p->M / 2 + 1;
+    // Alg. 1 steps 2-3: zero mode and set I into their padded buffers
+    if (p->D == 2) {
+        const int64_t n = int64_t(p->nI) * p->sMt + p->s0Mt;
+        k_pad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, p->s0Mt, row,
+                                                               int64_t(p->M) * row, spec, U, Z);
     } else {
-        C *U = reinterpret_cast<C *>(p->U);
-        C *Z = reinterpret_cast<C *>(p->Z);
+        const int64_t n = int64_t(p->nl) * p->sMt * p->sMt + int64_t(p->s0Mt) * p->s0Mt;
+        k_pad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
+    }
+    SE_LAUNCH_CHECK("pad");
+    // Alg. 1 steps 2-4: free-direction transforms of every class
+    if ((r = fft_c2c(p->free_main, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "free fwd");
+    if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "I fwd");
+    if ((r = fft_c2c(p->free_Z, Z, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "zero fwd");
+    return SE_OK;
+}
+
+// Alg. 4 step 3, Eq. (scale), in place on spec (and U, Z).  With ik, also the
+// three i k_a copies of method 2 (Sec. 7.2) into spec_d (and U_d, Z_d).
+template <typename T>
+static se_status scale(se_plan_s *p, bool ik)
+{
+    using C = typename Cplx<T>::type;
+    C *spec = reinterpret_cast<C *>(p->spec);
+    const T *tab = reinterpret_cast<const T *>(p->sigma_tab);
+    if (p->D == 0) {
+        if (ik)
+            k_scale_tab_ik<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(
+                tab, ib_spec<T>(p), spec, reinterpret_cast<C *>(p->spec_d));
+        else
+            k_scale_tab<T><<<blocks_for(p->spec_elems, 256), 256, 0, p->stream>>>(int64_t(p->spec_elems), tab, spec);
+        SE_LAUNCH_CHECK("scale");
+        return SE_OK;
+    }
+    const ScaleBox<T> &sb = sb_spec<T>(p);
+    const unsigned nb = blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256);
+    if (ik) k_scale_box_ik<T><<<nb, 256, 0, p->stream>>>(sb, ib_spec<T>(p), spec, reinterpret_cast<C *>(p->spec_d));
+    else k_scale_box<T><<<nb, 256, 0, p->stream>>>(sb, spec);
+    SE_LAUNCH_CHECK("scale");
+    if (p->D == 3) return SE_OK;
+    // the classes I and zero mode of the AFT (D = 1, 2)
+    C *U = reinterpret_cast<C *>(p->U);
+    C *Z = reinterpret_cast<C *>(p->Z);
+    if (p->have_free_I) {
+        const ScaleBox<T> &su = sb_U<T>(p);
+        const unsigned nu = blocks_for(int64_t(su.n0) * su.n1 * su.n2, 256);
+        if (ik) k_scale_box_ik<T><<<nu, 256, 0, p->stream>>>(su, ib_U<T>(p), U, reinterpret_cast<C *>(p->U_d));
+        else k_scale_box<T><<<nu, 256, 0, p->stream>>>(su, U);
+        SE_LAUNCH_CHECK("scale I");
+    }
+    if (ik)
+        k_scale_tab_ik<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(tab, ib_Z<T>(p), Z,
+                                                                             reinterpret_cast<C *>(p->Z_d));
+    else
+        k_scale_tab<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(int64_t(p->Z_elems), tab, Z);
+    SE_LAUNCH_CHECK("scale 0");
+    return SE_OK;
+}
+
+// Alg. 4 step 4: inverse FFT (D = 3, 0) or AIFT (Alg. 2, D = 1, 2) of the
+// spectrum in spec (U, Z) into the real grid gout.  The spectrum is consumed.
+template <typename T>
+static se_status inverse(se_plan_s *p, typename Cplx<T>::type *spec, typename Cplx<T>::type *U,
+                         typename Cplx<T>::type *Z, T *gout)
+{
+    cufftResult r;
+    if (p->D == 0) {
+        // inverse z-transform in place, 2D C2R of the M~ z-planes that are read back
+        if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse z");
+        if ((r = fft_c2r(p->inv, spec, gout)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse xy");
+        return SE_OK;
+    }
+    if (p->D != 3) {
         const int row = p->M / 2 + 1;
-        // Alg. 1 steps 2-3: zero mode and set I into their padded buffers
-        if (p->D == 2) {
-            const int64_t n = int64_t(p->nI) * p->sMt + p->s0Mt;
-            k_pad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, p->s0Mt, row,
-                                                                   int64_t(p->M) * row, spec, U, Z);
-        } else {
-            const int64_t n = int64_t(p->nl) * p->sMt * p->sMt + int64_t(p->s0Mt) * p->s0Mt;
-            k_pad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
-        }
-        SE_LAUNCH_CHECK("pad");
-        // Alg. 1 steps 2-4: free-direction transforms of every class
-        if ((r = fft_c2c(p->free_main, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "free fwd");
-        if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "I fwd");
-        if ((r = fft_c2c(p->free_Z, Z, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "zero fwd");
-        prof_mark(p, 4);
-        // Eq. (scale) per class
-        const ScaleBox<T> &sb = sb_spec<T>(p);
-        k_scale_box<T><<<blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256), 256, 0, p->stream>>>(sb, spec);
-        SE_LAUNCH_CHECK("scale J");
-        if (p->have_free_I) {
-            const ScaleBox<T> &su = sb_U<T>(p);
-            k_scale_box<T><<<blocks_for(int64_t(su.n0) * su.n1 * su.n2, 256), 256, 0, p->stream>>>(su, U);
-            SE_LAUNCH_CHECK("scale I");
-        }
-        k_scale_tab<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(
-            int64_t(p->Z_elems), reinterpret_cast<const T *>(p->sigma_tab), Z);
-        SE_LAUNCH_CHECK("scale 0");
-        prof_mark(p, 5);
         // Alg. 2 steps 1-3
         if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "free inv");
         if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "I inv");
@@ -320,9 +361,70 @@ se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
         }
         SE_LAUNCH_CHECK("unpad");
     }
-    r = fft_c2r(p->inv, spec, reinterpret_cast<T *>(gout));
-    if (r != CUFFT_SUCCESS) return cufft_fail(r, "inverse transform");
+    if ((r = fft_c2r(p->inv, spec, gout)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse transform");
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
+{
+    using C = typename Cplx<T>::type;
+    se_status st;
+    if ((st = forward<T>(p, gin)) != SE_OK) return st;
+    prof_mark(p, 4);
+    if ((st = scale<T>(p, false)) != SE_OK) return st;
+    prof_mark(p, 5);
+    if ((st = inverse<T>(p, reinterpret_cast<C *>(p->spec), reinterpret_cast<C *>(p->U), reinterpret_cast<C *>(p->Z),
+                         reinterpret_cast<T *>(gout))) != SE_OK)
+        return st;
     prof_mark(p, 6);
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::convolve_ik(se_plan_s *p, void *gin)
+{
+    using C = typename Cplx<T>::type;
+    se_status st;
+    if (!p->spec_d || !p->grid_d) return fail(SE_EINVAL, "the plan was not created with force_method = 2");
+    if ((st = forward<T>(p, gin)) != SE_OK) return st;
+    prof_mark(p, 4);
+    if ((st = scale<T>(p, true)) != SE_OK) return st;
+    prof_mark(p, 5);
+    if ((st = inverse<T>(p, reinterpret_cast<C *>(p->spec), reinterpret_cast<C *>(p->U), reinterpret_cast<C *>(p->Z),
+                         reinterpret_cast<T *>(p->grid_out))) != SE_OK)
+        return st;
+    for (int a = 0; a < 3; ++a) {
+        C *sd = reinterpret_cast<C *>(p->spec_d) + a * p->spec_elems;
+        C *ud = p->U_d ? reinterpret_cast<C *>(p->U_d) + a * p->U_elems : nullptr;
+        C *zd = p->Z_d ? reinterpret_cast<C *>(p->Z_d) + a * p->Z_elems : nullptr;
+        T *gd = reinterpret_cast<T *>(p->grid_d) + a * p->grid_out_elems;
+        if ((st = inverse<T>(p, sd, ud, zd, gd)) != SE_OK) return st;
+    }
+    prof_mark(p, 6);
+    return SE_OK;
+}
+
+template <typename T>
+se_status Ops<T>::gather_m2(se_plan_s *p, int64_t N, T *phi, T *F, double *energy, bool add_self)
+{
+    WindowArgs<T> wa = window_args<T>(p);
+    const auto *fq = reinterpret_cast<const typename Vec4<T>::type *>(p->prt.frac_q);
+    const T self = add_self ? T(-2.0 * p->xi / std::sqrt(M_PI)) : T(0);
+    double *part = energy ? p->tile_part : nullptr;
+    const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+    SE_DISPATCH_P(p->P, nu, {
+        constexpr int G = LaneMap<PP>::G;
+        const int64_t per_cta = int64_t(kThreads / 32) * G;
+        const unsigned nb = unsigned((N + per_cta - 1) / per_cta);
+        k_gather_flat_m2<T, PP, NN><<<nb, kThreads, 0, p->stream>>>(
+            N, p->tg, fq, p->prt.idx_anc, wa, reinterpret_cast<const T *>(p->grid_out),
+            reinterpret_cast<const T *>(p->grid_d), int64_t(p->grid_out_elems), p->gout, phi, F, part, energy,
+            p->counters + 1, self);
+    });
+    SE_LAUNCH_CHECK("gather m2");
+    prof_mark(p, 7);
+    prof_mark(p, 8);
     return SE_OK;
 }
 

@@ -377,28 +377,48 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     }
     __syncthreads();
 
-    for (int p = beg + rank * nw + warp; p < end; p += CL * nw) {
-        const typename Vec4<T>::type r = fq[p];
-        const int4 a = ia[p];
-        const T qv = g ? g[a.x] : r.w;
-        for (int j = lane; j < 3 * P; j += 32) {
-            const int ax = j / P, k = j - ax * P;
-            w[j] = win_val_smem<T, P>(wa.kind, wa.nu, wa.alpha, sc, ax == 0 ? r.x : (ax == 1 ? r.y : r.z), k);
+    // The warp's particles are p0, p0 + stride, ...; lane i loads the i-th of
+    // the next 32 of them, so one round of global loads serves 32 particles,
+    // which the warp then adds one at a time (coordinates, charge and block
+    // offset broadcast by shuffles).
+    const int stride = CL * nw;
+    for (int p0 = beg + rank * nw + warp; p0 < end; p0 += 32 * stride) {
+        const int pl = p0 + lane * stride;
+        T lx = T(0), ly = T(0), lz = T(0), lq = T(0);
+        int lb = 0;
+        if (pl < end) {
+            const typename Vec4<T>::type r = fq[pl];
+            const int4 a = ia[pl];
+            lx = r.x;
+            ly = r.y;
+            lz = r.z;
+            lq = g ? g[a.x] : r.w;
+            lb = block_base(tg, o, a);
         }
-        __syncwarp();
-        T wxy[NE];
+        const int cnt = min(32, (end - p0 + stride - 1) / stride);
+        for (int i = 0; i < cnt; ++i) {
+            const T rx = __shfl_sync(0xffffffffu, lx, i), ry = __shfl_sync(0xffffffffu, ly, i);
+            const T rz = __shfl_sync(0xffffffffu, lz, i), qv = __shfl_sync(0xffffffffu, lq, i);
+            const int bo = __shfl_sync(0xffffffffu, lb, i);
+            for (int j = lane; j < 3 * P; j += 32) {
+                const int ax = j / P, k = j - ax * P;
+                w[j] = win_val_smem<T, P>(wa.kind, wa.nu, wa.alpha, sc, ax == 0 ? rx : (ax == 1 ? ry : rz), k);
+            }
+            __syncwarp();
+            T wxy[NE];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) wxy[e] = qv * w[pdx[e]] * w[P + pdy[e]];
-        T *base = blk + block_base(tg, o, a);
+            for (int e = 0; e < NE; ++e) wxy[e] = qv * w[pdx[e]] * w[P + pdy[e]];
+            T *base = blk + bo;
 #pragma unroll
-        for (int dz = 0; dz < P; ++dz) {
-            const T wz = w[2 * P + dz];
-            T *row = base + dz * plane;
+            for (int dz = 0; dz < P; ++dz) {
+                const T wz = w[2 * P + dz];
+                T *row = base + dz * plane;
 #pragma unroll
-            for (int e = 0; e < NE; ++e)
-                if (pv[e]) atomicAdd(row + poff[e], wxy[e] * wz);
+                for (int e = 0; e < NE; ++e)
+                    if (pv[e]) atomicAdd(row + poff[e], wxy[e] * wz);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     cluster.sync();                                       // every copy complete and visible to the cluster
     T *dst = scratch + size_t(tile) * tg.blk;
@@ -524,6 +544,59 @@ __global__ void k_scale_tab(int64_t n, const T *__restrict__ tab, typename Cplx<
     v.x *= s;
     v.y *= s;
     data[i] = v;
+}
+
+// Method 2 of Sec. 7.2: after scaling element i to v, write i k_a v for a = 0..2
+// into the three derivative copies.
+template <typename T>
+__device__ __forceinline__ void ik_store(const IkBox<T> &ib, int64_t i, int i0, int i1, int i2,
+                                         typename Cplx<T>::type v, typename Cplx<T>::type *__restrict__ dst)
+{
+    const int idx[3] = {i0, i1, i2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T k = ib.dim[a] < 0 ? T(0) : ib.k[a][idx[ib.dim[a]]];
+        typename Cplx<T>::type d;
+        d.x = -k * v.y;
+        d.y = k * v.x;
+        dst[a * ib.stride + i] = d;
+    }
+}
+
+template <typename T>
+__global__ void k_scale_box_ik(ScaleBox<T> sb, IkBox<T> ib, typename Cplx<T>::type *__restrict__ data,
+                               typename Cplx<T>::type *__restrict__ dst)
+{
+    const int64_t n = int64_t(sb.n0) * sb.n1 * sb.n2;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int i0 = int(i % sb.n0), i1 = int((i / sb.n0) % sb.n1), i2 = int(i / (int64_t(sb.n0) * sb.n1));
+    bool excl = false;
+    if (sb.excl == 1) excl = i0 <= sb.nl;
+    else if (sb.excl == 2) excl = i0 <= sb.nl && (i1 <= sb.nl || i1 >= sb.n1 - sb.nl);
+    const T den = sb.k0[i0] + sb.k1[i1] + sb.k2[i2];
+    T s = (excl || den == T(0)) ? T(0) : sb.norm * sb.f0[i0] * sb.f1[i1] * sb.f2[i2] / den;
+    typename Cplx<T>::type v = data[i];
+    v.x *= s;
+    v.y *= s;
+    data[i] = v;
+    ik_store(ib, i, i0, i1, i2, v, dst);
+}
+
+template <typename T>
+__global__ void k_scale_tab_ik(const T *__restrict__ tab, IkBox<T> ib, typename Cplx<T>::type *__restrict__ data,
+                               typename Cplx<T>::type *__restrict__ dst)
+{
+    const int64_t n = int64_t(ib.n0) * ib.n1 * ib.n2;
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int i0 = int(i % ib.n0), i1 = int((i / ib.n0) % ib.n1), i2 = int(i / (int64_t(ib.n0) * ib.n1));
+    const T s = tab[i];
+    typename Cplx<T>::type v = data[i];
+    v.x *= s;
+    v.y *= s;
+    data[i] = v;
+    ik_store(ib, i, i0, i1, i2, v, dst);
 }
 
 // ----------------------------------------------------------------- AFT padding
@@ -908,6 +981,94 @@ k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__
             double s = 0.0;
             for (int i = 0; i < nw; ++i) s += epart[i];
             part[blockIdx.x] = s;
+        }
+        finish_energy(part, gridDim.x, energy, done);
+    }
+}
+
+// Gathering for method 2 of Sec. 7.2: phi from H~ and the three components of
+// grad phi from the grids d_a H~ (grid + (1 + a) gstride), all with the window
+// W itself (the same lane layout as k_gather_flat).
+template <typename T, int P, int NU>
+__global__ void __launch_bounds__(kThreads)
+k_gather_flat_m2(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__ fq, const int4 *__restrict__ ia,
+                 WindowArgs<T> wa, const T *__restrict__ grid, const T *__restrict__ gridd, int64_t gstride,
+                 GridView v, T *__restrict__ phi, T *__restrict__ F, double *__restrict__ part, double *energy,
+                 int *done, T self_coef)
+{
+    constexpr int G = LaneMap<P>::G;
+    __shared__ T wbs[kThreads / 32][32 * 3];
+    __shared__ double epart[kThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int grp = lane / P, dx = lane - grp * P;
+    const bool lane_on = grp < G;
+    LaneCoef<T, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+    T *w = &wbs[warp][(lane_on ? grp : 0) * 3 * P];
+    const int64_t p = (int64_t(blockIdx.x) * nw + warp) * G + grp;
+    const bool has = lane_on && p < N;
+    typename Vec4<T>::type r;
+    int4 a = make_int4(0, 0, 0, 0);
+    if (has) {
+        r = fq[p];
+        a = ia[p];
+        group_weights<T, P, NU, false>(wa, cf, r, dx, w);
+    }
+    __syncwarp();
+    T s[4] = {T(0), T(0), T(0), T(0)};
+    if (has) {
+        int g0 = a.y + dx;
+        if (g0 >= tg.n[0]) g0 -= tg.n[0];
+        int yo[P], zo[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            int y = a.z + j, z = a.w + j;
+            if (y >= tg.n[1]) y -= tg.n[1];
+            if (z >= tg.n[2]) z -= tg.n[2];
+            yo[j] = int(y * v.s1);
+            zo[j] = int(z * v.s2);
+        }
+        const T *cols[4] = {grid + g0, gridd + g0, gridd + gstride + g0, gridd + 2 * gstride + g0};
+#pragma unroll
+        for (int dz = 0; dz < P; ++dz) {
+            T t[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+            for (int dy = 0; dy < P; ++dy) {
+                const T wy = w[P + dy];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = fma(wy, __ldg(cols[c] + yo[dy] + zo[dz]), t[c]);
+            }
+            const T wz = w[2 * P + dz];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s[c] = fma(wz, t[c], s[c]);
+        }
+        const T wx = w[dx];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[c] *= wx;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s[c] = group_sum<T, P>(s[c], dx);
+    double esum = 0.0;
+    if (has && dx == 0) {
+        const T qv = r.w;
+        const T phv = s[0] + self_coef * qv;
+        const int64_t m = a.x;
+        if (phi) phi[m] = phv;
+        if (F) {
+            F[3 * m] = -qv * s[1];
+            F[3 * m + 1] = -qv * s[2];
+            F[3 * m + 2] = -qv * s[3];
+        }
+        esum = 0.5 * double(qv) * double(phv);
+    }
+    if (part) {
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if (lane == 0) epart[warp] = esum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < nw; ++i) t += epart[i];
+            part[blockIdx.x] = t;
         }
         finish_energy(part, gridDim.x, energy, done);
     }

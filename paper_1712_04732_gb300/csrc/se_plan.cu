@@ -156,6 +156,18 @@ static void axis_tables(const se_plan_s *p, int nf, std::vector<double> &f, std:
     }
 }
 
+// Signed k = 2 pi m / (nf h) of a transform of length nf (method 2 of Sec. 7.2),
+// zero at the Nyquist index m = -nf/2 of an even nf.
+static std::vector<double> ik_axis(const se_plan_s *p, int nf)
+{
+    std::vector<double> k(nf);
+    for (int m = 0; m < nf; ++m) {
+        const int ms = (m < (nf + 1) / 2) ? m : m - nf;
+        k[m] = (nf % 2 == 0 && m == nf / 2) ? 0.0 : 2.0 * M_PI * ms / (nf * p->h);
+    }
+    return k;
+}
+
 // ------------------------------------------------------------ Alg. 3 (D = 0), FP64 on the device
 
 __global__ void k_green0_samples(int ns, double dk, double R, cufftDoubleComplex *out)
@@ -362,6 +374,27 @@ static se_status build_tables(se_plan_s *p)
             o_kl = tb.add(kl);
         }
     }
+    // method 2 (Sec. 7.2): signed k per transform length and per I line / plane
+    const size_t o_dM = tb.add(ik_axis(p, M));
+    size_t o_dMt = 0, o_dsMt = 0, o_ds0Mt = 0, o_d2Mt = 0, o_dlx = 0, o_dly = 0;
+    if (D == 0) o_d2Mt = tb.add(ik_axis(p, 2 * Mt));
+    if (D == 1 || D == 2) {
+        o_dMt = tb.add(ik_axis(p, Mt));
+        if (p->nl > 0) o_dsMt = tb.add(ik_axis(p, p->sMt));
+        o_ds0Mt = tb.add(ik_axis(p, p->s0Mt));
+        const std::vector<double> kM = ik_axis(p, M);
+        std::vector<double> lx, ly;
+        if (D == 2) {
+            for (const int2 &l : lines) {
+                lx.push_back(kM[l.x]);
+                ly.push_back(kM[l.y]);
+            }
+        } else {
+            for (int pl = 0; pl < p->nl; ++pl) lx.push_back(kM[pl + 1]);
+        }
+        if (!lx.empty()) o_dlx = tb.add(lx);
+        if (!ly.empty()) o_dly = tb.add(ly);
+    }
     // upload the axis tables in the plan's precision
     std::vector<unsigned char> bytes;
     if (p->dtype == SE_F32) to_type<float>(tb.v, bytes); else to_type<double>(tb.v, bytes);
@@ -402,6 +435,36 @@ static se_status build_tables(se_plan_s *p)
     };
     if (p->dtype == SE_F32) { auto b = boxes(float()); p->sb_spec_f = b.first; p->sb_U_f = b.second; }
     else { auto b = boxes(double()); p->sb_spec_d = b.first; p->sb_U_d = b.second; }
+    // i k_a factors of method 2 on each spectrum buffer: (table offset, box dimension) per direction
+    auto ikbox = [&](auto tag, int n0, int n1, int n2, size_t s, size_t o0, int d0, size_t o1, int d1, size_t o2,
+                     int d2) {
+        using T = decltype(tag);
+        const T *base = reinterpret_cast<const T *>(p->tabs);
+        IkBox<T> b{};
+        b.n0 = n0; b.n1 = n1; b.n2 = n2;
+        b.k[0] = base + o0; b.k[1] = base + o1; b.k[2] = base + o2;
+        b.dim[0] = d0; b.dim[1] = d1; b.dim[2] = d2;
+        b.stride = int64_t(s);
+        return b;
+    };
+    auto ikboxes = [&](auto tag, IkBox<decltype(tag)> &spec, IkBox<decltype(tag)> &U, IkBox<decltype(tag)> &Z) {
+        const int sM = p->sMt, s0 = p->s0Mt;
+        if (D == 3) {
+            spec = ikbox(tag, row, M, M, p->spec_elems, o_dM, 0, o_dM, 1, o_dM, 2);
+        } else if (D == 0) {
+            spec = ikbox(tag, Mt + 1, 2 * Mt, 2 * Mt, p->spec_elems, o_d2Mt, 0, o_d2Mt, 1, o_d2Mt, 2);
+        } else if (D == 2) {
+            spec = ikbox(tag, row, M, Mt, p->spec_elems, o_dM, 0, o_dM, 1, o_dMt, 2);
+            if (p->nI > 0) U = ikbox(tag, sM, p->nI, 1, p->U_elems, o_dlx, 1, o_dly, 1, o_dsMt, 0);
+            Z = ikbox(tag, s0, 1, 1, p->Z_elems, 0, -1, 0, -1, o_ds0Mt, 0);
+        } else {
+            spec = ikbox(tag, row, Mt, Mt, p->spec_elems, o_dM, 0, o_dMt, 1, o_dMt, 2);
+            if (p->nl > 0) U = ikbox(tag, sM, sM, p->nl, p->U_elems, o_dlx, 2, o_dsMt, 0, o_dsMt, 1);
+            Z = ikbox(tag, s0, s0, 1, p->Z_elems, 0, -1, o_ds0Mt, 0, o_ds0Mt, 1);
+        }
+    };
+    if (p->dtype == SE_F32) ikboxes(float(), p->ib_spec_f, p->ib_U_f, p->ib_Z_f);
+    else ikboxes(double(), p->ib_spec_d, p->ib_U_d, p->ib_Z_d);
     if (D == 0) return precompute_free_space(p);
     return SE_OK;
 }
@@ -605,6 +668,13 @@ se_status plan_build(se_plan_s *p)
     if (p->U_elems && (st = dev_alloc(p, &p->U, p->U_elems * 2 * p->elem)) != SE_OK) return st;
     if (p->Z_elems && (st = dev_alloc(p, &p->Z, p->Z_elems * 2 * p->elem)) != SE_OK) return st;
     if (p->sigma_elems && (st = dev_alloc(p, &p->sigma_tab, p->sigma_elems * p->elem)) != SE_OK) return st;
+    if (p->force_method == 2) {
+        // three i k_a copies of every spectrum buffer and three gradient grids
+        if ((st = dev_alloc(p, &p->spec_d, 3 * p->spec_elems * 2 * p->elem)) != SE_OK) return st;
+        if (p->U_elems && (st = dev_alloc(p, &p->U_d, 3 * p->U_elems * 2 * p->elem)) != SE_OK) return st;
+        if (p->Z_elems && (st = dev_alloc(p, &p->Z_d, 3 * p->Z_elems * 2 * p->elem)) != SE_OK) return st;
+        if ((st = dev_alloc(p, &p->grid_d, 3 * p->grid_out_elems * p->elem)) != SE_OK) return st;
+    }
     if ((st = build_tables(p)) != SE_OK) return st;
     if ((st = make_plans(p)) != SE_OK) return st;
     if ((st = plan_set_fft_stream(p)) != SE_OK) return st;
@@ -670,7 +740,8 @@ void plan_release(se_plan_s *p)
     void **bufs[] = {&p->grid_in, &p->grid_out, &p->spec, &p->spec_pad, &p->U, &p->Z, (void **)&p->I_lines, &p->tabs, &p->sigma_tab,
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
                      (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
-                     (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2};
+                     (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2, &p->spec_d, &p->U_d, &p->Z_d,
+                     &p->grid_d};
     for (void **b : bufs) dev_free(p, b);
 }
 
