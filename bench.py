@@ -229,9 +229,9 @@ def run_ours(a):
     N = spec["N"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def make_form(dtype):
+    def make_form(dtype, force_method=1):
         plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"], dtype=dtype, device=dev,
-                       lam=spec.get("lam"))
+                       lam=spec.get("lam"), force_method=force_method)
         plan.reserve(N)
         x = torch.tensor(x_np, dtype=dtype, device=dev)
         q = torch.tensor(q_np, dtype=dtype, device=dev)
@@ -293,6 +293,11 @@ def run_ours(a):
     k64 = max(3, min(a.steps, 200))
     ms64, _ = timed(plan64, x64, q64, out64, g64, k64, min(a.warmup, 10))
 
+    # ---- FP32 form with forces by method 2 of Sec. 7.2 (i k in the scaling) --------
+    planm2, xm2, qm2, outm2 = make_form(torch.float32, force_method=2)
+    gm2 = capture(planm2, xm2, qm2, outm2)
+    msm2, _ = timed(planm2, xm2, qm2, outm2, gm2, k64, min(a.warmup, 10))
+
     # ---- stage profile of the FP32 form (eager calls, events on the plan's stream) --
     plan32.set_profiling(True)
     l0 = plan32.profile()["launches"]
@@ -348,6 +353,9 @@ def run_ours(a):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(spec),
             "fp64_form": {"value": aggregate_throughput(N, world, ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
                           "steps": k64, "speedup_fp32_over_fp64": ms64 / ms32},
+            "force_method_2": {"value": aggregate_throughput(N, world, msm2 * 1e-3), "unit": "particles/s",
+                               "ms_per_step": msm2, "steps": k64, "dtype": "f32",
+                               "what": "forces by i k in the scaling (Sec. 7.2 method 2): four inverse transforms"},
             "roofline": roof,
             "stage_ms": stage_ms,
             "spread_gather_gbs": sg_gbs,
@@ -371,7 +379,7 @@ def run_ours(a):
                                 "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                                 "sample": f"phi+F at all {N} targets, one pass of the direct FP64 sum (oracle A)"}
         acc = {}
-        for name, out in (("fp32", out32), ("fp64", out64)):
+        for name, out in (("fp32", out32), ("fp64", out64), ("fp32_method2", outm2)):
             F = out[0].double().cpu().numpy()
             phi = out[1].double().cpu().numpy()
             acc[name] = {"phi": float(np.linalg.norm(phi - pa) / np.linalg.norm(pa)),

@@ -94,6 +94,9 @@ typedef struct {
                            scaling by i k per direction and runs the inverse transform and a
                            gathering with W three more times (the plan then holds three more
                            spectra and grids).  se_potential and se_vjp are unaffected. */
+    int    fft_mode;    /* [<= 0] D = 0 transform: the z-direction FFT, scaling and inverse
+                           FFT fused into one kernel per column when 2 M~ is a power of two
+                           from 16 to 1024 (cuFFT otherwise); 1 cuFFT for every stage */
 } se_opts;
 
 /* Derived parameters of a plan (read-only report). */
@@ -105,6 +108,8 @@ typedef struct {
     double h, L, Lt, R, delta_L, xi, shape;
     int64_t capacity;     /* particles the workspace holds now */
     int64_t device_bytes; /* device memory held by the plan */
+    int column_fft;       /* 1: the D = 0 z-direction FFT, scaling and inverse FFT run fused
+                             in one kernel (se_opts.fft_mode) */
 } se_plan_info_t;
 
 /* Fill *o with the "unset" values. */

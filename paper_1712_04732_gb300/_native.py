@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("n_l", ctypes.c_int), ("nu", ctypes.c_int), ("shape", ctypes.c_double),
                 ("aft_eps", ctypes.c_double), ("tile", ctypes.c_int), ("spread_mode", ctypes.c_int),
                 ("gather_mode", ctypes.c_int), ("split", ctypes.c_int),
-                ("force_method", ctypes.c_int)]
+                ("force_method", ctypes.c_int), ("fft_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
                 ("grid", ctypes.c_int * 3), ("tile", ctypes.c_int * 3), ("n_tiles", ctypes.c_int),
                 ("h", ctypes.c_double), ("L", ctypes.c_double), ("Lt", ctypes.c_double), ("R", ctypes.c_double),
                 ("delta_L", ctypes.c_double), ("xi", ctypes.c_double), ("shape", ctypes.c_double),
-                ("capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("column_fft", ctypes.c_int)]
 
 
 _lib = None

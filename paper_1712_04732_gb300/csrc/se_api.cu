@@ -176,6 +176,7 @@ void se_opts_default(se_opts *o)
     o->gather_mode = 0;
     o->split = 0;
     o->force_method = 0;
+    o->fft_mode = 0;
 }
 
 se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P, se_window w,
@@ -213,6 +214,8 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
     if (o.force_method > 2) { delete p; return fail(SE_EINVAL, "force_method must be 1 or 2 (Sec. 7.2)"); }
     p->force_method = o.force_method == 2 ? 2 : 1;
+    if (o.fft_mode > 1) { delete p; return fail(SE_EINVAL, "fft_mode must be 0 or 1"); }
+    p->zcol_allowed = o.fft_mode != 1;
     // Sec. 6: shape parameters and PKB degree
     p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
     p->nu = o.nu > 0 ? o.nu : std::min(P / 2 + 2, 9);
@@ -292,6 +295,7 @@ se_status se_plan_get_info(se_plan_t p, se_plan_info_t *info)
     info->xi = p->xi; info->shape = p->shape;
     info->capacity = p->cap;
     info->device_bytes = p->device_bytes;
+    info->column_fft = p->zcol ? 1 : 0;
     return SE_OK;
 }
 

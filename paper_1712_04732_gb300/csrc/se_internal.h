@@ -14,6 +14,7 @@ namespace se {
 constexpr int kMaxP = 16;       // largest window support compiled in
 constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
+constexpr int kLocalScanTiles = 4096;   // up to this many tiles each binning CTA scans the counts itself
 constexpr int kMergeJ = 6;      // most tiles per axis whose blocks overlap one grid point
 
 // Window description passed by value to the tile kernels.  For the PKB the
@@ -74,6 +75,18 @@ struct IkBox {
     const T *k[3];
     int dim[3];
     int64_t stride;
+};
+
+// D = 0: the z-direction stage of the (2 M~)^3 transform done per column by
+// one kernel (forward FFT of the M~ non-zero values, scaling, inverse FFT, the
+// first M~ values kept).  Column c = y (M~ + 1) + x' of the 2D half spectra.
+template <typename T>
+struct ZCol {
+    int n, m;            // transform length 2 M~ and the M~ values read / kept
+    int64_t S;           // columns = complex elements per z-plane
+    int nx;              // M~ + 1 columns per y row
+    const T *tw;         // e^{-2 pi i t / n}, t = 0..n-1, as (re, im) pairs
+    const T *kx, *ky, *kz;   // method 2: signed k per x', y and z index (Nyquist zero)
 };
 
 }  // namespace se
@@ -149,6 +162,13 @@ struct se_plan_s {
     void *spec_d = nullptr, *U_d = nullptr, *Z_d = nullptr, *grid_d = nullptr;
     se::IkBox<float> ib_spec_f{}, ib_U_f{}, ib_Z_f{};
     se::IkBox<double> ib_spec_d{}, ib_U_d{}, ib_Z_d{};
+    // D = 0 column stage (used when 2 M~ is a power of two in [16, 1024])
+    bool zcol = false;
+    bool zcol_allowed = true;            // se_opts.fft_mode != 1
+    int zcol_cols = 16;                  // columns per CTA
+    void *ztw = nullptr;                 // twiddle table
+    se::ZCol<float> zc_f{};
+    se::ZCol<double> zc_d{};
 };
 
 namespace se {

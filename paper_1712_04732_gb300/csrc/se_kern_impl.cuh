@@ -125,12 +125,14 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     cudaError_t e = cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * (nt + 1), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
     BinArgs<T> a = bin_args<T>(p);
+    // few tiles: every scatter CTA scans the counts itself (no last-CTA scan)
+    const bool local_scan = nt <= kLocalScanTiles;
     k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
-                                                               p->tile_off, p->counters);
+                                                               p->tile_off, p->counters, !local_scan);
     SE_LAUNCH_CHECK("bin_count");
-    k_bin_scatter<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(
+    k_bin_scatter<T><<<blocks_for(N, 256), 256, local_scan ? sizeof(int) * (nt + 1) : 0, p->stream>>>(
         a, N, x, q, p->tile_off, p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
-        p->prt.idx_anc);
+        p->prt.idx_anc, local_scan ? p->tile_cnt : nullptr, nt);
     SE_LAUNCH_CHECK("bin_scatter");
     prof_mark(p, 1);
     return SE_OK;
@@ -252,6 +254,75 @@ template <typename T> static const IkBox<T> &ib_Z(const se_plan_s *p);
 template <> const IkBox<float> &ib_Z<float>(const se_plan_s *p) { return p->ib_Z_f; }
 template <> const IkBox<double> &ib_Z<double>(const se_plan_s *p) { return p->ib_Z_d; }
 
+template <typename T> static const ZCol<T> &zcol_args(const se_plan_s *p);
+template <> const ZCol<float> &zcol_args<float>(const se_plan_s *p) { return p->zc_f; }
+template <> const ZCol<double> &zcol_args<double>(const se_plan_s *p) { return p->zc_d; }
+
+// Shared memory of k_zcol: the twiddle table and two buffers of ncol columns.
+template <typename T>
+size_t zcol_smem(int n, int C, bool ik)
+{
+    const int ncol = ik ? 2 * C : C;
+    return (size_t(n) + 2 * size_t(ncol) * (n + 1)) * 2 * sizeof(T);
+}
+
+// D = 0 with the column stage: 2D R2C of the M~ non-zero z-planes into spec_pad,
+// k_zcol in place, 2D C2R of the M~ planes into gout (and, for method 2, of the
+// three derivative planes sets into grid_d).
+template <typename T>
+static se_status convolve_zcol(se_plan_s *p, void *gin, void *gout, bool ik)
+{
+    using C2 = typename Cplx<T>::type;
+    C2 *pad = reinterpret_cast<C2 *>(p->spec_pad);
+    cufftResult r;
+    if ((r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), pad)) != CUFFT_SUCCESS) return cufft_fail(r, "forward xy");
+    prof_mark(p, 4);
+    const ZCol<T> &zc = zcol_args<T>(p);
+    const int C = p->zcol_cols;
+    int lc = 0;
+    while ((1 << lc) < C) ++lc;
+    const unsigned nb = unsigned((zc.S + C - 1) / C);
+    const size_t sm = zcol_smem<T>(zc.n, C, ik);
+    const T *sig = reinterpret_cast<const T *>(p->sigma_tab);
+    C2 *dd = ik ? reinterpret_cast<C2 *>(p->spec_d) : nullptr;
+    const int64_t ds = ik ? int64_t(p->spec_elems) : 0;
+    cudaError_t e = cudaSuccess;
+#define SE_ZCOL_CASE(NV)                                                                         \
+    case NV:                                                                                     \
+        if (ik) {                                                                                \
+            auto kern = k_zcol<T, NV, true>;                                                     \
+            if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
+            kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
+        } else {                                                                                 \
+            auto kern = k_zcol<T, NV, false>;                                                    \
+            if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
+            kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
+        }                                                                                        \
+        break;
+    switch (zc.n) {
+        SE_ZCOL_CASE(16)
+        SE_ZCOL_CASE(32)
+        SE_ZCOL_CASE(64)
+        SE_ZCOL_CASE(128)
+        SE_ZCOL_CASE(256)
+        SE_ZCOL_CASE(512)
+        SE_ZCOL_CASE(1024)
+    default: return fail(SE_EINVAL, "column stage length not compiled in");
+    }
+#undef SE_ZCOL_CASE
+    SE_LAUNCH_CHECK("column stage");
+    prof_mark(p, 5);
+    if ((r = fft_c2r(p->inv, pad, reinterpret_cast<T *>(gout))) != CUFFT_SUCCESS) return cufft_fail(r, "inverse xy");
+    if (ik)
+        for (int a = 0; a < 3; ++a) {
+            C2 *sd = reinterpret_cast<C2 *>(p->spec_d) + a * p->spec_elems;
+            T *gd = reinterpret_cast<T *>(p->grid_d) + a * p->grid_out_elems;
+            if ((r = fft_c2r(p->inv, sd, gd)) != CUFFT_SUCCESS) return cufft_fail(r, "inverse xy (derivative)");
+        }
+    prof_mark(p, 6);
+    return SE_OK;
+}
+
 // Alg. 4 step 2: forward FFT (D = 3, 0) or AFT (Alg. 1, D = 1, 2) of gin into
 // spec (and U, Z).
 template <typename T>
@@ -370,6 +441,7 @@ se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
 {
     using C = typename Cplx<T>::type;
     se_status st;
+    if (p->zcol) return convolve_zcol<T>(p, gin, gout, false);
     if ((st = forward<T>(p, gin)) != SE_OK) return st;
     prof_mark(p, 4);
     if ((st = scale<T>(p, false)) != SE_OK) return st;
@@ -387,6 +459,7 @@ se_status Ops<T>::convolve_ik(se_plan_s *p, void *gin)
     using C = typename Cplx<T>::type;
     se_status st;
     if (!p->spec_d || !p->grid_d) return fail(SE_EINVAL, "the plan was not created with force_method = 2");
+    if (p->zcol) return convolve_zcol<T>(p, gin, p->grid_out, true);
     if ((st = forward<T>(p, gin)) != SE_OK) return st;
     prof_mark(p, 4);
     if ((st = scale<T>(p, true)) != SE_OK) return st;

@@ -94,12 +94,56 @@ __device__ __forceinline__ void block_scan(int n, const int *cnt, int *off, int 
     if (threadIdx.x == 0) off[n] = *carry;
 }
 
-// Tile of every particle (counting pass of the counting sort) and, in the CTA
-// that finishes last, the exclusive scan of the tile counts into tile offsets.
+// Exclusive prefix sum of the n counts cnt[] into shared memory soff[0..n]
+// (soff[n] = total) by one CTA: each thread sums a contiguous run, the run sums
+// are scanned with warp shuffles, then each run is written out.
+__device__ __forceinline__ void block_scan_smem(int n, const int *__restrict__ cnt, int *soff)
+{
+    __shared__ int wsum[32];
+    const int E = (n + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int loc = 0;
+    for (int i = 0; i < E; ++i)
+        if (b + i < n) {
+            const int v = cnt[b + i];
+            soff[b + i] = v;
+            loc += v;
+        }
+    int v = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = v - loc + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = 0; i < E; ++i)
+        if (b + i < n) {
+            const int c = soff[b + i];
+            soff[b + i] = run;
+            run += c;
+        }
+    if (threadIdx.x == blockDim.x - 1) soff[n] = run;
+    __syncthreads();
+}
+
+// Tile of every particle (counting pass of the counting sort) and, when
+// scan_last is set, the exclusive scan of the tile counts into tile offsets by
+// the CTA that finishes last (otherwise k_bin_scatter scans the counts itself).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q, int *__restrict__ cnt,
-            int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done)
+            int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done, bool scan_last)
 {
     __shared__ int part[256];
     __shared__ int carry;
@@ -115,6 +159,7 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
         const int r = atomicAdd(&cnt[tile], 1);
         tile_rank[i] = make_int2(tile, r);
     }
+    if (!scan_last) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
@@ -125,11 +170,23 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
     if (threadIdx.x == 0) *done = 0;
 }
 
+// Sorted records: particle i goes to position off[tile] + rank.  With cnt !=
+// nullptr every CTA first scans the ntiles counts into shared memory (few
+// tiles), and CTA 0 publishes the offsets to off[].
 template <typename T>
-__global__ void k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
-                              const int *__restrict__ off, const int2 *__restrict__ tile_rank,
-                              typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia)
+__global__ void __launch_bounds__(256)
+k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
+              int *__restrict__ off, const int2 *__restrict__ tile_rank,
+              typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia, const int *__restrict__ cnt, int ntiles)
 {
+    extern __shared__ int soff[];
+    const int *o = off;
+    if (cnt) {
+        block_scan_smem(ntiles, cnt, soff);
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = soff[t];
+        o = soff;
+    }
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= N) return;
     T xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
@@ -138,7 +195,7 @@ __global__ void k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, 
     T frac[3];
     locate(a, xp, qv, anc, frac, nullptr);
     int2 tr = tile_rank[i];
-    int pos = off[tr.x] + tr.y;
+    int pos = o[tr.x] + tr.y;
     typename Vec4<T>::type r;
     r.x = frac[0]; r.y = frac[1]; r.z = frac[2]; r.w = qv;
     fq[pos] = r;
@@ -238,6 +295,17 @@ __device__ __forceinline__ void tile_origin(const TileGeom &tg, int tile, int o[
     o[0] = (tile % tg.nt[0]) * tg.T[0];
     o[1] = ((tile / tg.nt[0]) % tg.nt[1]) * tg.T[1];
     o[2] = (tile / (tg.nt[0] * tg.nt[1])) * tg.T[2];
+}
+
+// Zero n elements of shared memory at a 16-byte aligned address, 16 bytes per store.
+template <typename T>
+__device__ __forceinline__ void zero_smem(T *a, int n)
+{
+    constexpr int V = 16 / sizeof(T);
+    float4 *a4 = reinterpret_cast<float4 *>(a);
+    const int n4 = n / V;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = n4 * V + threadIdx.x; i < n; i += blockDim.x) a[i] = T(0);
 }
 
 // Offset of a particle's lowest support point inside its tile's shared-memory block.
@@ -357,7 +425,7 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     T *sc = blk + align_up_elems<T>(tg.sblk);             // PKB coefficients
     const int ncoef = (wa.nu + 1) * P;
     T *wb = sc + align_up_elems<T>(ncoef);                // [warp][3P]
-    for (int i = threadIdx.x; i < tg.sblk; i += blockDim.x) blk[i] = T(0);
+    zero_smem(blk, tg.sblk);
     if (wa.kind == SE_WIN_PKB)
         for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -421,16 +489,25 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
         }
     }
     cluster.sync();                                       // every copy complete and visible to the cluster
+    // The cluster's copies are summed row by row (row r = z B1 + y sits at r pitch
+    // in shared memory and at r B0 in the compact block); CTA `rank` writes rows
+    // [rank R / CL, (rank + 1) R / CL), 32 / B0 rows per warp instruction.
+    const T *src[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
     T *dst = scratch + size_t(tile) * tg.blk;
-    const int chunk = (tg.blk + CL - 1) / CL;
-    const int lo = rank * chunk, hi = min(tg.blk, lo + chunk);
-    const int B0 = tg.B[0];
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const int si = (i / B0) * pitch + i % B0;
-        T s = T(0);
-        for (int j = 0; j < CL; ++j) s += cluster.map_shared_rank(blk, j)[si];
-        dst[i] = s;
-    }
+    const int B0 = tg.B[0], R = tg.B[1] * tg.B[2];
+    const int rpw = 32 / B0, sub = lane / B0, x = lane - sub * B0;
+    const int r0 = rank * R / CL, r1 = (rank + 1) * R / CL;
+    if (sub < rpw)
+        for (int r = r0 + warp * rpw + sub; r < r1; r += nw * rpw) {
+            const int si = r * pitch + x;
+            T v = src[0][si];
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (j < CL) v += src[j][si];
+            dst[r * B0 + x] = v;
+        }
     cluster.sync();                                       // no CTA leaves while its block is still read
 }
 
@@ -597,6 +674,156 @@ __global__ void k_scale_tab_ik(const T *__restrict__ tab, IkBox<T> ib, typename 
     v.y *= s;
     data[i] = v;
     ik_store(ib, i, i0, i1, i2, v, dst);
+}
+
+// ----------------------------------------------------------------- column FFT (D = 0)
+// Radix-4 (and one radix-2) Stockham FFT of length N = 2^e along columns held
+// in shared memory (column col at a + col * (N + 1)), after Govindaraju et al.
+// (2008): the pass with radix R maps element j + r N/R of the input, twiddled
+// by w^(r (j mod Ns)) with w = e^{-+2 pi i / (Ns R)}, through an R-point DFT to
+// element (j div Ns) Ns R + (j mod Ns) + r Ns of the output; Ns grows by R per
+// pass and the result comes out in natural order.  Twiddles are entries of the
+// table tw[t] = e^{-2 pi i t / N} (conjugated for the inverse).
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b)
+{
+    C2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+template <typename T, int N, int R, int NS>
+__device__ __forceinline__ void stockham_pass(const typename Cplx<T>::type *__restrict__ tw,
+                                              const typename Cplx<T>::type *a, typename Cplx<T>::type *b, int ncol,
+                                              bool inv)
+{
+    using C2 = typename Cplx<T>::type;
+    constexpr int NR = N / R, LD = N + 1, STEP = N / (NS * R);
+    for (int i = threadIdx.x; i < ncol * NR; i += blockDim.x) {
+        const int col = i / NR, j = i % NR, k = j % NS;
+        const C2 *in = a + col * LD;
+        C2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[j + r * NR];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C2 t = tw[r * k * STEP];
+            if (inv) t.y = -t.y;
+            v[r] = cmul(v[r], t);
+        }
+        C2 V[R];
+        if (R == 2) {
+            V[0].x = v[0].x + v[1].x; V[0].y = v[0].y + v[1].y;
+            V[1].x = v[0].x - v[1].x; V[1].y = v[0].y - v[1].y;
+        } else {
+            // 4-point DFT, w_4 = -i (forward) or +i (inverse)
+            const T s = inv ? T(-1) : T(1);
+            const T apc_x = v[0].x + v[2].x, apc_y = v[0].y + v[2].y;
+            const T amc_x = v[0].x - v[2].x, amc_y = v[0].y - v[2].y;
+            const T bpd_x = v[1].x + v[3].x, bpd_y = v[1].y + v[3].y;
+            const T bmd_x = v[1].x - v[3].x, bmd_y = v[1].y - v[3].y;
+            V[0].x = apc_x + bpd_x; V[0].y = apc_y + bpd_y;
+            V[2].x = apc_x - bpd_x; V[2].y = apc_y - bpd_y;
+            V[1].x = amc_x + s * bmd_y; V[1].y = amc_y - s * bmd_x;
+            V[3].x = amc_x - s * bmd_y; V[3].y = amc_y + s * bmd_x;
+        }
+        C2 *out = b + col * LD + (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[r * NS] = V[r];
+    }
+    __syncthreads();
+}
+
+// Radix-4 passes from Ns = NS upward, then a radix-2 pass if one factor 2 is
+// left; the result lands in a (after an even number of passes) or b.
+template <typename T, int N, int NS>
+__device__ __forceinline__ bool stockham_from(const typename Cplx<T>::type *tw, typename Cplx<T>::type *a,
+                                              typename Cplx<T>::type *b, int ncol, bool inv)
+{
+    if constexpr (NS >= N) {
+        return false;
+    } else if constexpr (NS * 4 <= N) {
+        stockham_pass<T, N, 4, NS>(tw, a, b, ncol, inv);
+        return !stockham_from<T, N, NS * 4>(tw, b, a, ncol, inv);
+    } else {
+        stockham_pass<T, N, 2, NS>(tw, a, b, ncol, inv);
+        return true;
+    }
+}
+
+// D = 0, z-direction stage of Alg. 4 steps 2-4 for C = 2^lc columns per CTA, in
+// place on `data` (the 2D half spectra of the M~ non-zero z-planes, plane
+// stride S): forward N-point FFT of the column (values at z >= M~ are the zero
+// padding), scaling by the table sigma[kz S + c] (Eq. scale with Alg. 3's
+// G^{0P}_R), inverse FFT, the first M~ values written back.  With IK (method 2
+// of Sec. 7.2) the three derivative columns i k_a sigma H^ go to dd + a dstride:
+// along x and y i k_a is constant on the column and multiplies the result;
+// along z the product i k_z sigma H^ is transformed as a second column set.
+template <typename T, int N, bool IK>
+__global__ void __launch_bounds__(256)
+k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *__restrict__ sigma,
+       typename Cplx<T>::type *__restrict__ dd, int64_t dstride)
+{
+    using C2 = typename Cplx<T>::type;
+    constexpr int LD = N + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int C = 1 << lc, m = zc.m;
+    const int64_t S = zc.S;
+    const int ncol = IK ? 2 * C : C;
+    C2 *tw = reinterpret_cast<C2 *>(smraw);
+    C2 *A = tw + N;
+    C2 *B = A + size_t(ncol) * LD;
+    const int64_t c0 = int64_t(blockIdx.x) << lc;
+    const int cc = int(min(int64_t(C), S - c0));
+    const C2 *gtw = reinterpret_cast<const C2 *>(zc.tw);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = gtw[t];
+    C2 zero;
+    zero.x = T(0);
+    zero.y = T(0);
+    for (int i = threadIdx.x; i < (N << lc); i += blockDim.x) {
+        const int col = i & (C - 1), z = i >> lc;
+        A[col * LD + z] = (z < m && col < cc) ? data[z * S + c0 + col] : zero;
+    }
+    __syncthreads();
+    C2 *X = stockham_from<T, N, 1>(tw, A, B, C, false) ? B : A;
+    C2 *Y = (X == A) ? B : A;
+    for (int i = threadIdx.x; i < (N << lc); i += blockDim.x) {
+        const int col = i & (C - 1), k = i >> lc;
+        const T s = col < cc ? sigma[k * S + c0 + col] : T(0);
+        C2 v = X[col * LD + k];
+        v.x *= s;
+        v.y *= s;
+        X[col * LD + k] = v;
+        if (IK) {
+            const T kz = zc.kz[k];
+            C2 d;
+            d.x = -kz * v.y;
+            d.y = kz * v.x;
+            X[(C + col) * LD + k] = d;
+        }
+    }
+    __syncthreads();
+    X = stockham_from<T, N, 1>(tw, X, Y, ncol, true) ? Y : X;
+    for (int i = threadIdx.x; i < (m << lc); i += blockDim.x) {
+        const int col = i & (C - 1), z = i >> lc;
+        if (col >= cc) continue;
+        const C2 v = X[col * LD + z];
+        const int64_t c = c0 + col;
+        data[z * S + c] = v;
+        if (IK) {
+            const int y = int(c / zc.nx), xq = int(c - int64_t(y) * zc.nx);
+            const T kx = zc.kx[xq], ky = zc.ky[y];
+            C2 d;
+            d.x = -kx * v.y;
+            d.y = kx * v.x;
+            dd[z * S + c] = d;
+            d.x = -ky * v.y;
+            d.y = ky * v.x;
+            dd[dstride + z * S + c] = d;
+            dd[2 * dstride + z * S + c] = X[(C + col) * LD + z];
+        }
+    }
 }
 
 // ----------------------------------------------------------------- AFT padding

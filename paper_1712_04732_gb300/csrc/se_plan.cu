@@ -465,6 +465,40 @@ static se_status build_tables(se_plan_s *p)
     };
     if (p->dtype == SE_F32) ikboxes(float(), p->ib_spec_f, p->ib_U_f, p->ib_Z_f);
     else ikboxes(double(), p->ib_spec_d, p->ib_U_d, p->ib_Z_d);
+    if (D == 0) {
+        // column stage: 2 M~ must be a power of two in [16, 1024] and the buffers
+        // of at least one column must fit in shared memory
+        const int n = 2 * Mt;
+        const bool pow2 = n >= 16 && n <= 1024 && (n & (n - 1)) == 0;
+        int C = 16;
+        const size_t per = 2 * (p->dtype == SE_F32 ? 4 : 8);
+        auto smem = [&](int c) { return (size_t(n) + 2 * size_t(2 * c) * (n + 1)) * per; };
+        while (C > 1 && smem(C) > 200 * 1024) C /= 2;
+        p->zcol = pow2 && smem(C) <= 200 * 1024 && p->zcol_allowed;
+        if (p->zcol) {
+            p->zcol_cols = C;
+            std::vector<double> tw(2 * size_t(n));
+            for (int t = 0; t < n; ++t) {
+                tw[2 * t] = std::cos(2.0 * M_PI * t / n);
+                tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / n);
+            }
+            std::vector<unsigned char> tb2;
+            if (p->dtype == SE_F32) to_type<float>(tw, tb2); else to_type<double>(tw, tb2);
+            if ((st = dev_alloc(p, &p->ztw, tb2.size())) != SE_OK) return st;
+            if ((st = upload(tb2.data(), p->ztw, tb2.size(), "twiddles")) != SE_OK) return st;
+            auto fill = [&](auto tag, auto &zc) {
+                using T = decltype(tag);
+                const T *base = reinterpret_cast<const T *>(p->tabs);
+                zc.n = n;
+                zc.m = Mt;
+                zc.S = int64_t(n) * (Mt + 1);
+                zc.nx = Mt + 1;
+                zc.tw = reinterpret_cast<const T *>(p->ztw);
+                zc.kx = zc.ky = zc.kz = base + o_d2Mt;
+            };
+            if (p->dtype == SE_F32) fill(float(), p->zc_f); else fill(double(), p->zc_d);
+        }
+    }
     if (D == 0) return precompute_free_space(p);
     return SE_OK;
 }
@@ -741,7 +775,7 @@ void plan_release(se_plan_s *p)
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
                      (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
                      (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2, &p->spec_d, &p->U_d, &p->Z_d,
-                     &p->grid_d};
+                     &p->grid_d, &p->ztw};
     for (void **b : bufs) dev_free(p, b);
 }
 

@@ -432,3 +432,25 @@ def test_wire_parameters_accuracy_against_direct_sum():
     pa, ga = E.fourier_xi_route(1, x, q, 1.0, spec["xi"])
     assert _rel(phi, pa) < 1e-5
     assert _rel(F, -q[:, None] * ga) < 1e-5
+
+
+@pytest.mark.parametrize("M,P,lam,fused", [(20, 8, None, 1), (10, 4, 1.3, 1), (20, 6, 1.3, 0), (16, 4, 1.3, 0)])
+@pytest.mark.parametrize("force_method", [1, 2])
+def test_free_space_column_stage_and_cufft_agree(M, P, lam, fused, force_method):
+    """D = 0: the fused column kernel (2 M~ = 64, 32) and the cuFFT stages
+    (fft_mode = 1, or 2 M~ = 56, 44 that are not powers of two) both match the
+    oracle, for both force methods."""
+    se = _se()
+    N = 900
+    x = wl.uniform_positions(N, 1.0, 61 + M + P)
+    q = wl.uniform_charges(N, 61 + M + P)
+    pb = gb = None
+    for mode in (0, 1):
+        plan = se.Plan(0, 1.0, 6.0, M, P, "pkb", dtype=torch.float64, lam=lam, force_method=force_method,
+                       fft_mode=mode)
+        assert plan.info()["column_fft"] == (fused if mode == 0 else 0)
+        F, phi, _ = _run(plan, x, q)
+        if pb is None:
+            pb, gb = _oracle_for(plan, lam=lam).potential(x, q, grad=True, force_method=force_method)
+        assert _rel(phi, pb) < 1e-11
+        assert _rel(F, -q[:, None] * gb) < 1e-10
