@@ -152,14 +152,15 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     }
 
 // CTAs per tile when a tile's particles are split (spread_mode 2, staged
-// gathering): 4 unless the tiles hold fewer than 4 particles on average
-// (measured on GB300 with one warp per particle: 4 was best or within 7 % of
-// best for 20 000 to 1.2e6 particles).
+// gathering), from the mean particles per tile (measured on GB300 with one warp
+// per particle: 2 was best at 39 and 156 per tile, 4 at 208 per tile with
+// dense clusters).
 static int split_for(const se_plan_s *p, int64_t N)
 {
     if (p->split > 0) return p->split;
-    const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
-    return N >= int64_t(4) * nt ? 4 : 1;
+    const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
+    if (N < 4 * nt) return 1;
+    return N < 192 * nt ? 2 : 4;
 }
 
 // Gridding (per-tile blocks into `scratch`) followed by the block merge into dst.
@@ -263,7 +264,7 @@ template <typename T>
 size_t zcol_smem(int n, int C, bool ik)
 {
     const int ncol = ik ? 2 * C : C;
-    return (size_t(n) + 2 * size_t(ncol) * (n + 1)) * 2 * sizeof(T);
+    return (size_t(n) + 2 * size_t(ncol) * zcol_ld(n)) * 2 * sizeof(T);
 }
 
 // D = 0 with the column stage: 2D R2C of the M~ non-zero z-planes into spec_pad,

@@ -677,13 +677,17 @@ __global__ void k_scale_tab_ik(const T *__restrict__ tab, IkBox<T> ib, typename 
 }
 
 // ----------------------------------------------------------------- column FFT (D = 0)
-// Radix-4 (and one radix-2) Stockham FFT of length N = 2^e along columns held
-// in shared memory (column col at a + col * (N + 1)), after Govindaraju et al.
-// (2008): the pass with radix R maps element j + r N/R of the input, twiddled
-// by w^(r (j mod Ns)) with w = e^{-+2 pi i / (Ns R)}, through an R-point DFT to
-// element (j div Ns) Ns R + (j mod Ns) + r Ns of the output; Ns grows by R per
-// pass and the result comes out in natural order.  Twiddles are entries of the
-// table tw[t] = e^{-2 pi i t / N} (conjugated for the inverse).
+// Stockham FFT of length N = 2^e along columns held in shared memory, after
+// Govindaraju et al. (2008): the pass with radix R maps element j + r N/R of
+// the input, twiddled by w^(r (j mod Ns)) with w = e^{-+2 pi i / (Ns R)},
+// through an R-point DFT to element (j div Ns) Ns R + (j mod Ns) + r Ns of the
+// output; Ns grows by R per pass and the result comes out in natural order.
+// Passes use radix 16 (FP32) or 8 (FP64) while possible (the R-point DFT runs
+// in registers as a radix-2 decimation in time), then one pass with the factor
+// left.  All
+// twiddles are entries of the table tw[t] = e^{-2 pi i t / N} (conjugated for
+// the inverse).  Element i of a column sits at zpad(i) = i + i / 16, which
+// keeps the strided stores of the first pass on distinct banks.
 template <typename C2>
 __device__ __forceinline__ C2 cmul(C2 a, C2 b)
 {
@@ -693,80 +697,102 @@ __device__ __forceinline__ C2 cmul(C2 a, C2 b)
     return r;
 }
 
+__host__ __device__ constexpr int zpad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int zcol_ld(int n) { return zpad(n) + 1; }
+
+// In-register R-point DFT (R a power of two): X[k] = sum_r v[r] w_R^{r k} with
+// w_R = tw[N / R] (conjugated when inv), by radix-2 decimation in time.
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(typename Cplx<T>::type *v, const typename Cplx<T>::type *tw, int tstride,
+                                        bool inv)
+{
+    using C2 = typename Cplx<T>::type;
+    if constexpr (R == 2) {
+        const C2 a = v[0], b = v[1];
+        v[0].x = a.x + b.x; v[0].y = a.y + b.y;
+        v[1].x = a.x - b.x; v[1].y = a.y - b.y;
+    } else if constexpr (R > 2) {
+        C2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        dft_reg<T, R / 2>(e, tw, 2 * tstride, inv);
+        dft_reg<T, R / 2>(o, tw, 2 * tstride, inv);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            C2 w = tw[k * tstride];
+            if (inv) w.y = -w.y;
+            const C2 t = cmul(o[k], w);
+            v[k].x = e[k].x + t.x; v[k].y = e[k].y + t.y;
+            v[k + R / 2].x = e[k].x - t.x; v[k + R / 2].y = e[k].y - t.y;
+        }
+    }
+}
+
 template <typename T, int N, int R, int NS>
 __device__ __forceinline__ void stockham_pass(const typename Cplx<T>::type *__restrict__ tw,
                                               const typename Cplx<T>::type *a, typename Cplx<T>::type *b, int ncol,
                                               bool inv)
 {
     using C2 = typename Cplx<T>::type;
-    constexpr int NR = N / R, LD = N + 1, STEP = N / (NS * R);
+    constexpr int NR = N / R, LD = zcol_ld(N), STEP = N / (NS * R);
     for (int i = threadIdx.x; i < ncol * NR; i += blockDim.x) {
         const int col = i / NR, j = i % NR, k = j % NS;
         const C2 *in = a + col * LD;
         C2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[j + r * NR];
+        for (int r = 0; r < R; ++r) v[r] = in[zpad(j + r * NR)];
+        if (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            C2 t = tw[r * k * STEP];
-            if (inv) t.y = -t.y;
-            v[r] = cmul(v[r], t);
+            for (int r = 1; r < R; ++r) {
+                C2 t = tw[r * k * STEP];
+                if (inv) t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
         }
-        C2 V[R];
-        if (R == 2) {
-            V[0].x = v[0].x + v[1].x; V[0].y = v[0].y + v[1].y;
-            V[1].x = v[0].x - v[1].x; V[1].y = v[0].y - v[1].y;
-        } else {
-            // 4-point DFT, w_4 = -i (forward) or +i (inverse)
-            const T s = inv ? T(-1) : T(1);
-            const T apc_x = v[0].x + v[2].x, apc_y = v[0].y + v[2].y;
-            const T amc_x = v[0].x - v[2].x, amc_y = v[0].y - v[2].y;
-            const T bpd_x = v[1].x + v[3].x, bpd_y = v[1].y + v[3].y;
-            const T bmd_x = v[1].x - v[3].x, bmd_y = v[1].y - v[3].y;
-            V[0].x = apc_x + bpd_x; V[0].y = apc_y + bpd_y;
-            V[2].x = apc_x - bpd_x; V[2].y = apc_y - bpd_y;
-            V[1].x = amc_x + s * bmd_y; V[1].y = amc_y - s * bmd_x;
-            V[3].x = amc_x - s * bmd_y; V[3].y = amc_y + s * bmd_x;
-        }
-        C2 *out = b + col * LD + (j / NS) * NS * R + k;
+        dft_reg<T, R>(v, tw, N / R, inv);
+        C2 *out = b + col * LD;
+        const int o = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[r * NS] = V[r];
+        for (int r = 0; r < R; ++r) out[zpad(o + r * NS)] = v[r];
     }
     __syncthreads();
 }
 
-// Radix-4 passes from Ns = NS upward, then a radix-2 pass if one factor 2 is
-// left; the result lands in a (after an even number of passes) or b.
+// Passes from Ns = NS upward; returns true when the result is in b.
 template <typename T, int N, int NS>
 __device__ __forceinline__ bool stockham_from(const typename Cplx<T>::type *tw, typename Cplx<T>::type *a,
                                               typename Cplx<T>::type *b, int ncol, bool inv)
 {
     if constexpr (NS >= N) {
         return false;
-    } else if constexpr (NS * 4 <= N) {
-        stockham_pass<T, N, 4, NS>(tw, a, b, ncol, inv);
-        return !stockham_from<T, N, NS * 4>(tw, b, a, ncol, inv);
     } else {
-        stockham_pass<T, N, 2, NS>(tw, a, b, ncol, inv);
-        return true;
+        constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;    // FP64 values take twice the registers
+        constexpr int R = (N / NS >= RMAX) ? RMAX : N / NS;
+        stockham_pass<T, N, R, NS>(tw, a, b, ncol, inv);
+        return !stockham_from<T, N, NS * R>(tw, b, a, ncol, inv);
     }
 }
 
-// D = 0, z-direction stage of Alg. 4 steps 2-4 for C = 2^lc columns per CTA, in
-// place on `data` (the 2D half spectra of the M~ non-zero z-planes, plane
-// stride S): forward N-point FFT of the column (values at z >= M~ are the zero
-// padding), scaling by the table sigma[kz S + c] (Eq. scale with Alg. 3's
-// G^{0P}_R), inverse FFT, the first M~ values written back.  With IK (method 2
-// of Sec. 7.2) the three derivative columns i k_a sigma H^ go to dd + a dstride:
-// along x and y i k_a is constant on the column and multiplies the result;
-// along z the product i k_z sigma H^ is transformed as a second column set.
+// D = 0, z-direction stage of Alg. 4 steps 2-4 for C = 2^lc columns per CTA
+// (C N <= 2048), in place on `data` (the 2D half spectra of the M~ non-zero
+// z-planes, plane stride S): forward N-point FFT of the column (values at
+// z >= M~ are the zero padding), scaling by the table sigma[kz S + c] (Eq.
+// scale with Alg. 3's G^{0P}_R, read into registers before the transform),
+// inverse FFT, the first M~ values written back.  With IK (method 2 of Sec.
+// 7.2) the three derivative columns i k_a sigma H^ go to dd + a dstride: along
+// x and y i k_a is constant on the column and multiplies the result; along z
+// the product i k_z sigma H^ is transformed as a second column set.
 template <typename T, int N, bool IK>
 __global__ void __launch_bounds__(256)
 k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *__restrict__ sigma,
        typename Cplx<T>::type *__restrict__ dd, int64_t dstride)
 {
     using C2 = typename Cplx<T>::type;
-    constexpr int LD = N + 1;
+    constexpr int LD = zcol_ld(N);
+    constexpr int kItems = 8;                       // (C N) / 256 <= 8 per thread
     extern __shared__ __align__(16) unsigned char smraw[];
     const int C = 1 << lc, m = zc.m;
     const int64_t S = zc.S;
@@ -776,6 +802,14 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
     C2 *B = A + size_t(ncol) * LD;
     const int64_t c0 = int64_t(blockIdx.x) << lc;
     const int cc = int(min(int64_t(C), S - c0));
+    // scaling factors of this thread's (column, kz) items, fetched early
+    T sg[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int i = threadIdx.x + it * blockDim.x;
+        const int col = i & (C - 1), k = i >> lc;
+        sg[it] = (i < (N << lc) && col < cc) ? sigma[k * S + c0 + col] : T(0);
+    }
     const C2 *gtw = reinterpret_cast<const C2 *>(zc.tw);
     for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = gtw[t];
     C2 zero;
@@ -783,24 +817,26 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
     zero.y = T(0);
     for (int i = threadIdx.x; i < (N << lc); i += blockDim.x) {
         const int col = i & (C - 1), z = i >> lc;
-        A[col * LD + z] = (z < m && col < cc) ? data[z * S + c0 + col] : zero;
+        A[col * LD + zpad(z)] = (z < m && col < cc) ? data[z * S + c0 + col] : zero;
     }
     __syncthreads();
     C2 *X = stockham_from<T, N, 1>(tw, A, B, C, false) ? B : A;
     C2 *Y = (X == A) ? B : A;
-    for (int i = threadIdx.x; i < (N << lc); i += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int i = threadIdx.x + it * blockDim.x;
+        if (i >= (N << lc)) break;
         const int col = i & (C - 1), k = i >> lc;
-        const T s = col < cc ? sigma[k * S + c0 + col] : T(0);
-        C2 v = X[col * LD + k];
-        v.x *= s;
-        v.y *= s;
-        X[col * LD + k] = v;
+        C2 v = X[col * LD + zpad(k)];
+        v.x *= sg[it];
+        v.y *= sg[it];
+        X[col * LD + zpad(k)] = v;
         if (IK) {
             const T kz = zc.kz[k];
             C2 d;
             d.x = -kz * v.y;
             d.y = kz * v.x;
-            X[(C + col) * LD + k] = d;
+            X[(C + col) * LD + zpad(k)] = d;
         }
     }
     __syncthreads();
@@ -808,7 +844,7 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
     for (int i = threadIdx.x; i < (m << lc); i += blockDim.x) {
         const int col = i & (C - 1), z = i >> lc;
         if (col >= cc) continue;
-        const C2 v = X[col * LD + z];
+        const C2 v = X[col * LD + zpad(z)];
         const int64_t c = c0 + col;
         data[z * S + c] = v;
         if (IK) {
@@ -821,7 +857,7 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
             d.x = -ky * v.y;
             d.y = ky * v.x;
             dd[dstride + z * S + c] = d;
-            dd[2 * dstride + z * S + c] = X[(C + col) * LD + z];
+            dd[2 * dstride + z * S + c] = X[(C + col) * LD + zpad(z)];
         }
     }
 }

@@ -470,10 +470,13 @@ static se_status build_tables(se_plan_s *p)
         // of at least one column must fit in shared memory
         const int n = 2 * Mt;
         const bool pow2 = n >= 16 && n <= 1024 && (n & (n - 1)) == 0;
-        int C = 16;
+        // columns per CTA: C n <= 2048 (8 scaling factors per thread) and the
+        // method-2 buffers within 200 KB
+        int C = 32;
         const size_t per = 2 * (p->dtype == SE_F32 ? 4 : 8);
-        auto smem = [&](int c) { return (size_t(n) + 2 * size_t(2 * c) * (n + 1)) * per; };
-        while (C > 1 && smem(C) > 200 * 1024) C /= 2;
+        const int ld = n + n / 16 + 1;
+        auto smem = [&](int c) { return (size_t(n) + 2 * size_t(2 * c) * ld) * per; };
+        while (C > 1 && (C * n > 2048 || smem(C) > 200 * 1024)) C /= 2;
         p->zcol = pow2 && smem(C) <= 200 * 1024 && p->zcol_allowed;
         if (p->zcol) {
             p->zcol_cols = C;
@@ -728,8 +731,8 @@ se_status plan_reserve(se_plan_s *p, int64_t n)
     if ((st = dev_alloc(p, (void **)&p->tile_rank, sizeof(int2) * cap)) != SE_OK) return st;
     if ((st = dev_alloc(p, &p->prt.frac_q, 4 * p->elem * cap)) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->prt.idx_anc, sizeof(int4) * cap)) != SE_OK) return st;
-    // per-CTA partial sums of the direct gathering: one per 8 warps x (32 / P) particles
-    const size_t nparts = std::max<size_t>(p->tile_part_elems, size_t(cap / 16 + 256));
+    // per-CTA partial sums of the direct gathering: one per 8 particles at most
+    const size_t nparts = std::max<size_t>(p->tile_part_elems, size_t(cap / 8 + 256));
     if (nparts > p->tile_part_elems) {
         dev_free(p, (void **)&p->tile_part);
         p->tile_part_elems = 0;
