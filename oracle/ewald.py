@@ -8,7 +8,8 @@ with gcc on first use and wraps each routine for numpy arrays.  Every function
 takes sources ``x`` (N, 3), charges ``q`` (N,), targets ``xt`` (Nt, 3) and
 returns ``(phi, grad)`` with ``grad`` the gradient of ``phi`` with respect to
 the target position.  The force on a target particle of charge q_t is
-``-q_t * grad``.
+``-q_t * grad``.  The box side ``L`` is a number (cube) or three numbers
+(sides along x, y, z; Sec. 2: the domain need not be a cube).
 """
 from __future__ import annotations
 
@@ -51,13 +52,13 @@ def _load():
             _lib.oa_special.restype = d
             _lib.oa_special.argtypes = [i, d, d]
             for name, args in {
-                "oa_fourier_3p": [i, p, p, i, p, d, d, i, p, p],
+                "oa_fourier_3p": [i, p, p, i, p, p, d, p, p, p],
                 "oa_fourier_0p": [i, p, p, i, p, d, p, p],
-                "oa_fourier_2p": [i, p, p, i, p, d, d, i, p, p],
-                "oa_fourier_1p": [i, p, p, i, p, d, d, i, p, p],
-                "oa_real": [i, i, p, p, i, p, d, d, d, p, p],
+                "oa_fourier_2p": [i, p, p, i, p, p, d, p, p, p],
+                "oa_fourier_1p": [i, p, p, i, p, p, d, p, p, p],
+                "oa_real": [i, i, p, p, i, p, p, d, d, p, p],
                 "oa_coulomb_0p": [i, p, p, i, p, p, p],
-                "oa_fourier_xi_route": [i, i, p, p, i, p, d, d, d, d, p, p],
+                "oa_fourier_xi_route": [i, i, p, p, i, p, p, d, d, d, p, p],
             }.items():
                 f = getattr(_lib, name)
                 f.restype = None
@@ -78,27 +79,38 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def box(L) -> np.ndarray:
+    """The three box sides from a number (cube) or a sequence of three."""
+    b = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,)).copy()
+    if not np.all(b > 0):
+        raise ValueError("box sides must be positive")
+    return b
+
+
 def kmax_n(xi: float, L: float, tail: float = 1e-20) -> int:
     """Largest |n| kept in the k-sums: e^{-k^2/(4 xi^2)} < tail at k = 2 pi n / L."""
     kmax = 2.0 * xi * np.sqrt(np.log(1.0 / tail))
     return int(np.ceil(kmax * L / (2.0 * np.pi)))
 
 
-def fourier(D: int, x, q, L: float, xi: float, xt=None, nmax: int | None = None):
+def fourier(D: int, x, q, L, xi: float, xt=None, nmax: int | None = None):
     """Fourier-space part phi^{DP,F} of Eq. (fourier_space_nonzero_ewald) in its
     closed forms: 3P k-sum (Eq. fourier_space_explicit_3P, k = 0 dropped),
     2P Eqs. (2pno0)+(2p0), 1P Eqs. (1pno0)+(1p0), 0P sum of q erf(xi r)/r."""
     lib = _load()
     x, q, xt, phi, grad = _prep(x, q, xt)
     N, Nt = x.shape[0], xt.shape[0]
+    b = box(L)
     if nmax is None:
-        nmax = kmax_n(xi, L)
+        nm = np.array([kmax_n(xi, v) for v in b], dtype=np.int32)
+    else:
+        nm = np.array([nmax] * 3, dtype=np.int32)
     if D == 3:
-        lib.oa_fourier_3p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), L, xi, nmax, _ptr(phi), _ptr(grad))
+        lib.oa_fourier_3p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), _ptr(b), xi, _ptr(nm), _ptr(phi), _ptr(grad))
     elif D == 2:
-        lib.oa_fourier_2p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), L, xi, nmax, _ptr(phi), _ptr(grad))
+        lib.oa_fourier_2p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), _ptr(b), xi, _ptr(nm), _ptr(phi), _ptr(grad))
     elif D == 1:
-        lib.oa_fourier_1p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), L, xi, nmax, _ptr(phi), _ptr(grad))
+        lib.oa_fourier_1p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), _ptr(b), xi, _ptr(nm), _ptr(phi), _ptr(grad))
     elif D == 0:
         lib.oa_fourier_0p(N, _ptr(x), _ptr(q), Nt, _ptr(xt), xi, _ptr(phi), _ptr(grad))
     else:
@@ -106,7 +118,7 @@ def fourier(D: int, x, q, L: float, xi: float, xt=None, nmax: int | None = None)
     return phi, grad
 
 
-def fourier_xi_route(D: int, x, q, L: float, xi: float, xt=None, xi2: float | None = None):
+def fourier_xi_route(D: int, x, q, L, xi: float, xt=None, xi2: float | None = None):
     """phi^{DP,F} for D = 1, 2 through the splitting-parameter independence of
     the total potential (Sec. 2): total evaluated at a small xi2 where only the
     zero mode survives.  Cost O(Nt N (images)), usable at large N."""
@@ -114,19 +126,21 @@ def fourier_xi_route(D: int, x, q, L: float, xi: float, xt=None, xi2: float | No
         raise ValueError("the xi route is for D = 1, 2")
     lib = _load()
     x, q, xt, phi, grad = _prep(x, q, xt)
+    b = box(L)
     if xi2 is None:
-        xi2 = 0.4 / L
+        xi2 = 0.4 / float(np.max(b[:D]))
     rc = 6.5 / xi2
     lib.oa_fourier_xi_route(D, x.shape[0], _ptr(x), _ptr(q), xt.shape[0], _ptr(xt),
-                            L, xi, xi2, rc, _ptr(phi), _ptr(grad))
+                            _ptr(b), xi, xi2, rc, _ptr(phi), _ptr(grad))
     return phi, grad
 
 
-def real(D: int, x, q, L: float, xi: float, rc: float, xt=None):
+def real(D: int, x, q, L, xi: float, rc: float, xt=None):
     """Real-space sum, Eq. (real_space_ewald), images in the D periodic directions."""
     lib = _load()
     x, q, xt, phi, grad = _prep(x, q, xt)
-    lib.oa_real(D, x.shape[0], _ptr(x), _ptr(q), xt.shape[0], _ptr(xt), L, xi, rc,
+    b = box(L)
+    lib.oa_real(D, x.shape[0], _ptr(x), _ptr(q), xt.shape[0], _ptr(xt), _ptr(b), xi, rc,
                 _ptr(phi), _ptr(grad))
     return phi, grad
 
@@ -144,7 +158,7 @@ def coulomb_0p(x, q, xt=None):
     return phi, grad
 
 
-def total(D: int, x, q, L: float, xi: float, rc: float | None = None):
+def total(D: int, x, q, L, xi: float, rc: float | None = None):
     """Full Ewald potential phi^R + phi^F + phi^self at the sources (Eq. potential_split)."""
     if rc is None:
         rc = 6.5 / xi

@@ -11,6 +11,8 @@
  * Every routine evaluates at Nt target points xt[Nt][3] the field of N
  * sources x[N][3] with charges q[N] and writes phi[Nt] and (if grad != NULL)
  * grad[Nt][3] = gradient of phi with respect to the target position.
+ * The box has sides L[0], L[1], L[2] (Sec. 2: the domain need not be a cube);
+ * only the sides of the periodic directions enter the sums.
  * A target that coincides exactly with a source gets that source's r -> 0
  * limit in the smooth (Fourier-space) kernels and is skipped in the singular
  * (real-space, Coulomb) kernels, which is the primed sum of Eq. (potential).
@@ -155,21 +157,23 @@ double oa_special(int which, double a, double b)
 
 /* D = 3, Eq. (fourier_space_explicit_3P): the k = 0 term is dropped
  * (Sec. 2, spherical order, tin-foil, neutrality).  Wave vectors
- * k = 2 pi n / L with 0 < |n| <= nmax, via the structure factors
- * S(k) = sum_n q_n e^{i k.x_n};  phi_t = (4 pi / L^3) sum_k g(k) Re[e^{i k.x_t} S(k)^*],
- * g = e^{-k^2/(4 xi^2)} / k^2.  Only half of k-space is visited (factor 2). */
+ * k = 2 pi (n0/L0, n1/L1, n2/L2), n != 0 inside the ellipsoid
+ * sum_i (n_i/nmax_i)^2 <= 1, via the structure factors
+ * S(k) = sum_n q_n e^{i k.x_n};  phi_t = (4 pi / V) sum_k g(k) Re[e^{i k.x_t} S(k)^*],
+ * g = e^{-k^2/(4 xi^2)} / k^2, V = L0 L1 L2.  Only half of k-space is visited (factor 2). */
 void oa_fourier_3p(int N, const double *x, const double *q, int Nt,
-                   const double *xt, double L, double xi, int nmax,
+                   const double *xt, const double *L, double xi, const int *nmax,
                    double *phi, double *grad)
 {
-    int side = 2 * nmax + 1;
-    int nk_all = side * side * side;
+    int nk_all = (2 * nmax[0] + 1) * (2 * nmax[1] + 1) * (2 * nmax[2] + 1);
     int *kn = (int *)malloc(sizeof(int) * 3 * nk_all);
     int nk = 0;
-    for (int a = -nmax; a <= nmax; ++a)
-        for (int b = -nmax; b <= nmax; ++b)
-            for (int c = -nmax; c <= nmax; ++c) {
-                if (a * a + b * b + c * c > nmax * nmax) continue;
+    for (int a = -nmax[0]; a <= nmax[0]; ++a)
+        for (int b = -nmax[1]; b <= nmax[1]; ++b)
+            for (int c = -nmax[2]; c <= nmax[2]; ++c) {
+                double e = (double)a * a / ((double)nmax[0] * nmax[0]) + (double)b * b / ((double)nmax[1] * nmax[1]) +
+                           (double)c * c / ((double)nmax[2] * nmax[2]);
+                if (e > 1.0 + 1e-12) continue;
                 int half = (a > 0) || (a == 0 && b > 0) || (a == 0 && b == 0 && c > 0);
                 if (!half) continue;
                 kn[3 * nk] = a; kn[3 * nk + 1] = b; kn[3 * nk + 2] = c; ++nk;
@@ -177,10 +181,10 @@ void oa_fourier_3p(int N, const double *x, const double *q, int Nt,
     double *Sc = (double *)calloc(nk, sizeof(double));
     double *Ss = (double *)calloc(nk, sizeof(double));
     double *gk = (double *)malloc(sizeof(double) * nk);
-    double tp = 2.0 * M_PI / L;
+    double tp0 = 2.0 * M_PI / L[0], tp1 = 2.0 * M_PI / L[1], tp2 = 2.0 * M_PI / L[2];
 #pragma omp parallel for schedule(dynamic, 16)
     for (int j = 0; j < nk; ++j) {
-        double k0 = tp * kn[3 * j], k1 = tp * kn[3 * j + 1], k2 = tp * kn[3 * j + 2];
+        double k0 = tp0 * kn[3 * j], k1 = tp1 * kn[3 * j + 1], k2 = tp2 * kn[3 * j + 2];
         double k2s = k0 * k0 + k1 * k1 + k2 * k2;
         gk[j] = exp(-k2s / (4.0 * xi * xi)) / k2s;
         double sc = 0.0, ss = 0.0;
@@ -191,12 +195,12 @@ void oa_fourier_3p(int N, const double *x, const double *q, int Nt,
         }
         Sc[j] = sc; Ss[j] = ss;
     }
-    double pref = 2.0 * 4.0 * M_PI / (L * L * L);
+    double pref = 2.0 * 4.0 * M_PI / (L[0] * L[1] * L[2]);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int t = 0; t < Nt; ++t) {
         double p = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
         for (int j = 0; j < nk; ++j) {
-            double k0 = tp * kn[3 * j], k1 = tp * kn[3 * j + 1], k2 = tp * kn[3 * j + 2];
+            double k0 = tp0 * kn[3 * j], k1 = tp1 * kn[3 * j + 1], k2 = tp2 * kn[3 * j + 2];
             double arg = k0 * xt[3 * t] + k1 * xt[3 * t + 1] + k2 * xt[3 * t + 2];
             double c = cos(arg), s = sin(arg);
             p += gk[j] * (c * Sc[j] + s * Ss[j]);
@@ -237,28 +241,31 @@ void oa_fourier_0p(int N, const double *x, const double *q, int Nt,
 
 /* D = 2 (x, y periodic; z free): Eq. (2pno0), with a "+" joining the two
  * erfc terms (the operator is lost in the printed equation; the sum must be
- * even in z), plus the zero mode Eq. (2p0).  Wave vectors k = 2 pi (n1,n2)/L,
- * 0 < |n| <= nmax.  The bracket depends on |k| only, so it is evaluated once
- * per shell n1^2 + n2^2 and multiplied by the shell's sum of cos(k.v). */
+ * even in z), plus the zero mode Eq. (2p0).  Wave vectors
+ * k = 2 pi (n1/L0, n2/L1), n != 0 inside the ellipse (n1/nmax0)^2 + (n2/nmax1)^2 <= 1.
+ * The bracket depends on |k| only, so it is evaluated once per class
+ * (|n1|, |n2|) and multiplied by that class's sum of cos(k.v). */
 void oa_fourier_2p(int N, const double *x, const double *q, int Nt,
-                   const double *xt, double L, double xi, int nmax,
+                   const double *xt, const double *L, double xi, const int *nmax,
                    double *phi, double *grad)
 {
-    int nsh = nmax * nmax + 1;            /* shells m = n1^2+n2^2 <= nmax^2 */
-    int side = 2 * nmax + 1;
-    int *kn = (int *)malloc(sizeof(int) * 2 * side * side);
-    int *ksh = (int *)malloc(sizeof(int) * side * side);
+    int w1 = nmax[1] + 1;
+    int nsh = (nmax[0] + 1) * w1;          /* classes (|n1|, |n2|) */
+    int side = (2 * nmax[0] + 1) * (2 * nmax[1] + 1);
+    int *kn = (int *)malloc(sizeof(int) * 2 * side);
+    int *ksh = (int *)malloc(sizeof(int) * side);
     int nk = 0;
-    for (int a = -nmax; a <= nmax; ++a)
-        for (int b = -nmax; b <= nmax; ++b) {
-            int m = a * a + b * b;
-            if (m == 0 || m > nmax * nmax) continue;
+    for (int a = -nmax[0]; a <= nmax[0]; ++a)
+        for (int b = -nmax[1]; b <= nmax[1]; ++b) {
+            if (a == 0 && b == 0) continue;
+            double e = (double)a * a / ((double)nmax[0] * nmax[0]) + (double)b * b / ((double)nmax[1] * nmax[1]);
+            if (e > 1.0 + 1e-12) continue;
             if (!(a > 0 || (a == 0 && b > 0))) continue;      /* half plane */
-            kn[2 * nk] = a; kn[2 * nk + 1] = b; ksh[nk] = m; ++nk;
+            kn[2 * nk] = a; kn[2 * nk + 1] = b; ksh[nk] = abs(a) * w1 + abs(b); ++nk;
         }
-    double tp = 2.0 * M_PI / L;
-    double pref = M_PI / (L * L);
-    double pref0 = -2.0 * SQRT_PI / (L * L);
+    double tp0 = 2.0 * M_PI / L[0], tp1 = 2.0 * M_PI / L[1];
+    double pref = M_PI / (L[0] * L[1]);
+    double pref0 = -2.0 * SQRT_PI / (L[0] * L[1]);
 #pragma omp parallel
     {
         double *C = (double *)malloc(sizeof(double) * nsh);    /* sum cos */
@@ -274,7 +281,7 @@ void oa_fourier_2p(int N, const double *x, const double *q, int Nt,
                 memset(Sx, 0, sizeof(double) * nsh);
                 memset(Sy, 0, sizeof(double) * nsh);
                 for (int j = 0; j < nk; ++j) {
-                    double k0 = tp * kn[2 * j], k1 = tp * kn[2 * j + 1];
+                    double k0 = tp0 * kn[2 * j], k1 = tp1 * kn[2 * j + 1];
                     double arg = k0 * v0 + k1 * v1;
                     double s = sin(arg);
                     C[ksh[j]] += 2.0 * cos(arg);               /* +k and -k */
@@ -283,7 +290,8 @@ void oa_fourier_2p(int N, const double *x, const double *q, int Nt,
                 }
                 for (int m = 1; m < nsh; ++m) {
                     if (C[m] == 0.0 && Sx[m] == 0.0 && Sy[m] == 0.0) continue;
-                    double k = tp * sqrt((double)m);
+                    double ka = tp0 * (m / w1), kb = tp1 * (m % w1);
+                    double k = sqrt(ka * ka + kb * kb);
                     double ep = oa_ekz_erfc(k, z, xi), em = oa_ekz_erfc(k, -z, xi);
                     double br = (ep + em) / k;
                     p += q[n] * C[m] * br;
@@ -303,14 +311,16 @@ void oa_fourier_2p(int N, const double *x, const double *q, int Nt,
     free(kn); free(ksh);
 }
 
-/* D = 1 (x periodic; y, z free): Eq. (1pno0) with k1 = 2 pi n / L,
+/* D = 1 (x periodic; y, z free): Eq. (1pno0) with k1 = 2 pi n / L0,
  * 0 < |n| <= nmax, and the zero mode Eq. (1p0) written with
  * Ein(s) = gamma + ln s + E1(s), s = xi^2 rho^2 (Ein(0) = 0 reproduces the
  * exclusion n != m). */
 void oa_fourier_1p(int N, const double *x, const double *q, int Nt,
-                   const double *xt, double L, double xi, int nmax,
+                   const double *xt, const double *Lv, double xi, const int *nmaxv,
                    double *phi, double *grad)
 {
+    const double L = Lv[0];
+    const int nmax = nmaxv[0];
     double tp = 2.0 * M_PI / L;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < Nt; ++t) {
@@ -345,24 +355,18 @@ void oa_fourier_1p(int N, const double *x, const double *q, int Nt,
 /* --------------------------------------------------- real-space parts */
 
 /* Image shifts p in the first D directions with |p| <= rad + diameter. */
-static int oa_images(int D, double L, double rad, int **out)
+static int oa_images(int D, const double *L, double rad, int **out)
 {
-    int nm = (int)ceil(rad / L) + 1;
-    int side = 2 * nm + 1;
-    int cap = 1;
-    for (int d = 0; d < D; ++d) cap *= side;
+    int nm[3];
+    for (int d = 0; d < 3; ++d) nm[d] = d < D ? (int)ceil(rad / L[d]) + 1 : 0;
+    int cap = (2 * nm[0] + 1) * (2 * nm[1] + 1) * (2 * nm[2] + 1);
     int *im = (int *)malloc(sizeof(int) * 3 * cap);
     int cnt = 0;
-    for (int a = -nm; a <= nm; ++a) {
-        if (D < 1 && a != 0) continue;
-        for (int b = -nm; b <= nm; ++b) {
-            if (D < 2 && b != 0) continue;
-            for (int c = -nm; c <= nm; ++c) {
-                if (D < 3 && c != 0) continue;
+    for (int a = -nm[0]; a <= nm[0]; ++a)
+        for (int b = -nm[1]; b <= nm[1]; ++b)
+            for (int c = -nm[2]; c <= nm[2]; ++c) {
                 im[3 * cnt] = a; im[3 * cnt + 1] = b; im[3 * cnt + 2] = c; ++cnt;
             }
-        }
-    }
     *out = im;
     return cnt;
 }
@@ -370,7 +374,7 @@ static int oa_images(int D, double L, double rad, int **out)
 /* Real-space sum, Eq. (real_space_ewald): sum over images p in P_D and
  * sources n, excluding r = 0, of q_n erfc(xi r)/r, truncated at r < rc. */
 void oa_real(int D, int N, const double *x, const double *q, int Nt,
-             const double *xt, double L, double xi, double rc,
+             const double *xt, const double *L, double xi, double rc,
              double *phi, double *grad)
 {
     int *im;
@@ -380,9 +384,9 @@ void oa_real(int D, int N, const double *x, const double *q, int Nt,
         double p = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
         for (int i = 0; i < nim; ++i)
             for (int n = 0; n < N; ++n) {
-                double d0 = xt[3 * t] - x[3 * n] + L * im[3 * i];
-                double d1 = xt[3 * t + 1] - x[3 * n + 1] + L * im[3 * i + 1];
-                double d2 = xt[3 * t + 2] - x[3 * n + 2] + L * im[3 * i + 2];
+                double d0 = xt[3 * t] - x[3 * n] + L[0] * im[3 * i];
+                double d1 = xt[3 * t + 1] - x[3 * n + 1] + L[1] * im[3 * i + 1];
+                double d2 = xt[3 * t + 2] - x[3 * n + 2] + L[2] * im[3 * i + 2];
                 double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 if (r2 == 0.0 || r2 >= rc * rc) continue;
                 double r = sqrt(r2);
@@ -433,7 +437,7 @@ void oa_coulomb_0p(int N, const double *x, const double *q, int Nt,
  * own charge.  The image sum is truncated at rc, where erfc(xi2 rc) is
  * negligible. */
 void oa_fourier_xi_route(int D, int N, const double *x, const double *q, int Nt,
-                         const double *xt, double L, double xi, double xi2,
+                         const double *xt, const double *L, double xi, double xi2,
                          double rc, double *phi, double *grad)
 {
     int *im;
@@ -443,9 +447,9 @@ void oa_fourier_xi_route(int D, int N, const double *x, const double *q, int Nt,
         double p = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
         for (int n = 0; n < N; ++n) {
             for (int i = 0; i < nim; ++i) {
-                double d0 = xt[3 * t] - x[3 * n] + L * im[3 * i];
-                double d1 = xt[3 * t + 1] - x[3 * n + 1] + L * im[3 * i + 1];
-                double d2 = xt[3 * t + 2] - x[3 * n + 2] + L * im[3 * i + 2];
+                double d0 = xt[3 * t] - x[3 * n] + L[0] * im[3 * i];
+                double d1 = xt[3 * t + 1] - x[3 * n + 1] + L[1] * im[3 * i + 1];
+                double d2 = xt[3 * t + 2] - x[3 * n + 2] + L[2] * im[3 * i + 2];
                 double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 if (r2 >= rc * rc) continue;
                 if (r2 == 0.0) { p += q[n] * 2.0 * (xi - xi2) / SQRT_PI; continue; }
@@ -459,14 +463,14 @@ void oa_fourier_xi_route(int D, int N, const double *x, const double *q, int Nt,
             }
             if (D == 2) {
                 double z = xt[3 * t + 2] - x[3 * n + 2];
-                double c = -2.0 * SQRT_PI / (L * L);
+                double c = -2.0 * SQRT_PI / (L[0] * L[1]);
                 p += c * q[n] * (exp(-xi2 * xi2 * z * z) / xi2 + SQRT_PI * z * erf(xi2 * z));
                 g2 += c * q[n] * SQRT_PI * erf(xi2 * z);
             } else if (D == 1) {
                 double w1 = xt[3 * t + 1] - x[3 * n + 1], w2 = xt[3 * t + 2] - x[3 * n + 2];
                 double b = xi2 * xi2 * (w1 * w1 + w2 * w2);
-                p -= q[n] * oa_ein(b) / L;
-                double fb = -q[n] * oa_dein(b) * 2.0 * xi2 * xi2 / L;
+                p -= q[n] * oa_ein(b) / L[0];
+                double fb = -q[n] * oa_dein(b) * 2.0 * xi2 * xi2 / L[0];
                 g1 += fb * w1; g2 += fb * w2;
             }
         }

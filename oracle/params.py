@@ -102,30 +102,72 @@ def from_tolerance(eps: float, xi: float, L: float, Q: float, window: str = "pkb
     return M, P
 
 
-def grid(D: int, L: float, M: int, P: int, window: str, eps_rel: float = 1e-10,
+def box_grid(L, M: int):
+    """Box sides and grid intervals per axis for a common spacing h = L_x / M
+    (Sec. 2: the domain need not be a cube).  Every side must be an even
+    multiple of h."""
+    Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,)).copy()
+    h = Lv[0] / M
+    Mv = []
+    for v in Lv:
+        m = int(round(v / h))
+        if m < 2 or m % 2 or abs(m * h - v) > 1e-9 * v:
+            raise ValueError("each box side must be an even multiple of h = L_x / M")
+        Mv.append(m)
+    return Lv, h, Mv
+
+
+def grid(D: int, L, M: int, P: int, window: str, eps_rel: float = 1e-10,
          lam: float | None = None, s0: float | None = None):
-    """Alg. 4 step 0 and the AFT parameters of Sec. 6:
-    h, M~ = 2 ceil((M + lambda P)/2), L~ = h M~, R = sqrt(3-D) L~, delta_L,
-    s0 M~, s M~ (both rounded up to even integers) and n_l.
-    ``eps_rel`` stands for eps_rms / B in Eqs. (estimate-s), (estimate-nl)."""
-    h = L / M
-    out = {"D": D, "L": L, "M": M, "P": P, "h": h, "window": window}
+    """Alg. 4 step 0 and the AFT parameters of Sec. 6 for a box with sides L
+    (a number for the cube) and M intervals along x; h = L_x / M on every axis.
+    Per free direction i: M~_i = 2 ceil((M_i + lambda P)/2), L~_i = h M~_i,
+    delta_L_i = L~_i - L_i; R = |(L~_i)_free| (sqrt(3 - D) L~ for the cube);
+    s0 M~_i and s M~_i rounded up to even integers, with s0 raised to
+    1 + R / L~_i where that is larger (the oversampled grid must hold the
+    truncated kernel, Sec. 3.4); n_l from Eq. (estimate-nl) per free
+    direction.  The set I of Eq. (I) is the box |k_j| < 2 pi (n_l + 1) / L_f
+    around k = 0 (its largest extent over the free directions f), i.e. mode
+    indices |m_j| <= nI_j along each periodic direction j; for the cube
+    nI_j = n_l.  The scalar entries are those of the first free axis (the
+    cube's values).  ``eps_rel`` stands for eps_rms / B in Eqs. (estimate-s),
+    (estimate-nl)."""
+    Lv, h, Mv = box_grid(L, M)
+    out = {"D": D, "L": float(Lv[0]), "Lv": Lv, "M": M, "Mv": Mv, "P": P, "h": h, "window": window}
     if D == 3:
-        out.update(Mt=M, Lt=L, R=0.0, dL=0.0, s0Mt=M, sMt=M, nl=0)
+        out.update(Mt=M, Lt=float(Lv[0]), R=0.0, dL=0.0, s0Mt=M, sMt=M, nl=0,
+                   Mt_v=list(Mv), Lt_v=Lv.copy(), dL_v=np.zeros(3), s0Mt_v=list(Mv), sMt_v=list(Mv),
+                   nI=[0, 0, 0])
         return out
     if lam is None:
         lam = LAMBDA[window][D]
-    Mt = 2 * math.ceil((M + lam * P) / 2.0)
-    Lt = h * Mt
-    out.update(Mt=Mt, Lt=Lt, R=math.sqrt(3 - D) * Lt, dL=Lt - L)
+    free = list(range(D, 3))
+    Mt_v = [Mv[i] if i < D else 2 * math.ceil((Mv[i] + lam * P) / 2.0) for i in range(3)]
+    Lt_v = np.array([h * m for m in Mt_v])
+    R = math.sqrt(sum(Lt_v[i] ** 2 for i in free))
     s0v = S0[D] if s0 is None else s0
-    out["s0Mt"] = even_up(s0v * Mt)
+    s0Mt_v = [Mv[i] if i < D else even_up(max(s0v, 1.0 + R / Lt_v[i]) * Mt_v[i]) for i in range(3)]
+    f = free[0]
+    out.update(Mt=Mt_v[f], Lt=float(Lt_v[f]), R=R, dL=float(Lt_v[f] - Lv[f]), Mt_v=Mt_v, Lt_v=Lt_v,
+               dL_v=Lt_v - Lv, s0Mt=s0Mt_v[f], s0Mt_v=s0Mt_v)
     if D == 0:
-        out.update(sMt=2 * Mt, nl=0)
+        out.update(sMt=2 * Mt_v[f], sMt_v=[2 * m for m in Mt_v], nl=0, nI=[0, 0, 0])
         return out
     lg = math.log(1.0 / (2.0 * eps_rel)) / (2.0 * math.pi)
-    out["sMt"] = even_up(M / Mt * (1.0 + lg) * Mt)
-    out["nl"] = max(0, math.ceil(M / (Mt - M) * lg - 1.0))
+    sMt_v = [Mv[i] if i < D else even_up(Mv[i] * (1.0 + lg)) for i in range(3)]
+    nl_v = {i: max(0, math.ceil(Mv[i] / (Mt_v[i] - Mv[i]) * lg - 1.0)) for i in free}
+    out.update(sMt=sMt_v[f], sMt_v=sMt_v, nl=nl_v[f], nl_v=nl_v)
+    out["nI"] = i_box(D, Lv, nl_v)
+    return out
+
+
+def i_box(D: int, Lv, nl_v) -> list:
+    """Mode-index half-widths of the set I along the periodic directions: the
+    box |k_j| < k_l = max_f 2 pi (n_l,f + 1) / L_f, i.e. |m_j| <= ceil(k_l L_j / 2 pi) - 1."""
+    kl = max(2.0 * math.pi * (nl_v[f] + 1) / Lv[f] for f in nl_v)
+    out = [0, 0, 0]
+    for j in range(D):
+        out[j] = max(0, math.ceil(kl * Lv[j] / (2.0 * math.pi) - 1e-9) - 1)
     return out
 
 

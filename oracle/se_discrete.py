@@ -83,26 +83,36 @@ def green(D: int, R: float, kper2, kap):
 class SEOracle:
     """Discrete Spectral Ewald evaluation with the paper's parameters.
 
-    window: 'gaussian', 'kb' or 'pkb'.  ``lam``, ``s0``, ``s_mt`` (= s M~),
-    ``nl`` override the Sec. 6 rules; ``eps_rel`` feeds Eqs. (estimate-s),
-    (estimate-nl).
+    window: 'gaussian', 'kb' or 'pkb'.  ``L`` is the cube's side or the three
+    box sides (each an even multiple of h = L_x / M).  ``lam``, ``s0``,
+    ``s_mt`` (= s M~, a number or one per axis), ``nl`` (the half-width of
+    the set I in mode indices, a number or one per axis) override the Sec. 6
+    rules; ``eps_rel`` feeds Eqs. (estimate-s), (estimate-nl).
     """
 
-    def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
+    def __init__(self, D: int, L, xi: float, M: int, P: int, window: str = "pkb",
                  eps_rel: float = 1e-10, lam=None, s0=None, s_mt=None, nl=None, nu=None,
                  shape=None):
         if M % 2 or P % 2 or P > M:
             raise ValueError("M and P must be even with P <= M (Sec. 3.3)")
-        self.D, self.L, self.xi, self.M, self.P = D, L, xi, M, P
         self.g = prm.grid(D, L, M, P, window, eps_rel=eps_rel, lam=lam, s0=s0)
+        self.D, self.xi, self.M, self.P = D, xi, M, P
+        self.Lv = self.g["Lv"]
+        self.L = float(self.Lv[0])
         if s_mt is not None:
-            self.g["sMt"] = s_mt
+            sv = list(np.broadcast_to(np.asarray(s_mt), (3,)))
+            self.g["sMt_v"] = [self.g["Mv"][i] if i < D else int(sv[i]) for i in range(3)]
+            self.g["sMt"] = self.g["sMt_v"][min(D, 2)]
         if nl is not None:
-            self.g["nl"] = nl
+            nv = list(np.broadcast_to(np.asarray(nl), (3,)))
+            self.g["nI"] = [int(nv[i]) if i < D else 0 for i in range(3)]
+            self.g["nl"] = self.g["nI"][0]
         self.h = self.g["h"]
         self.Mt = self.g["Mt"]
-        self.n = [M if i < D else self.Mt for i in range(3)]
-        self.off = [0.0 if i < D else self.g["dL"] / 2.0 for i in range(3)]
+        self.Mv = self.g["Mv"]
+        self.Mt_v = self.g["Mt_v"]
+        self.n = [self.Mv[i] if i < D else self.Mt_v[i] for i in range(3)]
+        self.off = [0.0 if i < D else self.g["dL_v"][i] / 2.0 for i in range(3)]
         kind = window
         self.shape = prm.shape("gaussian" if kind == "gaussian" else "kb", P) if shape is None else shape
         self.nu = prm.degree(P) if nu is None else nu
@@ -112,17 +122,19 @@ class SEOracle:
 
     # ---- Alg. 3 ---------------------------------------------------------
     def _precompute_free_space(self):
-        """Alg. 3: sample G^{0P} on (s0 M~)^3 at k = 2 pi n/(s0 L~), inverse FFT,
-        keep the indices -M~ <= j <= M~-1 (wrapped) on a (2 M~)^3 grid, FFT.
-        The result is G^{0P}_R at k = pi n / L~, n = -M~..M~-1 (FFT order)."""
-        Mt, Lt, R = self.Mt, self.g["Lt"], self.g["R"]
-        ns = self.g["s0Mt"]
-        k1 = 2.0 * np.pi * np.fft.fftfreq(ns, d=Lt / Mt)          # 2 pi n / (s0 L~)
-        kk = np.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + k1[None, None, :] ** 2)
+        """Alg. 3: sample G^{0P} on s0M~_0 x s0M~_1 x s0M~_2 points at
+        k_i = 2 pi n / (s0M~_i h), inverse FFT, keep the indices
+        -M~_i <= j <= M~_i - 1 (wrapped) on a 2M~_0 x 2M~_1 x 2M~_2 grid, FFT.
+        The result is G^{0P}_R at k_i = pi n / L~_i, n = -M~_i..M~_i-1 (FFT order)."""
+        Mt, R, h = self.Mt_v, self.g["R"], self.h
+        ns = self.g["s0Mt_v"]
+        k = [2.0 * np.pi * np.fft.fftfreq(ns[i], d=h) for i in range(3)]
+        kk = np.sqrt(k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + k[2][None, None, :] ** 2)
         G = np.fft.ifftn(green(0, R, 0.0, kk)).real
-        idx = np.arange(-Mt, Mt)
-        GR = np.zeros((2 * Mt,) * 3)
-        GR[np.ix_(idx % (2 * Mt), idx % (2 * Mt), idx % (2 * Mt))] = G[np.ix_(idx % ns, idx % ns, idx % ns)]
+        idx = [np.arange(-Mt[i], Mt[i]) for i in range(3)]
+        GR = np.zeros(tuple(2 * m for m in Mt))
+        GR[np.ix_(idx[0] % (2 * Mt[0]), idx[1] % (2 * Mt[1]), idx[2] % (2 * Mt[2]))] = \
+            G[np.ix_(idx[0] % ns[0], idx[1] % ns[1], idx[2] % ns[2])]
         return np.fft.fftn(GR).real
 
     # ---- step 1 ----------------------------------------------------------
@@ -171,26 +183,27 @@ class SEOracle:
         """Steps 2-4 of Alg. 4: returns H~ on the same grid as H.  With deriv = a
         (0, 1, 2) the scaling also multiplies by i k_a (method 2 of Sec. 7.2),
         which gives the derivative of H~ along direction a."""
-        D, h, M, Mt = self.D, self.h, self.M, self.Mt
+        D, h = self.D, self.h
         hat = self.win.hat
         if D == 3:
-            k = 2.0 * np.pi * np.fft.fftfreq(M, d=h)
-            kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+            k = [2.0 * np.pi * np.fft.fftfreq(m, d=h) for m in self.Mv]
+            kx, ky, kz = np.meshgrid(*k, indexing="ij")
             sig = self._sigma(kx ** 2 + ky ** 2 + kz ** 2, hat(kx) * hat(ky) * hat(kz), 0.0, 1.0)
             if deriv is not None:
-                sig = sig * self._ik_along(deriv, [M, M, M])
+                sig = sig * self._ik_along(deriv, list(self.Mv))
             return np.fft.ifftn(sig * np.fft.fftn(H)).real
         if D == 0:
-            n2 = 2 * Mt
-            Hp = np.zeros((n2,) * 3)
-            Hp[:Mt, :Mt, :Mt] = H
-            k = 2.0 * np.pi * np.fft.fftfreq(n2, d=h)                            # pi n / L~
-            kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+            Mt = self.Mt_v
+            n2 = [2 * m for m in Mt]
+            Hp = np.zeros(tuple(n2))
+            Hp[:Mt[0], :Mt[1], :Mt[2]] = H
+            k = [2.0 * np.pi * np.fft.fftfreq(m, d=h) for m in n2]                 # pi n / L~_i
+            kx, ky, kz = np.meshgrid(*k, indexing="ij")
             sig = np.exp(-(kx ** 2 + ky ** 2 + kz ** 2) / (4.0 * self.xi ** 2)) \
                 / (hat(kx) * hat(ky) * hat(kz)) ** 2 * self.GR
             if deriv is not None:
-                sig = sig * self._ik_along(deriv, [n2, n2, n2])
-            return np.fft.ifftn(sig * np.fft.fftn(Hp)).real[:Mt, :Mt, :Mt]
+                sig = sig * self._ik_along(deriv, n2)
+            return np.fft.ifftn(sig * np.fft.fftn(Hp)).real[:Mt[0], :Mt[1], :Mt[2]]
         return self._aft_scale_aift(H, deriv)
 
     def _ik_along(self, a, shape):
@@ -201,27 +214,31 @@ class SEOracle:
         return f.reshape(sh)
 
     def _classes(self):
-        """Periodic-mode classes of Sec. 3.4: zero mode, I (Eq. I: a box
-        |k_i| <= 2 pi n_l / L), J (the rest), with upsampling s0, s, 1
-        (Eq. upsamplings).  Returns boolean masks over the periodic mode grid."""
-        M, D, nl = self.M, self.D, self.g["nl"]
-        m = np.fft.fftfreq(M, d=1.0 / M).astype(np.int64)                        # signed mode index
-        grids = np.meshgrid(*([m] * D), indexing="ij")
-        amax = np.max(np.abs(np.stack(grids)), axis=0)
-        zero = amax == 0
-        inner = (amax <= nl) & ~zero
+        """Periodic-mode classes of Sec. 3.4: zero mode, I (Eq. I: a box of
+        mode indices |m_j| <= nI_j around k = 0), J (the rest), with the
+        free-direction transform lengths s0 M~_i, s M~_i and M~_i per free
+        axis (Eq. upsamplings).  Returns (mask over the periodic mode grid,
+        lengths of the free axes)."""
+        D = self.D
+        grids = np.meshgrid(*[np.fft.fftfreq(self.Mv[j], d=1.0 / self.Mv[j]).astype(np.int64) for j in range(D)],
+                            indexing="ij")
+        zero = np.all(np.stack([g == 0 for g in grids]), axis=0)
+        inner = np.all(np.stack([np.abs(grids[j]) <= self.g["nI"][j] for j in range(D)]), axis=0) & ~zero
         outer = ~zero & ~inner
-        return [(zero, self.g["s0Mt"]), (inner, self.g["sMt"]), (outer, self.Mt)]
+        free = range(D, 3)
+        return [(zero, [self.g["s0Mt_v"][i] for i in free]), (inner, [self.g["sMt_v"][i] for i in free]),
+                (outer, [self.Mt_v[i] for i in free])]
 
     def _aft_scale_aift(self, H, deriv=None):
         """Alg. 1 (AFT), scaling, Alg. 2 (AIFT) for D = 1, 2; deriv as in convolve."""
-        D, h, M, Mt = self.D, self.h, self.M, self.Mt
+        D, h = self.D, self.h
         hat = self.win.hat
         per_axes = tuple(range(D))
         free_axes_n = 3 - D
+        Mtf = [self.Mt_v[i] for i in range(D, 3)]
         Hk = np.fft.fftn(H, axes=per_axes)                       # Alg. 1 step 1
-        kp = 2.0 * np.pi * np.fft.fftfreq(M, d=h)
-        kgrid = np.meshgrid(*([kp] * D), indexing="ij")
+        kp = [2.0 * np.pi * np.fft.fftfreq(self.Mv[j], d=h) for j in range(D)]
+        kgrid = np.meshgrid(*kp, indexing="ij")
         kper2_all = sum(g ** 2 for g in kgrid)
         khat_all = np.prod([hat(g) for g in kgrid], axis=0)
         out = np.empty_like(Hk)
@@ -229,30 +246,30 @@ class SEOracle:
             if not mask.any():
                 continue
             lines = Hk[mask]                                     # (nc, Mt[, Mt])
-            padded = np.zeros((lines.shape[0],) + (nf,) * free_axes_n, dtype=complex)
-            sl = (slice(None),) + (slice(0, Mt),) * free_axes_n
+            padded = np.zeros((lines.shape[0],) + tuple(nf), dtype=complex)
+            sl = (slice(None),) + tuple(slice(0, m) for m in Mtf)
             padded[sl] = lines
             fax = tuple(range(1, 1 + free_axes_n))
             Fk = np.fft.fftn(padded, axes=fax)
-            kf = 2.0 * np.pi * np.fft.fftfreq(nf, d=h)            # 2 pi n / (s_f L~)
+            kf = [2.0 * np.pi * np.fft.fftfreq(m, d=h) for m in nf]   # 2 pi n / (s_f L~_i)
             if free_axes_n == 1:
-                kap = np.abs(kf)[None, :]
-                kaph = hat(kf)[None, :]
+                kap = np.abs(kf[0])[None, :]
+                kaph = hat(kf[0])[None, :]
             else:
-                a, b = np.meshgrid(kf, kf, indexing="ij")
+                a, b = np.meshgrid(kf[0], kf[1], indexing="ij")
                 kap = np.sqrt(a ** 2 + b ** 2)[None]
                 kaph = (hat(a) * hat(b))[None]
             kper2 = kper2_all[mask].reshape((-1,) + (1,) * free_axes_n)
             khat = khat_all[mask].reshape((-1,) + (1,) * free_axes_n)
             sig = self._sigma(kper2, khat, kap, kaph)
             if deriv is not None and deriv < D:                  # periodic direction
-                ikp = ik_factor(M, h)
-                ika = np.meshgrid(*([ikp if ax == deriv else np.ones(M) for ax in range(D)]), indexing="ij")
+                ika = np.meshgrid(*[ik_factor(self.Mv[j], h) if j == deriv else np.ones(self.Mv[j])
+                                    for j in range(D)], indexing="ij")
                 sig = sig * np.prod(ika, axis=0)[mask].reshape((-1,) + (1,) * free_axes_n)
             elif deriv is not None:                              # free direction deriv - D of the class grid
                 shp = [1] * (1 + free_axes_n)
-                shp[1 + deriv - D] = nf
-                sig = sig * ik_factor(nf, h).reshape(shp)
+                shp[1 + deriv - D] = nf[deriv - D]
+                sig = sig * ik_factor(nf[deriv - D], h).reshape(shp)
             back = np.fft.ifftn(sig * Fk, axes=fax)               # Alg. 2 steps 1-3
             out[mask] = back[sl]                                 # truncate to M~, merge (step 4)
         return np.fft.ifftn(out, axes=per_axes).real             # Alg. 2 step 5
