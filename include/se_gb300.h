@@ -110,18 +110,31 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the plan */
     int column_fft;       /* 1: the D = 0 z-direction FFT, scaling and inverse FFT run fused
                              in one kernel (se_opts.fft_mode) */
+    /* per axis (non-cubic boxes; the scalar fields above are the cube's values:
+       M of x, M~ / s0 M~ / s M~ of the first free axis, n_l of x) */
+    int M_v[3];           /* grid intervals L_i / h */
+    int Mt_v[3];          /* extended grid M~_i on free axes (M_i on periodic ones) */
+    int s0_mt_v[3];       /* zero-mode / free-space transform lengths of the free axes */
+    int s_mt_v[3];        /* set-I transform lengths of the free axes */
+    int n_I[3];           /* half-width of the set I in mode indices, periodic axes */
+    double L_v[3];        /* box sides */
 } se_plan_info_t;
 
 /* Fill *o with the "unset" values. */
 void se_opts_default(se_opts *o);
 
-/* Create a plan.  box[3] = side lengths (must be equal: cubic box); D = number
- * of periodic directions (the first D axes); xi = Ewald splitting parameter
- * (Eq. gamma); M = grid intervals per periodic direction (even); P = window
- * support in grid intervals (even, 2 <= P <= 16, P <= M); w, dt = window and
- * precision; opts may be NULL.  Sec. 3.3, Alg. 4 step 0, Sec. 6.  For D = 0 the
- * call also runs the precomputation of Alg. 3 on the current device (FP64).
- * Errors: SE_EINVAL (arguments), SE_ENOMEM, SE_ECUDA, SE_ECUFFT. */
+/* Create a plan.  box[3] = side lengths along x, y, z (Sec. 2: the box need
+ * not be a cube); D = number of periodic directions (the first D axes);
+ * xi = Ewald splitting parameter (Eq. gamma); M = grid intervals along x
+ * (even): the grid spacing h = box[0] / M is used on every axis, and every
+ * side must be an even multiple of h; P = window support in grid intervals
+ * (even, 2 <= P <= 16, P <= M and <= the grid of every periodic side);
+ * w, dt = window and precision; opts may be NULL.  Sec. 3.3, Alg. 4 step 0,
+ * Sec. 6, with the per-axis rules of the non-cubic box (the extended free
+ * sides, R = length of the extended free sides, s0 raised to 1 + R / L~_i
+ * where larger, s and n_l per free axis, the set I a box in k).  For D = 0
+ * the call also runs the precomputation of Alg. 3 on the current device
+ * (FP64).  Errors: SE_EINVAL (arguments), SE_ENOMEM, SE_ECUDA, SE_ECUFFT. */
 se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P,
                          se_window w, se_dtype dt, const se_opts *opts);
 

@@ -33,8 +33,9 @@ def _ptr(t):
 class Plan:
     """One Spectral Ewald configuration on one GPU (``se_plan_create``).
 
-    D: periodic directions (the first D axes); L: box side; xi: Ewald splitting
-    parameter; M: grid intervals per periodic direction; P: window support;
+    D: periodic directions (the first D axes); L: box side, or the three sides
+    of a non-cubic box (each an even multiple of h = L_x / M); xi: Ewald
+    splitting parameter; M: grid intervals along x; P: window support;
     window: "pkb" or "gaussian"; dtype: torch.float32 or torch.float64.
     Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
     shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants),
@@ -42,7 +43,7 @@ class Plan:
     fft_mode (1: cuFFT for every transform stage).
     """
 
-    def __init__(self, D: int, L: float, xi: float, M: int, P: int, window: str = "pkb",
+    def __init__(self, D: int, L, xi: float, M: int, P: int, window: str = "pkb",
                  dtype=torch.float32, device=None, lam=None, s0=None, s_mt=None, n_l=None, nu=None,
                  shape=None, aft_eps=None, tile=None, spread_mode=None, gather_mode=None, split=None,
                  force_method=None, fft_mode=None):
@@ -51,7 +52,12 @@ class Plan:
         if self.device.type != "cuda":
             raise ValueError("the Spectral Ewald library runs on CUDA devices only")
         self.dtype = dtype
-        self.D, self.L, self.xi, self.M, self.P, self.window = D, float(L), float(xi), M, P, window
+        sides = [float(v) for v in (L if hasattr(L, "__len__") else (L, L, L))]
+        if len(sides) != 3:
+            raise ValueError("L is one side or three sides")
+        self.box = tuple(sides)
+        self.L = sides[0] if sides[0] == sides[1] == sides[2] else self.box
+        self.D, self.xi, self.M, self.P, self.window = D, float(xi), M, P, window
         o = nat.Opts()
         self._lib.se_opts_default(ctypes.byref(o))
         if lam is not None: o.lambda_ = lam
@@ -67,7 +73,7 @@ class Plan:
         if split is not None: o.split = split
         if force_method is not None: o.force_method = force_method
         if fft_mode is not None: o.fft_mode = fft_mode
-        box = (ctypes.c_double * 3)(L, L, L)
+        box = (ctypes.c_double * 3)(*self.box)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             nat.check(self._lib.se_plan_create(ctypes.byref(h), box, D, float(xi), M, P, _WINDOWS[window],
@@ -97,6 +103,8 @@ class Plan:
         out = {f: getattr(i, f) for f, _ in nat.Info._fields_}
         out["grid"] = tuple(i.grid)
         out["tile"] = tuple(i.tile)
+        for f in ("M_v", "Mt_v", "s0_mt_v", "s_mt_v", "n_I", "L_v"):
+            out[f] = tuple(getattr(i, f))
         return out
 
     def set_profiling(self, enable: bool = True):

@@ -51,7 +51,9 @@ class Info(ctypes.Structure):
                 ("grid", ctypes.c_int * 3), ("tile", ctypes.c_int * 3), ("n_tiles", ctypes.c_int),
                 ("h", ctypes.c_double), ("L", ctypes.c_double), ("Lt", ctypes.c_double), ("R", ctypes.c_double),
                 ("delta_L", ctypes.c_double), ("xi", ctypes.c_double), ("shape", ctypes.c_double),
-                ("capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("column_fft", ctypes.c_int)]
+                ("capacity", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("column_fft", ctypes.c_int),
+                ("M_v", ctypes.c_int * 3), ("Mt_v", ctypes.c_int * 3), ("s0_mt_v", ctypes.c_int * 3),
+                ("s_mt_v", ctypes.c_int * 3), ("n_I", ctypes.c_int * 3), ("L_v", ctypes.c_double * 3)]
 
 
 _lib = None

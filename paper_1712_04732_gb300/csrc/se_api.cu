@@ -185,8 +185,8 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     if (!out) return fail(SE_EINVAL, "out is NULL");
     *out = nullptr;
     if (!box) return fail(SE_EINVAL, "box is NULL");
-    if (!(box[0] > 0) || box[0] != box[1] || box[0] != box[2] || !std::isfinite(box[0]))
-        return fail(SE_EINVAL, "the box must be cubic with a positive finite side");
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0) || !std::isfinite(box[a])) return fail(SE_EINVAL, "box sides must be positive and finite");
     if (D < 0 || D > 3) return fail(SE_EINVAL, "D must be 0, 1, 2 or 3");
     if (!(xi > 0) || !std::isfinite(xi)) return fail(SE_EINVAL, "xi must be positive");
     if (M < 2 || M % 2) return fail(SE_EINVAL, "M must be even and >= 2 (Sec. 3.3)");
@@ -203,6 +203,18 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     p->L = box[0]; p->xi = xi;
     p->h = p->L / M;
     p->inv_h = M / p->L;
+    // one spacing h on every axis: each side must be an even multiple of h
+    for (int a = 0; a < 3; ++a) {
+        const double m = box[a] / p->h;
+        const int mi = int(std::lround(m));
+        if (mi < 2 || mi % 2 || std::fabs(mi * p->h - box[a]) > 1e-9 * box[a]) {
+            delete p;
+            return fail(SE_EINVAL, "every box side must be an even multiple of h = box[0] / M");
+        }
+        p->Mv[a] = mi;
+        p->Lv[a] = box[a];
+        if (a < D && P > mi) { delete p; return fail(SE_EINVAL, "P must not exceed the grid of a periodic side"); }
+    }
     p->tile_pref = o.tile;
     p->spread_mode = o.spread_mode;
     p->gather_mode = o.gather_mode;
@@ -221,29 +233,53 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     p->nu = o.nu > 0 ? o.nu : std::min(P / 2 + 2, 9);
     if (p->nu > kMaxNu) { delete p; return fail(SE_EINVAL, "nu must be <= 12"); }
     p->aft_eps = o.aft_eps > 0 ? o.aft_eps : (dt == SE_F32 ? 1e-5 : 1e-10);
-    // Alg. 4 step 0 / Sec. 3.3: extended grid in the free directions
+    // Alg. 4 step 0 / Sec. 3.3: extended grid in the free directions, per axis
+    for (int a = 0; a < 3; ++a) {
+        p->Mtv[a] = p->s0v[a] = p->sv[a] = p->Mv[a];
+        p->Ltv[a] = p->Lv[a];
+    }
     if (D == 3) {
         p->Mt = M; p->Lt = p->L; p->R = 0; p->dL = 0;
     } else {
         static const double lam_g[3] = {1.0, 1.5, 1.5}, lam_k[3] = {1.3, 2.4, 2.4};
         const double lam = o.lambda > 0 ? o.lambda : (w == SE_WIN_GAUSSIAN ? lam_g[D] : lam_k[D]);
         if (lam < 1.0) { delete p; return fail(SE_EINVAL, "lambda must be >= 1 (Sec. 3.3)"); }
-        p->Mt = 2 * int(std::ceil((M + lam * P) / 2.0 - 1e-12));
-        p->Lt = p->h * p->Mt;
-        p->R = std::sqrt(double(3 - D)) * p->Lt;
-        p->dL = p->Lt - p->L;
+        double R2 = 0.0;
+        for (int a = D; a < 3; ++a) {
+            p->Mtv[a] = 2 * int(std::ceil((p->Mv[a] + lam * P) / 2.0 - 1e-12));
+            p->Ltv[a] = p->h * p->Mtv[a];
+            R2 += p->Ltv[a] * p->Ltv[a];
+        }
+        // R = length of the extended free sides (sqrt(3 - D) L~ for the cube)
+        p->R = std::sqrt(R2);
+        p->Mt = p->Mtv[D];
+        p->Lt = p->Ltv[D];
+        p->dL = p->Lt - p->Lv[D];
         static const double s0d[3] = {2.8, 2.5, 2.0};
         p->s0 = o.s0 > 0 ? o.s0 : s0d[D];
         if (p->s0 < 2.0) { delete p; return fail(SE_EINVAL, "s0 must be >= 2"); }
-        p->s0Mt = even_up(p->s0 * p->Mt);
+        // the oversampled free grid must hold the truncated kernel: s0_i >= 1 + R / L~_i
+        for (int a = D; a < 3; ++a) p->s0v[a] = even_up(std::max(p->s0, 1.0 + p->R / p->Ltv[a]) * p->Mtv[a]);
+        p->s0Mt = p->s0v[D];
         if (D != 0) {
             const double lg = std::log(1.0 / (2.0 * p->aft_eps)) / (2.0 * M_PI);
-            // Eqs. (estimate-s), (estimate-nl), with eps_rms / B = aft_eps
-            p->sMt = o.s_mt > 0 ? o.s_mt : even_up(M * (1.0 + lg));
-            p->nl = o.n_l >= 0 ? o.n_l : std::max(0, int(std::ceil(double(M) / (p->Mt - M) * lg - 1.0 - 1e-12)));
-            if (p->sMt < p->Mt) p->sMt = p->Mt;
-            if (p->sMt % 2) { delete p; return fail(SE_EINVAL, "s M~ must be even"); }
-            p->nl = std::min(p->nl, M / 2 - 1);
+            // Eqs. (estimate-s), (estimate-nl) per free axis, with eps_rms / B = aft_eps
+            double kl = 0.0;
+            for (int a = D; a < 3; ++a) {
+                int sm = o.s_mt > 0 ? o.s_mt : even_up(p->Mv[a] * (1.0 + lg));
+                if (sm < p->Mtv[a]) sm = p->Mtv[a];
+                if (sm % 2) { delete p; return fail(SE_EINVAL, "s M~ must be even"); }
+                p->sv[a] = sm;
+                const int nl = std::max(0, int(std::ceil(double(p->Mv[a]) / (p->Mtv[a] - p->Mv[a]) * lg - 1.0 - 1e-12)));
+                kl = std::max(kl, 2.0 * M_PI * (nl + 1) / p->Lv[a]);
+            }
+            // set I: the box |k_j| < k_l around k = 0, as mode indices per periodic axis
+            for (int j = 0; j < D; ++j) {
+                int nI = o.n_l >= 0 ? o.n_l : std::max(0, int(std::ceil(kl * p->Lv[j] / (2.0 * M_PI) - 1e-9)) - 1);
+                p->nIv[j] = std::min(nI, p->Mv[j] / 2 - 1);
+            }
+            p->sMt = p->sv[D];
+            p->nl = p->nIv[0];
         }
     }
     cudaError_t ce = cudaStreamSynchronize(nullptr);
@@ -296,6 +332,14 @@ se_status se_plan_get_info(se_plan_t p, se_plan_info_t *info)
     info->capacity = p->cap;
     info->device_bytes = p->device_bytes;
     info->column_fft = p->zcol ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        info->M_v[a] = p->Mv[a];
+        info->Mt_v[a] = p->Mtv[a];
+        info->s0_mt_v[a] = p->s0v[a];
+        info->s_mt_v[a] = p->sv[a];
+        info->n_I[a] = p->nIv[a];
+        info->L_v[a] = p->Lv[a];
+    }
     return SE_OK;
 }
 

@@ -61,8 +61,8 @@ struct ScaleBox {
     int n0, n1, n2;
     const T *f0, *f1, *f2, *k0, *k1, *k2;
     T norm;
-    int excl;      // 0: none; 1: i0 <= nl (D = 1); 2: i0 <= nl and (i1 <= nl or i1 >= n1 - nl) (D = 2)
-    int nl;
+    int excl;      // 0: none; 1: i0 <= nl (D = 1); 2: i0 <= nl and (i1 <= nl1 or i1 >= n1 - nl1) (D = 2)
+    int nl, nl1;   // half-widths of the set I along x and y (mode indices)
 };
 
 // Factor i k_a of method 2 (Sec. 7.2) for each element of a spectrum buffer of
@@ -96,6 +96,11 @@ struct se_plan_s {
     int D = 3, M = 0, P = 0, window = 0, dtype = 0;
     double L = 1, xi = 1, h = 1, inv_h = 1;
     int Mt = 0, s0Mt = 0, sMt = 0, nl = 0, nu = 0;
+    // per axis (Sec. 2 allows non-cubic boxes; h is common): grid intervals M_i = L_i / h,
+    // extended lengths M~_i (= M_i on periodic axes), zero-mode and set-I transform
+    // lengths of the free axes, half-widths of the set I along the periodic axes
+    int Mv[3] = {0, 0, 0}, Mtv[3] = {0, 0, 0}, s0v[3] = {0, 0, 0}, sv[3] = {0, 0, 0}, nIv[3] = {0, 0, 0};
+    double Lv[3] = {1, 1, 1}, Ltv[3] = {1, 1, 1};
     double Lt = 1, R = 0, dL = 0, s0 = 0, shape = 0, aft_eps = 0;
     double off[3] = {0, 0, 0};
     se::TileGeom tg{};

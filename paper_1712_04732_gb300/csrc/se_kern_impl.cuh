@@ -56,12 +56,12 @@ static BinArgs<T> bin_args(const se_plan_s *p)
         a.off[d] = T(p->off[d]);
         // largest representable t below M + delta_M/2 (free axes): keeps the
         // support inside the extended grid for x within an ulp of L
-        double tm = (p->L + p->off[d]) * p->inv_h;
+        double tm = (p->Lv[d] + p->off[d]) * p->inv_h;
         a.tmax[d] = std::nextafter(T(tm), T(0));
         if (double(a.tmax[d]) >= tm) a.tmax[d] = std::nextafter(a.tmax[d], T(0));
+        a.L[d] = T(p->Lv[d]);
+        a.inv_L[d] = T(1.0 / p->Lv[d]);
     }
-    a.L = T(p->L);
-    a.inv_L = T(1.0 / p->L);
     a.inv_h = T(p->inv_h);
     a.half = p->P / 2 - 1;
     return a;
@@ -343,15 +343,16 @@ static se_status forward(se_plan_s *p, void *gin)
     if (p->D == 3) return SE_OK;
     C *U = reinterpret_cast<C *>(p->U);
     C *Z = reinterpret_cast<C *>(p->Z);
-    const int row = p->M / 2 + 1;
+    const int row = p->Mv[0] / 2 + 1;
     // Alg. 1 steps 2-3: zero mode and set I into their padded buffers
     if (p->D == 2) {
-        const int64_t n = int64_t(p->nI) * p->sMt + p->s0Mt;
-        k_pad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, p->s0Mt, row,
-                                                               int64_t(p->M) * row, spec, U, Z);
+        const int64_t n = int64_t(p->nI) * p->sv[2] + p->s0v[2];
+        k_pad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mtv[2], p->sv[2], p->s0v[2], row,
+                                                               int64_t(p->Mv[1]) * row, spec, U, Z);
     } else {
-        const int64_t n = int64_t(p->nl) * p->sMt * p->sMt + int64_t(p->s0Mt) * p->s0Mt;
-        k_pad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
+        const int64_t n = int64_t(p->nI) * p->sv[1] * p->sv[2] + int64_t(p->s0v[1]) * p->s0v[2];
+        k_pad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->Mtv[1], p->Mtv[2], p->sv[1], p->sv[2],
+                                                               p->s0v[1], p->s0v[2], row, spec, U, Z);
     }
     SE_LAUNCH_CHECK("pad");
     // Alg. 1 steps 2-4: free-direction transforms of every class
@@ -417,19 +418,20 @@ static se_status inverse(se_plan_s *p, typename Cplx<T>::type *spec, typename Cp
         return SE_OK;
     }
     if (p->D != 3) {
-        const int row = p->M / 2 + 1;
+        const int row = p->Mv[0] / 2 + 1;
         // Alg. 2 steps 1-3
         if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "free inv");
         if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "I inv");
         if ((r = fft_c2c(p->free_Z, Z, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "zero inv");
         // Alg. 2 steps 2-4: truncate to M~ and merge back
         if (p->D == 2) {
-            const int64_t n = int64_t(p->nI) * p->Mt + p->Mt;
-            k_unpad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mt, p->sMt, row,
-                                                                     int64_t(p->M) * row, spec, U, Z);
+            const int64_t n = int64_t(p->nI) * p->Mtv[2] + p->Mtv[2];
+            k_unpad_2p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->I_lines, p->Mtv[2], p->sv[2], row,
+                                                                     int64_t(p->Mv[1]) * row, spec, U, Z);
         } else {
-            const int64_t n = int64_t(p->nl) * p->Mt * p->Mt + int64_t(p->Mt) * p->Mt;
-            k_unpad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nl, p->Mt, p->sMt, p->s0Mt, row, spec, U, Z);
+            const int64_t n = int64_t(p->nI) * p->Mtv[1] * p->Mtv[2] + int64_t(p->Mtv[1]) * p->Mtv[2];
+            k_unpad_1p<T><<<blocks_for(n, 256), 256, 0, p->stream>>>(p->nI, p->Mtv[1], p->Mtv[2], p->sv[1], p->sv[2],
+                                                                     p->s0v[1], row, spec, U, Z);
         }
         SE_LAUNCH_CHECK("unpad");
     }

@@ -29,7 +29,7 @@ constexpr int kErrNotFinite = 2;
 template <typename R>
 struct BinArgs {
     int n[3], periodic[3], T[3], nt[3];
-    R L, inv_L, inv_h, off[3], tmax[3];
+    R L[3], inv_L[3], inv_h, off[3], tmax[3];
     int half;   // P/2 - 1: anchor = floor(t) - half
 };
 
@@ -50,12 +50,12 @@ __device__ __forceinline__ bool locate(const BinArgs<T> &a, const T *xp, T &qv, 
         T t;
         if (!isfinite(x)) { if (err) atomicOr(err, kErrNotFinite); x = T(0); ok = false; }
         if (a.periodic[d]) {
-            x = x - a.L * dfloor(x * a.inv_L);
+            x = x - a.L[d] * dfloor(x * a.inv_L[d]);
             t = x * a.inv_h;
             if (t >= T(a.n[d])) t -= T(a.n[d]);
             if (t < T(0)) t = T(0);
         } else {
-            if (!(x >= T(0) && x < a.L)) { if (ok && err) atomicOr(err, kErrOutOfBox); x = T(0); ok = false; }
+            if (!(x >= T(0) && x < a.L[d])) { if (ok && err) atomicOr(err, kErrOutOfBox); x = T(0); ok = false; }
             t = (x + a.off[d]) * a.inv_h;
             if (t > a.tmax[d]) t = a.tmax[d];
         }
@@ -600,7 +600,7 @@ __global__ void k_scale_box(ScaleBox<T> sb, typename Cplx<T>::type *__restrict__
     const int i0 = int(i % sb.n0), i1 = int((i / sb.n0) % sb.n1), i2 = int(i / (int64_t(sb.n0) * sb.n1));
     bool excl = false;
     if (sb.excl == 1) excl = i0 <= sb.nl;
-    else if (sb.excl == 2) excl = i0 <= sb.nl && (i1 <= sb.nl || i1 >= sb.n1 - sb.nl);
+    else if (sb.excl == 2) excl = i0 <= sb.nl && (i1 <= sb.nl1 || i1 >= sb.n1 - sb.nl1);
     const T den = sb.k0[i0] + sb.k1[i1] + sb.k2[i2];
     T s = (excl || den == T(0)) ? T(0) : sb.norm * sb.f0[i0] * sb.f1[i1] * sb.f2[i2] / den;
     typename Cplx<T>::type v = data[i];
@@ -650,7 +650,7 @@ __global__ void k_scale_box_ik(ScaleBox<T> sb, IkBox<T> ib, typename Cplx<T>::ty
     const int i0 = int(i % sb.n0), i1 = int((i / sb.n0) % sb.n1), i2 = int(i / (int64_t(sb.n0) * sb.n1));
     bool excl = false;
     if (sb.excl == 1) excl = i0 <= sb.nl;
-    else if (sb.excl == 2) excl = i0 <= sb.nl && (i1 <= sb.nl || i1 >= sb.n1 - sb.nl);
+    else if (sb.excl == 2) excl = i0 <= sb.nl && (i1 <= sb.nl1 || i1 >= sb.n1 - sb.nl1);
     const T den = sb.k0[i0] + sb.k1[i1] + sb.k2[i2];
     T s = (excl || den == T(0)) ? T(0) : sb.norm * sb.f0[i0] * sb.f1[i1] * sb.f2[i2] / den;
     typename Cplx<T>::type v = data[i];
@@ -864,8 +864,11 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
 
 // ----------------------------------------------------------------- AFT padding
 // Alg. 1 steps 2-3 / Alg. 2 steps 2-4 for D = 2: copy the z-lines of the zero
-// mode and of the set I out of the spectrum (layout [z][ky][kx], row = M/2 + 1,
-// zstride = M row) into zero-padded buffers of length s0 M~ and s M~, and back.
+// mode and of the set I out of the spectrum (layout [z][ky][kx], row = M_0/2 + 1,
+// zstride = M_1 row) into zero-padded buffers of length s0 M~_2 and s M~_2, and
+// back.  D = 1: the (z, y) planes of the zero mode and of kx = 1..n_I out of the
+// spectrum (layout [z][y][kx]) into padded planes s0M~_1 x s0M~_2 (z1, z2) and
+// sM~_1 x sM~_2 (s1, s2), y fastest, and back.
 template <typename T>
 __global__ void k_pad_2p(int nI, const int2 *__restrict__ lines, int Mt, int sMt, int s0Mt, int row,
                          int64_t zstride, const typename Cplx<T>::type *__restrict__ spec,
@@ -906,11 +909,12 @@ __global__ void k_unpad_2p(int nI, const int2 *__restrict__ lines, int Mt, int s
 // D = 1: the planes kx = 1..n_l (set I) and kx = 0 (zero mode) of the spectrum
 // (layout [z][y][kx], row = M/2 + 1) padded to (s M~)^2 and (s0 M~)^2, and back.
 template <typename T>
-__global__ void k_pad_1p(int nl, int Mt, int sMt, int s0Mt, int row, const typename Cplx<T>::type *__restrict__ spec,
-                         typename Cplx<T>::type *__restrict__ U, typename Cplx<T>::type *__restrict__ Z)
+__global__ void k_pad_1p(int nl, int Mt1, int Mt2, int s1, int s2, int z1, int z2, int row,
+                         const typename Cplx<T>::type *__restrict__ spec, typename Cplx<T>::type *__restrict__ U,
+                         typename Cplx<T>::type *__restrict__ Z)
 {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t plane = int64_t(sMt) * sMt;
+    const int64_t plane = int64_t(s1) * s2;
     const int64_t nU = nl * plane;
     typename Cplx<T>::type zero;
     zero.x = T(0);
@@ -918,31 +922,32 @@ __global__ void k_pad_1p(int nl, int Mt, int sMt, int s0Mt, int row, const typen
     if (i < nU) {
         const int p = int(i / plane);
         const int64_t r = i % plane;
-        const int z = int(r / sMt), y = int(r % sMt);
-        U[i] = (y < Mt && z < Mt) ? spec[(int64_t(z) * Mt + y) * row + p + 1] : zero;
-    } else if (i < nU + int64_t(s0Mt) * s0Mt) {
+        const int z = int(r / s1), y = int(r % s1);
+        U[i] = (y < Mt1 && z < Mt2) ? spec[(int64_t(z) * Mt1 + y) * row + p + 1] : zero;
+    } else if (i < nU + int64_t(z1) * z2) {
         const int64_t r = i - nU;
-        const int z = int(r / s0Mt), y = int(r % s0Mt);
-        Z[r] = (y < Mt && z < Mt) ? spec[(int64_t(z) * Mt + y) * row] : zero;
+        const int z = int(r / z1), y = int(r % z1);
+        Z[r] = (y < Mt1 && z < Mt2) ? spec[(int64_t(z) * Mt1 + y) * row] : zero;
     }
 }
 
 template <typename T>
-__global__ void k_unpad_1p(int nl, int Mt, int sMt, int s0Mt, int row, typename Cplx<T>::type *__restrict__ spec,
-                           const typename Cplx<T>::type *__restrict__ U, const typename Cplx<T>::type *__restrict__ Z)
+__global__ void k_unpad_1p(int nl, int Mt1, int Mt2, int s1, int s2, int z1, int row,
+                           typename Cplx<T>::type *__restrict__ spec, const typename Cplx<T>::type *__restrict__ U,
+                           const typename Cplx<T>::type *__restrict__ Z)
 {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t pl = int64_t(Mt) * Mt;
+    const int64_t pl = int64_t(Mt1) * Mt2;
     const int64_t nU = nl * pl;
     if (i < nU) {
         const int p = int(i / pl);
         const int64_t r = i % pl;
-        const int z = int(r / Mt), y = int(r % Mt);
-        spec[(int64_t(z) * Mt + y) * row + p + 1] = U[int64_t(p) * sMt * sMt + int64_t(z) * sMt + y];
+        const int z = int(r / Mt1), y = int(r % Mt1);
+        spec[(int64_t(z) * Mt1 + y) * row + p + 1] = U[int64_t(p) * s1 * s2 + int64_t(z) * s1 + y];
     } else if (i < nU + pl) {
         const int64_t r = i - nU;
-        const int z = int(r / Mt), y = int(r % Mt);
-        spec[(int64_t(z) * Mt + y) * row] = Z[int64_t(z) * s0Mt + y];
+        const int z = int(r / Mt1), y = int(r % Mt1);
+        spec[(int64_t(z) * Mt1 + y) * row] = Z[int64_t(z) * z1 + y];
     }
 }
 

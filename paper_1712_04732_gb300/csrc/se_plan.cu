@@ -170,14 +170,22 @@ static std::vector<double> ik_axis(const se_plan_s *p, int nf)
 
 // ------------------------------------------------------------ Alg. 3 (D = 0), FP64 on the device
 
-__global__ void k_green0_samples(int ns, double dk, double R, cufftDoubleComplex *out)
+struct Dim3 {
+    int n[3];
+};
+
+__device__ __forceinline__ int signed_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// samples of G^{0P} at k_i = dk_i m_i on the s0M~_0 x s0M~_1 x s0M~_2 grid (x fastest)
+__global__ void k_green0_samples(Dim3 ns, double dk0, double dk1, double dk2, double R, cufftDoubleComplex *out)
 {
-    const int64_t n = int64_t(ns) * ns * ns;
+    const int64_t n = int64_t(ns.n[0]) * ns.n[1] * ns.n[2];
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    const int a = int(i % ns), b = int((i / ns) % ns), c = int(i / (int64_t(ns) * ns));
-    const int sa = a < ns / 2 ? a : a - ns, sb = b < ns / 2 ? b : b - ns, sc = c < ns / 2 ? c : c - ns;
-    const double k = dk * sqrt(double(sa) * sa + double(sb) * sb + double(sc) * sc);
+    const int a = int(i % ns.n[0]), b = int((i / ns.n[0]) % ns.n[1]), c = int(i / (int64_t(ns.n[0]) * ns.n[1]));
+    const double k0 = dk0 * signed_index(a, ns.n[0]), k1 = dk1 * signed_index(b, ns.n[1]),
+                 k2 = dk2 * signed_index(c, ns.n[2]);
+    const double k = sqrt(k0 * k0 + k1 * k1 + k2 * k2);
     double g;
     if (k == 0.0) g = R * R / 2.0;                         // Eq. (G_hat_0d) at k = 0
     else { const double s = sin(R * k / 2.0) / k; g = 2.0 * s * s; }
@@ -185,81 +193,101 @@ __global__ void k_green0_samples(int ns, double dk, double R, cufftDoubleComplex
     out[i].y = 0.0;
 }
 
-// keep j in [-M~, M~ - 1]^3 (wrapped) of the (s0 M~)^3 inverse transform on a (2 M~)^3 grid
-__global__ void k_green0_truncate(int ns, int Mt, double scale, const cufftDoubleComplex *in, double *out)
+// keep j_i in [-M~_i, M~_i - 1] (wrapped) of the oversampled inverse transform on
+// the 2M~_0 x 2M~_1 x 2M~_2 grid
+__global__ void k_green0_truncate(Dim3 ns, Dim3 Mt, double scale, const cufftDoubleComplex *in, double *out)
 {
-    const int n2 = 2 * Mt;
-    const int64_t n = int64_t(n2) * n2 * n2;
+    const int n0 = 2 * Mt.n[0], n1 = 2 * Mt.n[1], n2 = 2 * Mt.n[2];
+    const int64_t n = int64_t(n0) * n1 * n2;
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    const int a = int(i % n2), b = int((i / n2) % n2), c = int(i / (int64_t(n2) * n2));
-    const int sa = a < Mt ? a : a - n2, sb = b < Mt ? b : b - n2, sc = c < Mt ? c : c - n2;
-    const int ia = (sa + ns) % ns, ib = (sb + ns) % ns, ic = (sc + ns) % ns;
-    out[i] = in[(int64_t(ic) * ns + ib) * ns + ia].x * scale;
+    const int a = int(i % n0), b = int((i / n0) % n1), c = int(i / (int64_t(n0) * n1));
+    const int sa = a < Mt.n[0] ? a : a - n0, sb = b < Mt.n[1] ? b : b - n1, sc = c < Mt.n[2] ? c : c - n2;
+    const int ia = (sa + ns.n[0]) % ns.n[0], ib = (sb + ns.n[1]) % ns.n[1], ic = (sc + ns.n[2]) % ns.n[2];
+    out[i] = in[(int64_t(ic) * ns.n[1] + ib) * ns.n[0] + ia].x * scale;
 }
 
+// sigma on the R2C box (M~_0 + 1) x 2M~_1 x 2M~_2 from the per-axis factors
 template <typename T>
-__global__ void k_sigma0(int Mt, double norm, const double *fax, const cufftDoubleComplex *gr, T *out)
+__global__ void k_sigma0(Dim3 Mt, double norm, const double *f0, const double *f1, const double *f2,
+                         const cufftDoubleComplex *gr, T *out)
 {
-    const int n2 = 2 * Mt, nx = Mt + 1;
-    const int64_t n = int64_t(n2) * n2 * nx;
+    const int nx = Mt.n[0] + 1, n1 = 2 * Mt.n[1], n2 = 2 * Mt.n[2];
+    const int64_t n = int64_t(nx) * n1 * n2;
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    const int a = int(i % nx), b = int((i / nx) % n2), c = int(i / (int64_t(nx) * n2));
-    out[i] = T(norm * fax[a] * fax[b] * fax[c] * gr[i].x);
+    const int a = int(i % nx), b = int((i / nx) % n1), c = int(i / (int64_t(nx) * n1));
+    out[i] = T(norm * f0[a] * f1[b] * f2[c] * gr[i].x);
 }
 
 static se_status precompute_free_space(se_plan_s *p)
 {
-    const int Mt = p->Mt, ns = p->s0Mt, n2 = 2 * Mt;
-    const int64_t nsamp = int64_t(ns) * ns * ns;
-    const int64_t ngr = int64_t(n2) * n2 * n2;
-    const int64_t nhat = int64_t(n2) * n2 * (Mt + 1);
+    Dim3 ns, Mt;
+    for (int a = 0; a < 3; ++a) {
+        ns.n[a] = p->s0v[a];
+        Mt.n[a] = p->Mtv[a];
+    }
+    const int64_t nsamp = int64_t(ns.n[0]) * ns.n[1] * ns.n[2];
+    const int64_t ngr = int64_t(8) * Mt.n[0] * Mt.n[1] * Mt.n[2];
+    const int64_t nhat = int64_t(Mt.n[0] + 1) * (2 * Mt.n[1]) * (2 * Mt.n[2]);
     void *samp = nullptr, *gr = nullptr, *grh = nullptr, *fax = nullptr;
     se_status st = SE_OK;
     cufftHandle h1 = 0, h2 = 0;
     bool have1 = false, have2 = false;
     cufftResult r;
-    std::vector<double> f, k2;
-    axis_tables(p, n2, f, k2);
-    const double norm = 4.0 * M_PI * p->h * p->h * p->h / (double(n2) * n2 * n2);
+    std::vector<double> f[3], k2;
+    for (int a = 0; a < 3; ++a) axis_tables(p, 2 * Mt.n[a], f[a], k2);
+    std::vector<double> fall;
+    for (int a = 0; a < 3; ++a) fall.insert(fall.end(), f[a].begin(), f[a].end());
+    const double norm = 4.0 * M_PI * p->h * p->h * p->h / (double(ngr));
+    const double *fd = nullptr;
     if ((st = dev_alloc(p, &samp, sizeof(cufftDoubleComplex) * nsamp)) != SE_OK) goto done;
     if ((st = dev_alloc(p, &gr, sizeof(double) * ngr)) != SE_OK) goto done;
     if ((st = dev_alloc(p, &grh, sizeof(cufftDoubleComplex) * nhat)) != SE_OK) goto done;
-    if ((st = dev_alloc(p, &fax, sizeof(double) * n2)) != SE_OK) goto done;
-    if (cudaMemcpy(fax, f.data(), sizeof(double) * n2, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if ((st = dev_alloc(p, &fax, sizeof(double) * fall.size())) != SE_OK) goto done;
+    if (cudaMemcpy(fax, fall.data(), sizeof(double) * fall.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         st = cuda_fail(cudaGetLastError(), "precompute upload");
         goto done;
     }
-    // step 1: samples of G^{0P} at k = 2 pi n / (s0 L~)
-    k_green0_samples<<<unsigned((nsamp + 255) / 256), 256, 0, p->stream>>>(ns, 2.0 * M_PI / (ns * p->h), p->R,
-                                                                           (cufftDoubleComplex *)samp);
-    // step 2: 3D inverse FFT (normalised by 1/(s0 M~)^3 in step 3)
-    if ((r = cufftPlan3d(&h1, ns, ns, ns, CUFFT_Z2Z)) != CUFFT_SUCCESS) { st = cufft_fail(r, "precompute plan"); goto done; }
+    fd = static_cast<const double *>(fax);
+    // step 1: samples of G^{0P} at k_i = 2 pi m / (s0M~_i h)
+    k_green0_samples<<<unsigned((nsamp + 255) / 256), 256, 0, p->stream>>>(
+        ns, 2.0 * M_PI / (ns.n[0] * p->h), 2.0 * M_PI / (ns.n[1] * p->h), 2.0 * M_PI / (ns.n[2] * p->h), p->R,
+        (cufftDoubleComplex *)samp);
+    // step 2: 3D inverse FFT (normalised by 1 / (number of samples) in step 3)
+    if ((r = cufftPlan3d(&h1, ns.n[2], ns.n[1], ns.n[0], CUFFT_Z2Z)) != CUFFT_SUCCESS) {
+        st = cufft_fail(r, "precompute plan");
+        goto done;
+    }
     have1 = true;
     cufftSetStream(h1, p->stream);
     if ((r = cufftExecZ2Z(h1, (cufftDoubleComplex *)samp, (cufftDoubleComplex *)samp, CUFFT_INVERSE)) != CUFFT_SUCCESS) {
         st = cufft_fail(r, "precompute inverse");
         goto done;
     }
-    // step 3: truncate to (2 M~)^3
+    // step 3: truncate to 2M~_0 x 2M~_1 x 2M~_2
     k_green0_truncate<<<unsigned((ngr + 255) / 256), 256, 0, p->stream>>>(
         ns, Mt, 1.0 / double(nsamp), (const cufftDoubleComplex *)samp, (double *)gr);
-    // step 4: 3D FFT -> G^{0P}_R at k = pi n / L~
-    if ((r = cufftPlan3d(&h2, n2, n2, n2, CUFFT_D2Z)) != CUFFT_SUCCESS) { st = cufft_fail(r, "precompute plan 2"); goto done; }
+    // step 4: 3D FFT -> G^{0P}_R at k_i = pi m / L~_i
+    if ((r = cufftPlan3d(&h2, 2 * Mt.n[2], 2 * Mt.n[1], 2 * Mt.n[0], CUFFT_D2Z)) != CUFFT_SUCCESS) {
+        st = cufft_fail(r, "precompute plan 2");
+        goto done;
+    }
     have2 = true;
     cufftSetStream(h2, p->stream);
     if ((r = cufftExecD2Z(h2, (double *)gr, (cufftDoubleComplex *)grh)) != CUFFT_SUCCESS) {
         st = cufft_fail(r, "precompute forward");
         goto done;
     }
-    // sigma = 4 pi h^3 / (2 M~)^3 * prod_i e^{-k_i^2/4xi^2} / W^0(k_i)^2 * G^{0P}_R
+    // sigma = 4 pi h^3 / (8 M~_0 M~_1 M~_2) * prod_i e^{-k_i^2/4xi^2} / W^0(k_i)^2 * G^{0P}_R
     if (p->dtype == SE_F32)
         k_sigma0<float><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
-            Mt, norm, (const double *)fax, (const cufftDoubleComplex *)grh, (float *)p->sigma_tab);
+            Mt, norm, fd, fd + 2 * Mt.n[0], fd + 2 * Mt.n[0] + 2 * Mt.n[1], (const cufftDoubleComplex *)grh,
+            (float *)p->sigma_tab);
     else
         k_sigma0<double><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
-            Mt, norm, (const double *)fax, (const cufftDoubleComplex *)grh, (double *)p->sigma_tab);
+            Mt, norm, fd, fd + 2 * Mt.n[0], fd + 2 * Mt.n[0] + 2 * Mt.n[1], (const cufftDoubleComplex *)grh,
+            (double *)p->sigma_tab);
     {
         cudaError_t e = cudaStreamSynchronize(p->stream);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -308,7 +336,8 @@ static ScaleBox<T> make_box(const se_plan_s *p, int n0, int n1, int n2, size_t f
     b.f2 = base + f2; b.k2 = base + k2;
     b.norm = T(norm);
     b.excl = excl;
-    b.nl = p->nl;
+    b.nl = p->nIv[0];
+    b.nl1 = p->nIv[1];
     return b;
 }
 
@@ -318,79 +347,103 @@ static se_status upload(const void *host, void *dev, size_t bytes, const char *w
     return e == cudaSuccess ? SE_OK : cuda_fail(e, what);
 }
 
+// Number of lines of the set I for D = 2 (half spectrum in x): |kx| <= nI_0 (kx >= 0),
+// |ky| <= nI_1, without the zero mode.  D = 1: the planes kx = 1..nI_0.
+static int count_I(const se_plan_s *p)
+{
+    if (p->D == 2) return (p->nIv[0] + 1) * (2 * p->nIv[1] + 1) - 1;
+    if (p->D == 1) return p->nIv[0];
+    return 0;
+}
+
 static se_status build_tables(se_plan_s *p)
 {
-    const int M = p->M, Mt = p->Mt, D = p->D;
+    const int D = p->D;
+    const int *Mv = p->Mv, *Mtv = p->Mtv;
     const double h3 = p->h * p->h * p->h, fpi = 4.0 * M_PI * h3;
+    // length of the main transform along each axis (D = 0: the zero-padded 2 M~_i)
+    int len[3];
+    for (int a = 0; a < 3; ++a) len[a] = a < D ? Mv[a] : (D == 0 ? 2 * Mtv[a] : Mtv[a]);
     TabBuilder tb;
-    std::vector<double> fper, kper, fJ, kJ, fI, kI, fZ, kZ;
-    axis_tables(p, M, fper, kper);
-    const size_t o_fper = tb.add(fper), o_kper = tb.add(kper);
+    std::vector<double> f[3], k2[3];
+    size_t o_f[3], o_k[3];
+    for (int a = 0; a < 3; ++a) {
+        axis_tables(p, len[a], f[a], k2[a]);
+        o_f[a] = tb.add(f[a]);
+        o_k[a] = tb.add(k2[a]);
+    }
     const size_t o_one = tb.add({1.0}), o_zero = tb.add({0.0});
-    size_t o_fJ = 0, o_kJ = 0, o_fI = 0, o_kI = 0, o_fl = 0, o_kl = 0;
+    std::vector<double> fI[3], kI[3], fZ[3], kZ[3];
+    size_t o_fI[3] = {0, 0, 0}, o_kI[3] = {0, 0, 0}, o_fl = 0, o_kl = 0;
     std::vector<double> sig0;
     std::vector<int2> lines;
+    const int nI = count_I(p);
     if (D == 1 || D == 2) {
-        axis_tables(p, Mt, fJ, kJ);
-        o_fJ = tb.add(fJ);
-        o_kJ = tb.add(kJ);
-        if (p->nl > 0) {
-            axis_tables(p, p->sMt, fI, kI);
-            o_fI = tb.add(fI);
-            o_kI = tb.add(kI);
+        for (int a = D; a < 3; ++a) {
+            if (nI > 0) {
+                axis_tables(p, p->sv[a], fI[a], kI[a]);
+                o_fI[a] = tb.add(fI[a]);
+                o_kI[a] = tb.add(kI[a]);
+            }
+            axis_tables(p, p->s0v[a], fZ[a], kZ[a]);
         }
-        axis_tables(p, p->s0Mt, fZ, kZ);
         std::vector<double> fl, kl;
         if (D == 2) {
-            for (int ky = -p->nl; ky <= p->nl; ++ky)
-                for (int kx = 0; kx <= p->nl; ++kx) {
+            const int M1 = Mv[1];
+            for (int ky = -p->nIv[1]; ky <= p->nIv[1]; ++ky)
+                for (int kx = 0; kx <= p->nIv[0]; ++kx) {
                     if (kx == 0 && ky == 0) continue;
-                    const int iy = (ky + M) % M;
+                    const int iy = (ky + M1) % M1;
                     lines.push_back(make_int2(kx, iy));
-                    fl.push_back(fper[kx] * fper[iy]);
-                    kl.push_back(kper[kx] + kper[iy]);
+                    fl.push_back(f[0][kx] * f[1][iy]);
+                    kl.push_back(k2[0][kx] + k2[1][iy]);
                 }
-            p->nI = int(lines.size());
-            // zero mode: sigma(kz) = 4 pi h^3 / (M^2 s0 M~) f(0)^2 f(kz) G^{2P}(0, kz)
-            sig0.resize(p->s0Mt);
-            const double nz = fpi / (double(M) * M * p->s0Mt);
-            for (int m = 0; m < p->s0Mt; ++m)
-                sig0[m] = nz * fper[0] * fper[0] * fZ[m] * green_zero_2p(p->R, std::sqrt(kZ[m]));
+            // zero mode: sigma(kz) = 4 pi h^3 / (M_0 M_1 s0M~_2) f(0)^2 f(kz) G^{2P}(0, kz)
+            const int s2 = p->s0v[2];
+            sig0.resize(s2);
+            const double nz = fpi / (double(Mv[0]) * Mv[1] * s2);
+            for (int m = 0; m < s2; ++m)
+                sig0[m] = nz * f[0][0] * f[1][0] * fZ[2][m] * green_zero_2p(p->R, std::sqrt(kZ[2][m]));
         } else {
-            for (int pl = 0; pl < p->nl; ++pl) {
-                fl.push_back(fper[pl + 1]);
-                kl.push_back(kper[pl + 1]);
+            for (int pl = 0; pl < nI; ++pl) {
+                fl.push_back(f[0][pl + 1]);
+                kl.push_back(k2[0][pl + 1]);
             }
-            // zero plane: sigma(ky, kz) = 4 pi h^3 / (M (s0 M~)^2) f(0) f(ky) f(kz) G^{1P}(0, |kappa|)
-            const int s = p->s0Mt;
-            sig0.resize(size_t(s) * s);
-            const double nz = fpi / (double(M) * s * s);
-            for (int z = 0; z < s; ++z)
-                for (int y = 0; y < s; ++y)
-                    sig0[size_t(z) * s + y] = nz * fper[0] * fZ[y] * fZ[z] * green_zero_1p(p->R, std::sqrt(kZ[y] + kZ[z]));
+            // zero plane [z][y]: sigma = 4 pi h^3 / (M_0 s0M~_1 s0M~_2) f(0) f(ky) f(kz) G^{1P}(0, |kappa|)
+            const int s1 = p->s0v[1], s2 = p->s0v[2];
+            sig0.resize(size_t(s1) * s2);
+            const double nz = fpi / (double(Mv[0]) * s1 * s2);
+            for (int z = 0; z < s2; ++z)
+                for (int y = 0; y < s1; ++y)
+                    sig0[size_t(z) * s1 + y] =
+                        nz * f[0][0] * fZ[1][y] * fZ[2][z] * green_zero_1p(p->R, std::sqrt(kZ[1][y] + kZ[2][z]));
         }
         if (!fl.empty()) {
             o_fl = tb.add(fl);
             o_kl = tb.add(kl);
         }
     }
-    // method 2 (Sec. 7.2): signed k per transform length and per I line / plane
-    const size_t o_dM = tb.add(ik_axis(p, M));
-    size_t o_dMt = 0, o_dsMt = 0, o_ds0Mt = 0, o_d2Mt = 0, o_dlx = 0, o_dly = 0;
-    if (D == 0) o_d2Mt = tb.add(ik_axis(p, 2 * Mt));
+    p->nI = nI;
+    // method 2 (Sec. 7.2): signed k per axis and transform length, per I line / plane
+    size_t o_d[3], o_dI[3] = {0, 0, 0}, o_dZ[3] = {0, 0, 0}, o_dlx = 0, o_dly = 0;
+    std::vector<double> kd[3];
+    for (int a = 0; a < 3; ++a) {
+        kd[a] = ik_axis(p, len[a]);
+        o_d[a] = tb.add(kd[a]);
+    }
     if (D == 1 || D == 2) {
-        o_dMt = tb.add(ik_axis(p, Mt));
-        if (p->nl > 0) o_dsMt = tb.add(ik_axis(p, p->sMt));
-        o_ds0Mt = tb.add(ik_axis(p, p->s0Mt));
-        const std::vector<double> kM = ik_axis(p, M);
+        for (int a = D; a < 3; ++a) {
+            if (nI > 0) o_dI[a] = tb.add(ik_axis(p, p->sv[a]));
+            o_dZ[a] = tb.add(ik_axis(p, p->s0v[a]));
+        }
         std::vector<double> lx, ly;
         if (D == 2) {
             for (const int2 &l : lines) {
-                lx.push_back(kM[l.x]);
-                ly.push_back(kM[l.y]);
+                lx.push_back(kd[0][l.x]);
+                ly.push_back(kd[1][l.y]);
             }
         } else {
-            for (int pl = 0; pl < p->nl; ++pl) lx.push_back(kM[pl + 1]);
+            for (int pl = 0; pl < nI; ++pl) lx.push_back(kd[0][pl + 1]);
         }
         if (!lx.empty()) o_dlx = tb.add(lx);
         if (!ly.empty()) o_dly = tb.add(ly);
@@ -411,25 +464,25 @@ static se_status build_tables(se_plan_s *p)
         if ((st = upload(bytes.data(), p->sigma_tab, bytes.size(), "zero-mode table")) != SE_OK) return st;
     }
     // scaling boxes
-    const int row = M / 2 + 1;
+    const int row = Mv[0] / 2 + 1;
     auto boxes = [&](auto tag) {
         using T = decltype(tag);
         ScaleBox<T> spec{}, U{};
         if (D == 3) {
-            spec = make_box<T>(p, row, M, M, o_fper, o_kper, o_fper, o_kper, o_fper, o_kper,
-                               fpi / (double(M) * M * M), 0);
+            spec = make_box<T>(p, row, Mv[1], Mv[2], o_f[0], o_k[0], o_f[1], o_k[1], o_f[2], o_k[2],
+                               fpi / (double(Mv[0]) * Mv[1] * Mv[2]), 0);
         } else if (D == 2) {
-            spec = make_box<T>(p, row, M, Mt, o_fper, o_kper, o_fper, o_kper, o_fJ, o_kJ,
-                               fpi / (double(M) * M * Mt), 2);
-            if (p->nI > 0)
-                U = make_box<T>(p, p->sMt, p->nI, 1, o_fI, o_kI, o_fl, o_kl, o_one, o_zero,
-                                fpi / (double(M) * M * p->sMt), 0);
+            spec = make_box<T>(p, row, Mv[1], Mtv[2], o_f[0], o_k[0], o_f[1], o_k[1], o_f[2], o_k[2],
+                               fpi / (double(Mv[0]) * Mv[1] * Mtv[2]), 2);
+            if (nI > 0)
+                U = make_box<T>(p, p->sv[2], nI, 1, o_fI[2], o_kI[2], o_fl, o_kl, o_one, o_zero,
+                                fpi / (double(Mv[0]) * Mv[1] * p->sv[2]), 0);
         } else if (D == 1) {
-            spec = make_box<T>(p, row, Mt, Mt, o_fper, o_kper, o_fJ, o_kJ, o_fJ, o_kJ,
-                               fpi / (double(M) * Mt * Mt), 1);
-            if (p->nl > 0)
-                U = make_box<T>(p, p->sMt, p->sMt, p->nl, o_fI, o_kI, o_fI, o_kI, o_fl, o_kl,
-                                fpi / (double(M) * p->sMt * p->sMt), 0);
+            spec = make_box<T>(p, row, Mtv[1], Mtv[2], o_f[0], o_k[0], o_f[1], o_k[1], o_f[2], o_k[2],
+                               fpi / (double(Mv[0]) * Mtv[1] * Mtv[2]), 1);
+            if (nI > 0)
+                U = make_box<T>(p, p->sv[1], p->sv[2], nI, o_fI[1], o_kI[1], o_fI[2], o_kI[2], o_fl, o_kl,
+                                fpi / (double(Mv[0]) * p->sv[1] * p->sv[2]), 0);
         }
         return std::make_pair(spec, U);
     };
@@ -448,27 +501,26 @@ static se_status build_tables(se_plan_s *p)
         return b;
     };
     auto ikboxes = [&](auto tag, IkBox<decltype(tag)> &spec, IkBox<decltype(tag)> &U, IkBox<decltype(tag)> &Z) {
-        const int sM = p->sMt, s0 = p->s0Mt;
         if (D == 3) {
-            spec = ikbox(tag, row, M, M, p->spec_elems, o_dM, 0, o_dM, 1, o_dM, 2);
+            spec = ikbox(tag, row, Mv[1], Mv[2], p->spec_elems, o_d[0], 0, o_d[1], 1, o_d[2], 2);
         } else if (D == 0) {
-            spec = ikbox(tag, Mt + 1, 2 * Mt, 2 * Mt, p->spec_elems, o_d2Mt, 0, o_d2Mt, 1, o_d2Mt, 2);
+            spec = ikbox(tag, Mtv[0] + 1, 2 * Mtv[1], 2 * Mtv[2], p->spec_elems, o_d[0], 0, o_d[1], 1, o_d[2], 2);
         } else if (D == 2) {
-            spec = ikbox(tag, row, M, Mt, p->spec_elems, o_dM, 0, o_dM, 1, o_dMt, 2);
-            if (p->nI > 0) U = ikbox(tag, sM, p->nI, 1, p->U_elems, o_dlx, 1, o_dly, 1, o_dsMt, 0);
-            Z = ikbox(tag, s0, 1, 1, p->Z_elems, 0, -1, 0, -1, o_ds0Mt, 0);
+            spec = ikbox(tag, row, Mv[1], Mtv[2], p->spec_elems, o_d[0], 0, o_d[1], 1, o_d[2], 2);
+            if (nI > 0) U = ikbox(tag, p->sv[2], nI, 1, p->U_elems, o_dlx, 1, o_dly, 1, o_dI[2], 0);
+            Z = ikbox(tag, p->s0v[2], 1, 1, p->Z_elems, 0, -1, 0, -1, o_dZ[2], 0);
         } else {
-            spec = ikbox(tag, row, Mt, Mt, p->spec_elems, o_dM, 0, o_dMt, 1, o_dMt, 2);
-            if (p->nl > 0) U = ikbox(tag, sM, sM, p->nl, p->U_elems, o_dlx, 2, o_dsMt, 0, o_dsMt, 1);
-            Z = ikbox(tag, s0, s0, 1, p->Z_elems, 0, -1, o_ds0Mt, 0, o_ds0Mt, 1);
+            spec = ikbox(tag, row, Mtv[1], Mtv[2], p->spec_elems, o_d[0], 0, o_d[1], 1, o_d[2], 2);
+            if (nI > 0) U = ikbox(tag, p->sv[1], p->sv[2], nI, p->U_elems, o_dlx, 2, o_dI[1], 0, o_dI[2], 1);
+            Z = ikbox(tag, p->s0v[1], p->s0v[2], 1, p->Z_elems, 0, -1, o_dZ[1], 0, o_dZ[2], 1);
         }
     };
     if (p->dtype == SE_F32) ikboxes(float(), p->ib_spec_f, p->ib_U_f, p->ib_Z_f);
     else ikboxes(double(), p->ib_spec_d, p->ib_U_d, p->ib_Z_d);
     if (D == 0) {
-        // column stage: 2 M~ must be a power of two in [16, 1024] and the buffers
-        // of at least one column must fit in shared memory
-        const int n = 2 * Mt;
+        // column stage along z: 2 M~_2 must be a power of two in [16, 1024] and the
+        // buffers of at least one column must fit in shared memory
+        const int n = 2 * Mtv[2];
         const bool pow2 = n >= 16 && n <= 1024 && (n & (n - 1)) == 0;
         // columns per CTA: C n <= 2048 (8 scaling factors per thread) and the
         // method-2 buffers within 200 KB
@@ -493,11 +545,13 @@ static se_status build_tables(se_plan_s *p)
                 using T = decltype(tag);
                 const T *base = reinterpret_cast<const T *>(p->tabs);
                 zc.n = n;
-                zc.m = Mt;
-                zc.S = int64_t(n) * (Mt + 1);
-                zc.nx = Mt + 1;
+                zc.m = Mtv[2];
+                zc.S = int64_t(2 * Mtv[1]) * (Mtv[0] + 1);
+                zc.nx = Mtv[0] + 1;
                 zc.tw = reinterpret_cast<const T *>(p->ztw);
-                zc.kx = zc.ky = zc.kz = base + o_d2Mt;
+                zc.kx = base + o_d[0];
+                zc.ky = base + o_d[1];
+                zc.kz = base + o_d[2];
             };
             if (p->dtype == SE_F32) fill(float(), p->zc_f); else fill(double(), p->zc_d);
         }
@@ -512,50 +566,53 @@ static se_status make_plans(se_plan_s *p)
 {
     const bool f32 = p->dtype == SE_F32;
     const cufftType R2C = f32 ? CUFFT_R2C : CUFFT_D2Z, C2R = f32 ? CUFFT_C2R : CUFFT_Z2D, C2C = f32 ? CUFFT_C2C : CUFFT_Z2Z;
-    const int M = p->M, Mt = p->Mt, row = M / 2 + 1;
+    const int *Mv = p->Mv, *Mt = p->Mtv;
+    const int row = Mv[0] / 2 + 1;
     cufftResult r;
 #define SE_PLAN(call, flag, what)                                   \
     if ((r = (call)) != CUFFT_SUCCESS) return cufft_fail(r, what);  \
     flag = true;
     if (p->D == 3) {
-        SE_PLAN(cufftPlan3d(&p->fwd, M, M, M, R2C), p->have_fwd, "plan fwd");
-        SE_PLAN(cufftPlan3d(&p->inv, M, M, M, C2R), p->have_inv, "plan inv");
+        SE_PLAN(cufftPlan3d(&p->fwd, Mv[2], Mv[1], Mv[0], R2C), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlan3d(&p->inv, Mv[2], Mv[1], Mv[0], C2R), p->have_inv, "plan inv");
     } else if (p->D == 0) {
-        // (2 M~)^3 transform of a grid that is zero outside its M~^3 corner: 2D
-        // transforms of the M~ non-zero z-planes, then one strided z-transform
-        // over all (x', y) columns; the inverse mirrors it and keeps z < M~.
-        const int n2 = 2 * Mt;
-        int n[2] = {n2, n2};
-        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt), p->have_fwd, "plan fwd");
-        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt), p->have_inv, "plan inv");
-        int nz[1] = {n2};
-        const int col = n2 * (Mt + 1);
+        // 2M~_0 x 2M~_1 x 2M~_2 transform of a grid that is zero outside its
+        // M~_0 x M~_1 x M~_2 corner: 2D transforms of the M~_2 non-zero z-planes,
+        // then one strided z-transform over all (x', y) columns; the inverse
+        // mirrors it and keeps z < M~_2.
+        int n[2] = {2 * Mt[1], 2 * Mt[0]};
+        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt[2]), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt[2]), p->have_inv, "plan inv");
+        int nz[1] = {2 * Mt[2]};
+        const int col = 2 * Mt[1] * (Mt[0] + 1);
         SE_PLAN(cufftPlanMany(&p->free_main, 1, nz, nz, col, 1, nz, col, 1, C2C, col), p->have_free_main,
                 "plan z");
     } else if (p->D == 2) {
-        int n[2] = {M, M};
-        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt), p->have_fwd, "plan fwd");
-        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt), p->have_inv, "plan inv");
-        int nz[1] = {Mt};
-        SE_PLAN(cufftPlanMany(&p->free_main, 1, nz, nz, M * row, 1, nz, M * row, 1, C2C, M * row), p->have_free_main,
+        int n[2] = {Mv[1], Mv[0]};
+        SE_PLAN(cufftPlanMany(&p->fwd, 2, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt[2]), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 2, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt[2]), p->have_inv, "plan inv");
+        int nz[1] = {Mt[2]};
+        const int lines = Mv[1] * row;
+        SE_PLAN(cufftPlanMany(&p->free_main, 1, nz, nz, lines, 1, nz, lines, 1, C2C, lines), p->have_free_main,
                 "plan free");
         if (p->nI > 0) {
-            int ns[1] = {p->sMt};
+            int ns[1] = {p->sv[2]};
             SE_PLAN(cufftPlanMany(&p->free_I, 1, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nI), p->have_free_I, "plan I");
         }
-        int n0[1] = {p->s0Mt};
+        int n0[1] = {p->s0v[2]};
         SE_PLAN(cufftPlanMany(&p->free_Z, 1, n0, nullptr, 1, 0, nullptr, 1, 0, C2C, 1), p->have_free_Z, "plan zero");
     } else {
-        int n[1] = {M};
-        SE_PLAN(cufftPlanMany(&p->fwd, 1, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt * Mt), p->have_fwd, "plan fwd");
-        SE_PLAN(cufftPlanMany(&p->inv, 1, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt * Mt), p->have_inv, "plan inv");
-        int nz[2] = {Mt, Mt};
+        int n[1] = {Mv[0]};
+        SE_PLAN(cufftPlanMany(&p->fwd, 1, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt[1] * Mt[2]), p->have_fwd, "plan fwd");
+        SE_PLAN(cufftPlanMany(&p->inv, 1, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt[1] * Mt[2]), p->have_inv, "plan inv");
+        // (z, y) planes of each x' (element stride M_0/2 + 1)
+        int nz[2] = {Mt[2], Mt[1]};
         SE_PLAN(cufftPlanMany(&p->free_main, 2, nz, nz, row, 1, nz, row, 1, C2C, row), p->have_free_main, "plan free");
-        if (p->nl > 0) {
-            int ns[2] = {p->sMt, p->sMt};
-            SE_PLAN(cufftPlanMany(&p->free_I, 2, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nl), p->have_free_I, "plan I");
+        if (p->nI > 0) {
+            int ns[2] = {p->sv[2], p->sv[1]};
+            SE_PLAN(cufftPlanMany(&p->free_I, 2, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nI), p->have_free_I, "plan I");
         }
-        int n0[2] = {p->s0Mt, p->s0Mt};
+        int n0[2] = {p->s0v[2], p->s0v[1]};
         SE_PLAN(cufftPlanMany(&p->free_Z, 2, n0, nullptr, 1, 0, nullptr, 1, 0, C2C, 1), p->have_free_Z, "plan zero");
     }
 #undef SE_PLAN
@@ -621,9 +678,9 @@ se_status plan_build(se_plan_s *p)
     // grid geometry (Alg. 4 step 1)
     for (int a = 0; a < 3; ++a) {
         const bool per = a < p->D;
-        p->tg.n[a] = per ? p->M : p->Mt;
+        p->tg.n[a] = per ? p->Mv[a] : p->Mtv[a];
         p->tg.periodic[a] = per ? 1 : 0;
-        p->off[a] = per ? 0.0 : p->dL / 2.0;
+        p->off[a] = per ? 0.0 : (p->Ltv[a] - p->Lv[a]) / 2.0;
     }
     if (p->window == SE_WIN_PKB) fit_pkb(p);
     // tiles: pick the edge so that the extended blocks fit in shared memory
@@ -665,30 +722,27 @@ se_status plan_build(se_plan_s *p)
     p->scratch_bytes = size_t(nt) * p->tg.blk * p->elem;
     if ((st = dev_alloc(p, &p->scratch, p->scratch_bytes)) != SE_OK) return st;
     // grids and spectra
-    const int M = p->M, Mt = p->Mt, row = M / 2 + 1;
+    const int row = p->Mv[0] / 2 + 1;
     const int64_t nlog = int64_t(p->tg.n[0]) * p->tg.n[1] * p->tg.n[2];
     if (p->D == 0) {
-        const int64_t n2 = 2 * int64_t(Mt);
-        p->grid_in_elems = p->grid_out_elems = size_t(Mt * n2 * n2);     // the M~ non-zero z-planes
-        p->gin.s1 = p->gout.s1 = n2;
-        p->gin.s2 = p->gout.s2 = n2 * n2;
-        p->spec_elems = size_t(n2 * n2 * (Mt + 1));
+        const int64_t n0 = 2 * int64_t(p->Mtv[0]), n1 = 2 * int64_t(p->Mtv[1]), n2 = 2 * int64_t(p->Mtv[2]);
+        p->grid_in_elems = p->grid_out_elems = size_t(p->Mtv[2] * n1 * n0);     // the M~_2 non-zero z-planes
+        p->gin.s1 = p->gout.s1 = n0;
+        p->gin.s2 = p->gout.s2 = n0 * n1;
+        p->spec_elems = size_t(n2 * n1 * (p->Mtv[0] + 1));
         p->sigma_elems = p->spec_elems;
     } else {
         p->grid_in_elems = p->grid_out_elems = size_t(nlog);
         p->gin.s1 = p->gout.s1 = p->tg.n[0];
         p->gin.s2 = p->gout.s2 = int64_t(p->tg.n[0]) * p->tg.n[1];
         p->spec_elems = size_t(nlog / p->tg.n[0]) * row;
+        p->nI = count_I(p);
         if (p->D == 2) {
-            int nI = 0;
-            for (int ky = -p->nl; ky <= p->nl; ++ky)
-                for (int kx = 0; kx <= p->nl; ++kx) nI += !(kx == 0 && ky == 0);
-            p->nI = nI;
-            p->U_elems = size_t(nI) * p->sMt;
-            p->Z_elems = p->s0Mt;
+            p->U_elems = size_t(p->nI) * p->sv[2];
+            p->Z_elems = p->s0v[2];
         } else if (p->D == 1) {
-            p->U_elems = size_t(p->nl) * p->sMt * p->sMt;
-            p->Z_elems = size_t(p->s0Mt) * p->s0Mt;
+            p->U_elems = size_t(p->nI) * p->sv[1] * p->sv[2];
+            p->Z_elems = size_t(p->s0v[1]) * p->s0v[2];
         }
         p->sigma_elems = p->Z_elems;
     }

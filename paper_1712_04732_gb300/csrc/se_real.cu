@@ -18,7 +18,7 @@ template <> struct RV4<double> { using type = double4_32a; };
 struct CellGeom {
     int nc[3];          // cells per axis
     int periodic[3];
-    double L, inv_cell[3], cell[3];
+    double L[3], inv_cell[3], cell[3];
 };
 
 __device__ __forceinline__ float d_erfc(float v) { return erfcf(v); }
@@ -37,7 +37,7 @@ __device__ __forceinline__ int cell_of(const CellGeom &g, T *xp)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         T x = xp[a];
-        if (g.periodic[a]) x = x - T(g.L) * floor(x / T(g.L));
+        if (g.periodic[a]) x = x - T(g.L[a]) * floor(x / T(g.L[a]));
         xp[a] = x;
         int k = int(double(x) * g.inv_cell[a]);
         k = max(0, min(g.nc[a] - 1, k));
@@ -121,7 +121,7 @@ k_real_pairs(CellGeom g, int64_t N, T xi, T rc2, const int *__restrict__ off,
         T sh2 = T(0);
         if (k2 < 0 || k2 >= g.nc[2]) {
             if (!g.periodic[2]) continue;
-            sh2 = k2 < 0 ? T(-g.L) : T(g.L);
+            sh2 = k2 < 0 ? T(-g.L[2]) : T(g.L[2]);
             k2 = k2 < 0 ? k2 + g.nc[2] : k2 - g.nc[2];
         }
         for (int s1 = -1; s1 <= 1; ++s1) {
@@ -129,7 +129,7 @@ k_real_pairs(CellGeom g, int64_t N, T xi, T rc2, const int *__restrict__ off,
             T sh1 = T(0);
             if (k1 < 0 || k1 >= g.nc[1]) {
                 if (!g.periodic[1]) continue;
-                sh1 = k1 < 0 ? T(-g.L) : T(g.L);
+                sh1 = k1 < 0 ? T(-g.L[1]) : T(g.L[1]);
                 k1 = k1 < 0 ? k1 + g.nc[1] : k1 - g.nc[1];
             }
             for (int s0 = -1; s0 <= 1; ++s0) {
@@ -137,7 +137,7 @@ k_real_pairs(CellGeom g, int64_t N, T xi, T rc2, const int *__restrict__ off,
                 T sh0 = T(0);
                 if (k0 < 0 || k0 >= g.nc[0]) {
                     if (!g.periodic[0]) continue;
-                    sh0 = k0 < 0 ? T(-g.L) : T(g.L);
+                    sh0 = k0 < 0 ? T(-g.L[0]) : T(g.L[0]);
                     k0 = k0 < 0 ? k0 + g.nc[0] : k0 - g.nc[0];
                 }
                 const int cell = (k2 * g.nc[1] + k1) * g.nc[0] + k0;
@@ -217,19 +217,20 @@ extern "C" se_status se_real_space(se_plan_t p, int64_t N, const void *x, const 
     if (flags & SE_HOST_IO) return se::fail(SE_EINVAL, "SE_HOST_IO is not supported here");
     if (N == 0) return SE_OK;
     CellGeom g;
-    g.L = p->L;
     int ncell = 1;
     for (int a = 0; a < 3; ++a) {
+        const double L = p->Lv[a];
+        g.L[a] = L;
         g.periodic[a] = a < p->D ? 1 : 0;
-        int n = int(std::floor(p->L / rc));
+        int n = int(std::floor(L / rc));
         n = std::max(1, std::min(n, 256));
         // periodic axes: fewer than 3 cells would visit one cell under several
         // shifts; use one cell and let the shifts enumerate the images instead
-        if (g.periodic[a] && n < 3 && rc * 2 > p->L) return se::fail(SE_EINVAL, "rc must be < L/2 in periodic directions");
+        if (g.periodic[a] && n < 3 && rc * 2 > L) return se::fail(SE_EINVAL, "rc must be < L/2 in periodic directions");
         if (g.periodic[a] && n < 3) n = 1;
         g.nc[a] = n;
-        g.cell[a] = p->L / n;
-        g.inv_cell[a] = n / p->L;
+        g.cell[a] = L / n;
+        g.inv_cell[a] = n / L;
         ncell *= n;
     }
     // workspace (grown on demand; the call allocates when N or the cell count grows)

@@ -55,10 +55,16 @@ def test_plan_create_rejects_bad_arguments(lib, D, M, P, xi, box):
     assert lib.se_last_error()
 
 
-def test_plan_create_rejects_non_cubic_box(lib):
+@pytest.mark.parametrize("sides", [(1.0, 1.0, 1.03), (1.0, 1.0 + 1.0 / 32, 1.0), (1.0, 1.0, -1.0),
+                                   (1.0, 0.125, 1.0)])
+def test_plan_create_rejects_sides_off_the_grid(lib, sides):
+    """Non-cubic boxes share h = L_x / M: every side must be an even multiple of
+    h (33 h and 32.96 h are not), positive, and long enough for the support of
+    a periodic direction (4 h < P = 8)."""
     h = ctypes.c_void_p()
-    b = (ctypes.c_double * 3)(1.0, 1.0, 2.0)
+    b = (ctypes.c_double * 3)(*sides)
     assert lib.se_plan_create(ctypes.byref(h), b, 3, 8.0, 32, 8, 1, 0, None) == 1
+    assert not h.value
 
 
 def test_calls_reject_null_plan(lib):
