@@ -77,14 +77,16 @@ struct IkBox {
     int64_t stride;
 };
 
-// D = 0: the z-direction stage of the (2 M~)^3 transform done per column by
-// one kernel (forward FFT of the M~ non-zero values, scaling, inverse FFT, the
-// first M~ values kept).  Column c = y (M~ + 1) + x' of the 2D half spectra.
+// D = 0: the z-direction stage of the 2M~_0 x 2M~_1 x 2M~_2 transform done per
+// column by one kernel (forward FFT of the M~_2 non-zero values, scaling,
+// inverse FFT, the first M~_2 values kept).  Column c = y (M~_0 + 1) + x' of the
+// 2D half spectra; the scaling table holds ky, kz in [0, M~] only.
 template <typename T>
 struct ZCol {
     int n, m;            // transform length 2 M~ and the M~ values read / kept
     int64_t S;           // columns = complex elements per z-plane
-    int nx;              // M~ + 1 columns per y row
+    int nx;              // M~_0 + 1 columns per y row
+    int n1;              // 2 M~_1 rows (y) per plane
     const T *tw;         // e^{-2 pi i t / n}, t = 0..n-1, as (re, im) pairs
     const T *kx, *ky, *kz;   // method 2: signed k per x', y and z index (Nyquist zero)
 };

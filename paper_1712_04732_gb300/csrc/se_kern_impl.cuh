@@ -118,6 +118,21 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
     return e;
 }
 
+// Ask for the largest shared-memory carveout for a kernel whose residency is
+// limited by shared memory (set once per kernel).
+template <typename K>
+static cudaError_t prefer_shared(K kernel)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, bool> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(reinterpret_cast<const void *>(kernel))) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         int(cudaSharedmemCarveoutMaxShared));
+    if (e == cudaSuccess) done[reinterpret_cast<const void *>(kernel)] = true;
+    return e;
+}
+
 template <typename T>
 se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
 {
@@ -293,10 +308,12 @@ static se_status convolve_zcol(se_plan_s *p, void *gin, void *gout, bool ik)
         if (ik) {                                                                                \
             auto kern = k_zcol<T, NV, true>;                                                     \
             if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
+            if ((e = prefer_shared(kern)) != cudaSuccess) return cuda_fail(e, "column stage carveout"); \
             kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
         } else {                                                                                 \
             auto kern = k_zcol<T, NV, false>;                                                    \
             if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
+            if ((e = prefer_shared(kern)) != cudaSuccess) return cuda_fail(e, "column stage carveout"); \
             kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
         }                                                                                        \
         break;

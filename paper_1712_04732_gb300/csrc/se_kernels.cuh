@@ -786,7 +786,7 @@ __device__ __forceinline__ bool stockham_from(const typename Cplx<T>::type *tw, 
 // x and y i k_a is constant on the column and multiplies the result; along z
 // the product i k_z sigma H^ is transformed as a second column set.
 template <typename T, int N, bool IK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *__restrict__ sigma,
        typename Cplx<T>::type *__restrict__ dd, int64_t dstride)
 {
@@ -802,13 +802,21 @@ k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *_
     C2 *B = A + size_t(ncol) * LD;
     const int64_t c0 = int64_t(blockIdx.x) << lc;
     const int cc = int(min(int64_t(C), S - c0));
-    // scaling factors of this thread's (column, kz) items, fetched early
+    // scaling factors of this thread's (column, kz) items, fetched early from the
+    // table of ky, kz >= 0 (sigma is even in each wavenumber)
     T sg[kItems];
+    {
+        const int64_t c = c0 + (threadIdx.x & (C - 1));
+        const int y = int(c / zc.nx), xq = int(c - int64_t(y) * zc.nx);
+        const int ay = min(y, zc.n1 - y);
+        const int64_t rowoff = int64_t(ay) * zc.nx + xq, plane = int64_t(zc.n1 / 2 + 1) * zc.nx;
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        const int i = threadIdx.x + it * blockDim.x;
-        const int col = i & (C - 1), k = i >> lc;
-        sg[it] = (i < (N << lc) && col < cc) ? sigma[k * S + c0 + col] : T(0);
+        for (int it = 0; it < kItems; ++it) {
+            const int i = threadIdx.x + it * blockDim.x;
+            const int col = i & (C - 1), k = i >> lc;
+            const int ak = min(k, N - k);
+            sg[it] = (i < (N << lc) && col < cc) ? sigma[ak * plane + rowoff] : T(0);
+        }
     }
     const C2 *gtw = reinterpret_cast<const C2 *>(zc.tw);
     for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = gtw[t];

@@ -207,17 +207,22 @@ __global__ void k_green0_truncate(Dim3 ns, Dim3 Mt, double scale, const cufftDou
     out[i] = in[(int64_t(ic) * ns.n[1] + ib) * ns.n[0] + ia].x * scale;
 }
 
-// sigma on the R2C box (M~_0 + 1) x 2M~_1 x 2M~_2 from the per-axis factors
+// sigma on the R2C box (M~_0 + 1) x 2M~_1 x 2M~_2 from the per-axis factors; with
+// half set, only ky, kz in [0, M~] ((M~_0 + 1) x (M~_1 + 1) x (M~_2 + 1) values):
+// sigma is even in each wavenumber (the factors are, and G^{0P}_R enters as the
+// real part of the transform of a real sequence).
 template <typename T>
 __global__ void k_sigma0(Dim3 Mt, double norm, const double *f0, const double *f1, const double *f2,
-                         const cufftDoubleComplex *gr, T *out)
+                         const cufftDoubleComplex *gr, T *out, bool half)
 {
     const int nx = Mt.n[0] + 1, n1 = 2 * Mt.n[1], n2 = 2 * Mt.n[2];
-    const int64_t n = int64_t(nx) * n1 * n2;
+    const int m1 = half ? Mt.n[1] + 1 : n1, m2 = half ? Mt.n[2] + 1 : n2;
+    const int64_t n = int64_t(nx) * m1 * m2;
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    const int a = int(i % nx), b = int((i / nx) % n1), c = int(i / (int64_t(nx) * n1));
-    out[i] = T(norm * f0[a] * f1[b] * f2[c] * gr[i].x);
+    const int a = int(i % nx), b = int((i / nx) % m1), c = int(i / (int64_t(nx) * m1));
+    const int64_t g = (int64_t(c) * n1 + b) * nx + a;
+    out[i] = T(norm * f0[a] * f1[b] * f2[c] * gr[g].x);
 }
 
 static se_status precompute_free_space(se_plan_s *p)
@@ -230,6 +235,7 @@ static se_status precompute_free_space(se_plan_s *p)
     const int64_t nsamp = int64_t(ns.n[0]) * ns.n[1] * ns.n[2];
     const int64_t ngr = int64_t(8) * Mt.n[0] * Mt.n[1] * Mt.n[2];
     const int64_t nhat = int64_t(Mt.n[0] + 1) * (2 * Mt.n[1]) * (2 * Mt.n[2]);
+    const int64_t nsig = int64_t(p->sigma_elems);
     void *samp = nullptr, *gr = nullptr, *grh = nullptr, *fax = nullptr;
     se_status st = SE_OK;
     cufftHandle h1 = 0, h2 = 0;
@@ -281,13 +287,13 @@ static se_status precompute_free_space(se_plan_s *p)
     }
     // sigma = 4 pi h^3 / (8 M~_0 M~_1 M~_2) * prod_i e^{-k_i^2/4xi^2} / W^0(k_i)^2 * G^{0P}_R
     if (p->dtype == SE_F32)
-        k_sigma0<float><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
+        k_sigma0<float><<<unsigned((nsig + 255) / 256), 256, 0, p->stream>>>(
             Mt, norm, fd, fd + 2 * Mt.n[0], fd + 2 * Mt.n[0] + 2 * Mt.n[1], (const cufftDoubleComplex *)grh,
-            (float *)p->sigma_tab);
+            (float *)p->sigma_tab, p->zcol);
     else
-        k_sigma0<double><<<unsigned((nhat + 255) / 256), 256, 0, p->stream>>>(
+        k_sigma0<double><<<unsigned((nsig + 255) / 256), 256, 0, p->stream>>>(
             Mt, norm, fd, fd + 2 * Mt.n[0], fd + 2 * Mt.n[0] + 2 * Mt.n[1], (const cufftDoubleComplex *)grh,
-            (double *)p->sigma_tab);
+            (double *)p->sigma_tab, p->zcol);
     {
         cudaError_t e = cudaStreamSynchronize(p->stream);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -345,6 +351,25 @@ static se_status upload(const void *host, void *dev, size_t bytes, const char *w
 {
     cudaError_t e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? SE_OK : cuda_fail(e, what);
+}
+
+// D = 0 column stage along z: 2 M~_2 a power of two in [16, 1024], and the
+// buffers of C columns (C n <= 2048: 8 scaling factors per thread; the method-2
+// buffers within 200 KB) in shared memory.
+static void choose_zcol(se_plan_s *p)
+{
+    p->zcol = false;
+    if (p->D != 0 || !p->zcol_allowed) return;
+    const int n = 2 * p->Mtv[2];
+    if (n < 16 || n > 1024 || (n & (n - 1)) != 0) return;
+    int C = 32;
+    const size_t per = 2 * (p->dtype == SE_F32 ? 4 : 8);
+    const int ld = n + n / 16 + 1;
+    auto smem = [&](int c) { return (size_t(n) + 2 * size_t(2 * c) * ld) * per; };
+    while (C > 1 && (C * n > 2048 || smem(C) > 200 * 1024)) C /= 2;
+    if (smem(C) > 200 * 1024) return;
+    p->zcol = true;
+    p->zcol_cols = C;
 }
 
 // Number of lines of the set I for D = 2 (half spectrum in x): |kx| <= nI_0 (kx >= 0),
@@ -517,44 +542,31 @@ static se_status build_tables(se_plan_s *p)
     };
     if (p->dtype == SE_F32) ikboxes(float(), p->ib_spec_f, p->ib_U_f, p->ib_Z_f);
     else ikboxes(double(), p->ib_spec_d, p->ib_U_d, p->ib_Z_d);
-    if (D == 0) {
-        // column stage along z: 2 M~_2 must be a power of two in [16, 1024] and the
-        // buffers of at least one column must fit in shared memory
+    if (p->zcol) {
         const int n = 2 * Mtv[2];
-        const bool pow2 = n >= 16 && n <= 1024 && (n & (n - 1)) == 0;
-        // columns per CTA: C n <= 2048 (8 scaling factors per thread) and the
-        // method-2 buffers within 200 KB
-        int C = 32;
-        const size_t per = 2 * (p->dtype == SE_F32 ? 4 : 8);
-        const int ld = n + n / 16 + 1;
-        auto smem = [&](int c) { return (size_t(n) + 2 * size_t(2 * c) * ld) * per; };
-        while (C > 1 && (C * n > 2048 || smem(C) > 200 * 1024)) C /= 2;
-        p->zcol = pow2 && smem(C) <= 200 * 1024 && p->zcol_allowed;
-        if (p->zcol) {
-            p->zcol_cols = C;
-            std::vector<double> tw(2 * size_t(n));
-            for (int t = 0; t < n; ++t) {
-                tw[2 * t] = std::cos(2.0 * M_PI * t / n);
-                tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / n);
-            }
-            std::vector<unsigned char> tb2;
-            if (p->dtype == SE_F32) to_type<float>(tw, tb2); else to_type<double>(tw, tb2);
-            if ((st = dev_alloc(p, &p->ztw, tb2.size())) != SE_OK) return st;
-            if ((st = upload(tb2.data(), p->ztw, tb2.size(), "twiddles")) != SE_OK) return st;
-            auto fill = [&](auto tag, auto &zc) {
-                using T = decltype(tag);
-                const T *base = reinterpret_cast<const T *>(p->tabs);
-                zc.n = n;
-                zc.m = Mtv[2];
-                zc.S = int64_t(2 * Mtv[1]) * (Mtv[0] + 1);
-                zc.nx = Mtv[0] + 1;
-                zc.tw = reinterpret_cast<const T *>(p->ztw);
-                zc.kx = base + o_d[0];
-                zc.ky = base + o_d[1];
-                zc.kz = base + o_d[2];
-            };
-            if (p->dtype == SE_F32) fill(float(), p->zc_f); else fill(double(), p->zc_d);
+        std::vector<double> tw(2 * size_t(n));
+        for (int t = 0; t < n; ++t) {
+            tw[2 * t] = std::cos(2.0 * M_PI * t / n);
+            tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / n);
         }
+        std::vector<unsigned char> tb2;
+        if (p->dtype == SE_F32) to_type<float>(tw, tb2); else to_type<double>(tw, tb2);
+        if ((st = dev_alloc(p, &p->ztw, tb2.size())) != SE_OK) return st;
+        if ((st = upload(tb2.data(), p->ztw, tb2.size(), "twiddles")) != SE_OK) return st;
+        auto fill = [&](auto tag, auto &zc) {
+            using T = decltype(tag);
+            const T *base = reinterpret_cast<const T *>(p->tabs);
+            zc.n = n;
+            zc.m = Mtv[2];
+            zc.S = int64_t(2 * Mtv[1]) * (Mtv[0] + 1);
+            zc.nx = Mtv[0] + 1;
+            zc.n1 = 2 * Mtv[1];
+            zc.tw = reinterpret_cast<const T *>(p->ztw);
+            zc.kx = base + o_d[0];
+            zc.ky = base + o_d[1];
+            zc.kz = base + o_d[2];
+        };
+        if (p->dtype == SE_F32) fill(float(), p->zc_f); else fill(double(), p->zc_d);
     }
     if (D == 0) return precompute_free_space(p);
     return SE_OK;
@@ -730,7 +742,9 @@ se_status plan_build(se_plan_s *p)
         p->gin.s1 = p->gout.s1 = n0;
         p->gin.s2 = p->gout.s2 = n0 * n1;
         p->spec_elems = size_t(n2 * n1 * (p->Mtv[0] + 1));
-        p->sigma_elems = p->spec_elems;
+        choose_zcol(p);
+        // the column stage reads the scaling table at ky, kz >= 0 only (sigma is even in each)
+        p->sigma_elems = p->zcol ? size_t(p->Mtv[2] + 1) * (p->Mtv[1] + 1) * (p->Mtv[0] + 1) : p->spec_elems;
     } else {
         p->grid_in_elems = p->grid_out_elems = size_t(nlog);
         p->gin.s1 = p->gout.s1 = p->tg.n[0];
