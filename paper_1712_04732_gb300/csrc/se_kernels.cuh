@@ -962,13 +962,16 @@ __global__ void k_unpad_1p(int nl, int Mt1, int Mt2, int s1, int s2, int z1, int
 // ----------------------------------------------------------------- gathering
 // Energy E = sum of the per-CTA partial sums part[0..n), added in index order by
 // the CTA that finishes last (the others have published their partials).
+// Thread 0 of every CTA has written part[blockIdx.x]; it alone fences before
+// taking its ticket.
 __device__ __forceinline__ void finish_energy(double *part, int n, double *energy, int *done)
 {
     __shared__ bool last;
     __shared__ double red[256];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+    }
     __syncthreads();
     if (!last) return;
     __threadfence();
