@@ -210,6 +210,58 @@ def run_batch(se, wl, dev, flush, steps):
     return res
 
 
+def run_other_workloads(se, wl, dev, flush, steps):
+    """The FP32 step on the larger workloads (slab 1e5 and wire 1.2e6 particles):
+    particles/s from graph replays after an L2 flush, and the gridding and
+    gathering stages' algorithmic FLOP rate against the derived FP32 peak."""
+    import torch
+    out = {}
+    for name in ("slab_2p", "wire_1p"):
+        x_np, q_np, spec = wl.make(name, seed=1)
+        n = len(q_np)
+        plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"],
+                       dtype=torch.float32, device=dev, lam=spec.get("lam"))
+        plan.reserve(n)
+        x = torch.tensor(x_np, dtype=torch.float32, device=dev)
+        q = torch.tensor(q_np, dtype=torch.float32, device=dev)
+        res = (torch.empty((n, 3), device=dev), torch.empty(n, device=dev),
+               torch.empty((), dtype=torch.float64, device=dev))
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                plan.force(x, q, energy=True, out=res)
+        torch.cuda.current_stream(dev).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            plan.force(x, q, energy=True, out=res)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record()
+            g.replay()
+            e1.record()
+        torch.cuda.synchronize(dev)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        plan.set_profiling(True)
+        for _ in range(5):
+            flush.zero_()
+            plan.force(x, q, energy=True, out=res)
+        torch.cuda.synchronize(dev)
+        pr = plan.profile()
+        plan.set_profiling(False)
+        st = {k: v / pr["calls"] for k, v in pr["ms"].items()}
+        cnt = algorithmic_counts(spec["P"], plan.info()["nu"], spec["window"])
+        frac = {}
+        for k in ("spread", "gather"):
+            tf = 2.0 * cnt[k] * n / (st[k] * 1e-3) / 1e12
+            frac[k] = {"tflops": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS}
+        out[name] = {"particles": n, "ms_per_step": ms, "value": n / (ms * 1e-3), "unit": "particles/s",
+                     "stage_ms": st, "alu": frac}
+        plan.close()
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -368,6 +420,7 @@ def run_ours(a):
     # ---- batched independent systems: one CUDA graph vs one se_force per system ---
     if not a.no_batch:
         line["batch_form"] = run_batch(se, wl, dev, flush, min(a.steps, 50))
+        line["other_workloads"] = run_other_workloads(se, wl, dev, flush, min(a.steps, 20))
 
     # ---- CPU baseline and accuracy (rank 0, one GPU only) -------------------------
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
