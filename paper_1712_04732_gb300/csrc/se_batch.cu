@@ -12,7 +12,7 @@
 
 namespace {
 
-constexpr int kBranches = 8;   // concurrent graph branches (streams during capture)
+constexpr int kBranches = 16;  // concurrent graph branches (streams during capture)
 
 // Smallest even M' >= M whose prime factors are 2, 3, 5 (sizes cuFFT handles best).
 int fft_friendly(int M)
@@ -37,6 +37,7 @@ struct se_batch_s {
     std::vector<int64_t> N, off;
     std::vector<se_plan_t> plans;
     std::vector<Variant> chosen;
+    std::vector<float> cost;                // tuned time of each system's call (ms)
     cudaStream_t stream = nullptr;          // caller's stream: graph launches and tuning runs
     cudaStream_t cap = nullptr;             // internal stream the graph is captured from
     cudaStream_t branch[kBranches] = {};
@@ -99,7 +100,7 @@ se_status autotune(se_batch_s *b, const void *x, const void *q, void *F, void *p
                    const std::vector<double> &L, const std::vector<int> &D, const std::vector<double> &xi,
                    const std::vector<int> &M, const std::vector<int> &P, se_window w)
 {
-    const Variant cand[] = {{8, 1, 1, 2}, {8, 2, 4, 2}, {4, 1, 1, 2}, {16, 1, 1, 2}, {8, 1, 1, 1}};
+    const Variant cand[] = {{8, 1, 1, 2}, {8, 2, 2, 2}, {8, 2, 4, 2}, {4, 1, 1, 2}, {16, 1, 1, 2}, {8, 1, 1, 1}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -132,6 +133,7 @@ se_status autotune(se_batch_s *b, const void *x, const void *q, void *F, void *p
             std::sort(t, t + 3);
             if (t[1] < best) {
                 best = t[1];
+                b->cost[i] = best;
                 se_plan_destroy(b->plans[i]);
                 b->plans[i] = p;
                 b->chosen[i] = v;
@@ -156,13 +158,17 @@ se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *ph
     se_status st = SE_OK;
     cudaEventRecord(b->fork, b->cap);
     for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(b->branch[k], b->fork, 0);
-    // systems dealt round-robin, largest first, onto the branches
+    // longest first onto the least-loaded branch (costs from the tuner, else N)
     std::vector<int> order(b->nsys);
     for (int i = 0; i < b->nsys; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int u, int v) { return b->N[u] > b->N[v]; });
+    auto cost = [&](int i) { return b->cost[i] > 0 ? double(b->cost[i]) : double(b->N[i]); };
+    std::sort(order.begin(), order.end(), [&](int u, int v) { return cost(u) > cost(v); });
+    double load[kBranches] = {};
     for (int r = 0; r < b->nsys && st == SE_OK; ++r) {
         const int i = order[r];
-        st = run_system(b, i, x, q, F, phi, energy, b->branch[r % kBranches]);
+        const int k = int(std::min_element(load, load + kBranches) - load);
+        load[k] += cost(i);
+        st = run_system(b, i, x, q, F, phi, energy, b->branch[k]);
     }
     for (int k = 0; k < kBranches; ++k) {
         cudaEventRecord(b->join[k], b->branch[k]);
@@ -210,6 +216,7 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
     }
     b->plans.assign(nsys, nullptr);
     b->chosen.assign(nsys, Variant{8, 0, 0, 0});
+    b->cost.assign(nsys, 0.0f);
     b->window = w;
     b->L.assign(L, L + nsys);
     b->xi.assign(xi, xi + nsys);
