@@ -42,6 +42,34 @@ namespace se {
     }
 
 static inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+// Launch with programmatic stream serialisation: the kernel may begin while the
+// previous kernel on the stream drains, and waits in pdl_wait() for its results
+// (cluster > 1 adds the cluster dimension).
+template <typename K, typename... Args>
+static cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t sm, cudaStream_t s, unsigned cluster,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    int na = 1;
+    if (cluster > 1) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        na = 2;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 static inline size_t al16(size_t n) { return (n + 15) & ~size_t(15); }
 
 template <typename T>
@@ -145,9 +173,13 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
                                                                p->tile_off, p->counters, !local_scan);
     SE_LAUNCH_CHECK("bin_count");
-    k_bin_scatter<T><<<blocks_for(N, 256), 256, local_scan ? sizeof(int) * (nt + 1) : 0, p->stream>>>(
-        a, N, x, q, p->tile_off, p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
-        p->prt.idx_anc, local_scan ? p->tile_cnt : nullptr, nt);
+    {
+        cudaError_t e = launch_pdl(k_bin_scatter<T>, dim3(blocks_for(N, 256)), dim3(256),
+                                   local_scan ? sizeof(int) * (nt + 1) : 0, p->stream, 1, a, N, x, q, p->tile_off,
+                                   (const int2 *)p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
+                                   p->prt.idx_anc, (const int *)(local_scan ? p->tile_cnt : nullptr), nt);
+        if (e != cudaSuccess) return cuda_fail(e, "bin_scatter launch");
+    }
     SE_LAUNCH_CHECK("bin_scatter");
     prof_mark(p, 1);
     return SE_OK;
@@ -197,26 +229,15 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
         });
     } else {
         const int CL = mode == 1 ? 1 : split_for(p, N);
-        const size_t sm = (al32(p->tg.sblk) + al32((kMaxNu + 1) * p->P) + size_t(kThreads / 32) * 3 * p->P) *
-                          sizeof(T);
-        SE_DISPATCH_P_ONLY(p->P, {
-            auto kern = k_spread_cl<T, PP>;
+        const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
+        const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+        SE_DISPATCH_P(p->P, nu, {
+            auto kern = k_spread_cl<T, PP, NN>;
             cudaError_t e = allow_smem(kern, sm);
             if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(unsigned(nt * CL));
-            cfg.blockDim = dim3(kThreads);
-            cfg.dynamicSmemBytes = sm;
-            cfg.stream = p->stream;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = unsigned(CL);
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            e = cudaLaunchKernelEx(&cfg, kern, p->tg, (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g,
-                                   wa, reinterpret_cast<T *>(scratch));
+            e = launch_pdl(kern, dim3(unsigned(nt * CL)), dim3(kThreads), sm, p->stream, unsigned(CL), p->tg,
+                           (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
+                           reinterpret_cast<T *>(scratch));
             if (e != cudaSuccess) return cuda_fail(e, "spread launch");
         });
     }
@@ -226,12 +247,14 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
     dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
     bool two = true;                                  // at most two tiles overlap a point per axis
     for (int a = 0; a < 3; ++a) two = two && (p->tg.B[a] - 1) / p->tg.T[a] + 1 <= 2;
-    if (two)
-        k_merge<T, 2><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
-                                                reinterpret_cast<T *>(dst), p->gin);
-    else
-        k_merge<T, kMergeJ><<<nt, mb, 0, p->stream>>>(p->tg, p->tile_off, reinterpret_cast<const T *>(scratch),
-                                                      reinterpret_cast<T *>(dst), p->gin);
+    {
+        cudaError_t e = two ? launch_pdl(k_merge<T, 2>, dim3(nt), mb, 0, p->stream, 1, p->tg, (const int *)p->tile_off,
+                                         reinterpret_cast<const T *>(scratch), reinterpret_cast<T *>(dst), p->gin)
+                            : launch_pdl(k_merge<T, kMergeJ>, dim3(nt), mb, 0, p->stream, 1, p->tg,
+                                         (const int *)p->tile_off, reinterpret_cast<const T *>(scratch),
+                                         reinterpret_cast<T *>(dst), p->gin);
+        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+    }
     SE_LAUNCH_CHECK("merge");
     prof_mark(p, 3);
     return SE_OK;
@@ -309,12 +332,14 @@ static se_status convolve_zcol(se_plan_s *p, void *gin, void *gout, bool ik)
             auto kern = k_zcol<T, NV, true>;                                                     \
             if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
             if ((e = prefer_shared(kern)) != cudaSuccess) return cuda_fail(e, "column stage carveout"); \
-            kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
+            if ((e = launch_pdl(kern, dim3(nb), dim3(256), sm, p->stream, 1, zc, lc, pad, sig, dd, ds)) != cudaSuccess) \
+                return cuda_fail(e, "column stage launch");                                      \
         } else {                                                                                 \
             auto kern = k_zcol<T, NV, false>;                                                    \
             if ((e = allow_smem(kern, sm)) != cudaSuccess) return cuda_fail(e, "column stage smem"); \
             if ((e = prefer_shared(kern)) != cudaSuccess) return cuda_fail(e, "column stage carveout"); \
-            kern<<<nb, 256, sm, p->stream>>>(zc, lc, pad, sig, dd, ds);                          \
+            if ((e = launch_pdl(kern, dim3(nb), dim3(256), sm, p->stream, 1, zc, lc, pad, sig, dd, ds)) != cudaSuccess) \
+                return cuda_fail(e, "column stage launch");                                      \
         }                                                                                        \
         break;
     switch (zc.n) {
@@ -510,10 +535,11 @@ se_status Ops<T>::gather_m2(se_plan_s *p, int64_t N, T *phi, T *F, double *energ
         constexpr int G = LaneMap<PP>::G;
         const int64_t per_cta = int64_t(kThreads / 32) * G;
         const unsigned nb = unsigned((N + per_cta - 1) / per_cta);
-        k_gather_flat_m2<T, PP, NN><<<nb, kThreads, 0, p->stream>>>(
-            N, p->tg, fq, p->prt.idx_anc, wa, reinterpret_cast<const T *>(p->grid_out),
-            reinterpret_cast<const T *>(p->grid_d), int64_t(p->grid_out_elems), p->gout, phi, F, part, energy,
-            p->counters + 1, self);
+        cudaError_t e = launch_pdl(k_gather_flat_m2<T, PP, NN>, dim3(nb), dim3(kThreads), 0, p->stream, 1, N, p->tg, fq,
+                                   (const int4 *)p->prt.idx_anc, wa, reinterpret_cast<const T *>(p->grid_out),
+                                   reinterpret_cast<const T *>(p->grid_d), int64_t(p->grid_out_elems), p->gout, phi,
+                                   F, part, energy, p->counters + 1, self);
+        if (e != cudaSuccess) return cuda_fail(e, "gather m2 launch");
     });
     SE_LAUNCH_CHECK("gather m2");
     prof_mark(p, 7);
@@ -543,14 +569,16 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
             const int64_t per_cta = int64_t(kThreads / 32) * G;
             const unsigned nb = unsigned((N + per_cta - 1) / per_cta);
             nparts = int(nb);
+            cudaError_t e;
             if (grad)
-                k_gather_flat<T, PP, NN, true><<<nb, kThreads, 0, p->stream>>>(
-                    N, p->tg, fq, p->prt.idx_anc, wa, grid, p->gout, phi, F, part, energy, p->counters + 1,
-                    T(p->inv_h), self);
+                e = launch_pdl(k_gather_flat<T, PP, NN, true>, dim3(nb), dim3(kThreads), 0, p->stream, 1, N, p->tg,
+                               fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, F, part, energy,
+                               p->counters + 1, T(p->inv_h), self);
             else
-                k_gather_flat<T, PP, NN, false><<<nb, kThreads, 0, p->stream>>>(
-                    N, p->tg, fq, p->prt.idx_anc, wa, grid, p->gout, phi, nullptr, part, energy, p->counters + 1,
-                    T(p->inv_h), self);
+                e = launch_pdl(k_gather_flat<T, PP, NN, false>, dim3(nb), dim3(kThreads), 0, p->stream, 1, N, p->tg,
+                               fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, (T *)nullptr, part, energy,
+                               p->counters + 1, T(p->inv_h), self);
+            if (e != cudaSuccess) return cuda_fail(e, "gather launch");
         });
     } else {
         const size_t sm = gather_smem<T>(p, 1);

@@ -21,6 +21,12 @@ __device__ __forceinline__ double dfloor(double v) { return floor(v); }
 __device__ __forceinline__ float dexp(float v) { return expf(v); }
 __device__ __forceinline__ double dexp(double v) { return exp(v); }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while the previous kernel of the
+// stream drains; it waits here before it reads anything that kernel wrote
+// (a no-op for an ordinary launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Bits latched in the plan's error word.
 constexpr int kErrOutOfBox = 1;
 constexpr int kErrNotFinite = 2;
@@ -179,6 +185,8 @@ k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restr
               int *__restrict__ off, const int2 *__restrict__ tile_rank,
               typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia, const int *__restrict__ cnt, int ntiles)
 {
+    pdl_wait();
+
     extern __shared__ int soff[];
     const int *o = off;
     if (cnt) {
@@ -408,11 +416,12 @@ k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
 // distributed shared memory, each CTA writing a slice of the compact block to
 // `scratch`.  When g != nullptr the charges are taken from g (original
 // particle order).
-template <typename T, int P>
+template <typename T, int P, int NU>
 __global__ void __launch_bounds__(kThreads)
 k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
             const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
 {
+    pdl_wait();
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int NE = (P * P + 31) / 32;
@@ -422,14 +431,18 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     if (beg == end) return;                               // the same for every CTA of the cluster
     extern __shared__ __align__(16) unsigned char smraw[];
     T *blk = reinterpret_cast<T *>(smraw);
-    T *sc = blk + align_up_elems<T>(tg.sblk);             // PKB coefficients
-    const int ncoef = (wa.nu + 1) * P;
-    T *wb = sc + align_up_elems<T>(ncoef);                // [warp][3P]
+    T *wb = blk + align_up_elems<T>(tg.sblk);             // [warp][3P]
     zero_smem(blk, tg.sblk);
-    if (wa.kind == SE_WIN_PKB)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) sc[i] = wa.c[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     T *w = wb + warp * 3 * P;
+    // lane j < 3P evaluates the window along axis j / P at stencil point j mod P
+    // (and lane j + 32 when 3P > 32), with that point's PKB coefficients in registers
+    const int j0 = lane, j1 = lane + 32;
+    LaneCoef<T, NU> cf0, cf1;
+    if (wa.kind == SE_WIN_PKB) {
+        if (j0 < 3 * P) cf0.load(wa, P, j0 % P);
+        if (3 * P > 32 && j1 < 3 * P) cf1.load(wa, P, j1 % P);
+    }
     int o[3];
     tile_origin(tg, tile, o);
     const int pitch = tg.pitch, plane = tg.B[1] * tg.pitch;
@@ -468,9 +481,17 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
             const T rx = __shfl_sync(0xffffffffu, lx, i), ry = __shfl_sync(0xffffffffu, ly, i);
             const T rz = __shfl_sync(0xffffffffu, lz, i), qv = __shfl_sync(0xffffffffu, lq, i);
             const int bo = __shfl_sync(0xffffffffu, lb, i);
-            for (int j = lane; j < 3 * P; j += 32) {
-                const int ax = j / P, k = j - ax * P;
-                w[j] = win_val_smem<T, P>(wa.kind, wa.nu, wa.alpha, sc, ax == 0 ? rx : (ax == 1 ? ry : rz), k);
+            if (j0 < 3 * P) {
+                const int ax = j0 / P;
+                T v, dv;
+                win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf0, ax == 0 ? rx : (ax == 1 ? ry : rz), j0 - ax * P, v, dv);
+                w[j0] = v;
+            }
+            if (3 * P > 32 && j1 < 3 * P) {
+                const int ax = j1 / P;
+                T v, dv;
+                win_eval<T, P, NU, false>(wa.kind, wa.alpha, cf1, ax == 0 ? rx : (ax == 1 ? ry : rz), j1 - ax * P, v, dv);
+                w[j1] = v;
             }
             __syncwarp();
             T wxy[NE];
@@ -522,6 +543,8 @@ template <typename T, int J>
 __global__ void k_merge(TileGeom tg, const int *__restrict__ off, const T *__restrict__ scratch,
                         T *__restrict__ dst, GridView v)
 {
+    pdl_wait();
+
     __shared__ int src_tile[J][J][J];
     const int tile = blockIdx.x;
     int c[3];
@@ -790,6 +813,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_zcol(ZCol<T> zc, int lc, typename Cplx<T>::type *__restrict__ data, const T *__restrict__ sigma,
        typename Cplx<T>::type *__restrict__ dd, int64_t dstride)
 {
+    pdl_wait();
+
     using C2 = typename Cplx<T>::type;
     constexpr int LD = zcol_ld(N);
     constexpr int kItems = 8;                       // (C N) / 256 <= 8 per thread
@@ -1196,6 +1221,8 @@ k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__
               WindowArgs<T> wa, const T *__restrict__ grid, GridView v, T *__restrict__ phi, T *__restrict__ F,
               double *__restrict__ part, double *energy, int *done, T inv_h, T self_coef)
 {
+    pdl_wait();
+
     constexpr int G = LaneMap<P>::G;
     __shared__ T wbs[kThreads / 32][32 * 6];
     __shared__ double epart[kThreads / 32];
@@ -1275,6 +1302,8 @@ k_gather_flat_m2(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restric
                  GridView v, T *__restrict__ phi, T *__restrict__ F, double *__restrict__ part, double *energy,
                  int *done, T self_coef)
 {
+    pdl_wait();
+
     constexpr int G = LaneMap<P>::G;
     __shared__ T wbs[kThreads / 32][32 * 3];
     __shared__ double epart[kThreads / 32];
