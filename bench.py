@@ -40,7 +40,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the tile kernels on this workload,
 # from one ncu --set full capture (profiles/free_0p_tile_kernels.md); reset to None whenever the
 # kernel changes
-NCU_TRAFFIC = {"spread": 663040, "gather": 1436160}
+NCU_TRAFFIC = {"spread": 660736, "gather": 1435648}
 
 
 def args_parse():
@@ -369,7 +369,7 @@ def run_ours(a):
     if dom in ("spread", "gather"):
         flop = 2.0 * counts[dom] * N
         ach = flop / (stage_ms[dom] * 1e-3) / 1e12
-        roof = {"kernel": "k_gather_flat<float,8,6,true>" if dom == "gather" else "k_spread_cl<float,8>",
+        roof = {"kernel": "k_gather_flat<float,8,6,true>" if dom == "gather" else "k_spread_cl<float,8,6>",
                 "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
                 "per_launch": f"{flop:.3e} flop ({counts[dom]} FMA/particle x {N})",
