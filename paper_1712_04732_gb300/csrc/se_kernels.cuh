@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "se_internal.h"
 
@@ -406,22 +407,52 @@ k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
     }
 }
 
+// Fixed-point accumulator of the gridding blocks: 32-bit integers for FP32 and
+// 64-bit for FP64 (shared-memory integer atomics run about 3x faster than float
+// atomics on GB300, and FP64 shared atomics slower still), with a per-tile
+// power-of-two scale s such that s times the tile's sum of |q| stays below
+// kFixMax (the window is at most 1; the margin below 2^31 (at most kFixTile
+// roundings of 1/2) or 2^63 covers the rounding of the updates): every block
+// value then fits, the conversions x s
+// and / s are exact, and integer sums do not depend on the order of updates.
+// The resolution 1/s follows the sum of |q|, which grows faster than the block
+// values for charges of both signs, so FP32 tiles with more than kFixTile
+// particles keep float atomics (their rounding then stays below float's).
+template <typename T> struct Fix;
+template <> struct Fix<float> {
+    using type = int;
+    static constexpr double kFixMax = 2147418112.0;                 // 2^31 - 2^16
+    static constexpr int kMaxExp = 120;
+    static constexpr int kFixTile = 512;
+    __device__ static int to(float v) { return __float2int_rn(v); }
+};
+template <> struct Fix<double> {
+    using type = long long;
+    static constexpr double kFixMax = 4611686018427387904.0;        // 2^62
+    static constexpr int kMaxExp = 1000;
+    static constexpr int kFixTile = 1 << 30;
+    __device__ static long long to(double v) { return __double2ll_rn(v); }
+};
+
 // Eq. (gridding) with shared-memory atomics, one tile per thread-block cluster
 // of CL CTAs (CL = 1: one CTA per tile).  Each CTA adds a 1/CL share of the
 // tile's particles to its own copy of the extended block, one particle per warp
 // at a time: the lanes own distinct (x, y) points of the stencil plane
 // (pp = lane + 32 e -> (pp mod P, pp div P)) and walk z, so an atomic
 // instruction never carries two updates of one word and the row pitch keeps
-// the lanes on distinct banks.  The cluster then sums the copies through
-// distributed shared memory, each CTA writing a slice of the compact block to
-// `scratch`.  When g != nullptr the charges are taken from g (original
-// particle order).
+// the lanes on distinct banks.  The block holds fixed-point integers (Fix<T>)
+// with a scale common to the cluster, from the sum of |q| over the whole tile
+// (FP32 tiles with more than Fix<T>::kFixTile particles: floats).
+// The cluster then sums the copies through distributed shared memory, each CTA
+// writing a slice of the compact block, converted back to T, to `scratch`.
+// When g != nullptr the charges are taken from g (original particle order).
 template <typename T, int P, int NU>
 __global__ void __launch_bounds__(kThreads)
 k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
             const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
 {
     pdl_wait();
+    using A = typename Fix<T>::type;
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int NE = (P * P + 31) / 32;
@@ -430,11 +461,19 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     const int beg = off[tile], end = off[tile + 1];
     if (beg == end) return;                               // the same for every CTA of the cluster
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *blk = reinterpret_cast<T *>(smraw);
-    T *wb = blk + align_up_elems<T>(tg.sblk);             // [warp][3P]
+    A *blk = reinterpret_cast<A *>(smraw);
+    T *wb = reinterpret_cast<T *>(blk + align_up_elems<A>(tg.sblk));   // [warp][3P]
+    __shared__ T qsum[kThreads / 32];
     zero_smem(blk, tg.sblk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     T *w = wb + warp * 3 * P;
+    // sum of |q| over the tile's particles: the bound of every block value / s
+    {
+        T aq = T(0);
+        for (int p = beg + threadIdx.x; p < end; p += blockDim.x) aq += fabs(g ? g[ia[p].x] : fq[p].w);
+        for (int o = 16; o > 0; o >>= 1) aq += __shfl_xor_sync(0xffffffffu, aq, o);
+        if (lane == 0) qsum[warp] = aq;
+    }
     // lane j < 3P evaluates the window along axis j / P at stencil point j mod P
     // (and lane j + 32 when 3P > 32), with that point's PKB coefficients in registers
     const int j0 = lane, j1 = lane + 32;
@@ -457,6 +496,18 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
         poff[e] = pdy[e] * pitch + pdx[e];
     }
     __syncthreads();
+    // s = 2^e, e the largest with s (1 + 1e-6) sum|q| <= kFixMax (the PKB fit
+    // stays within 1e-6 of the window's maximum 1)
+    T bound = T(0);
+    for (int i = 0; i < nw; ++i) bound += qsum[i];
+    const bool fix = end - beg <= Fix<T>::kFixTile;           // the same in every CTA of the cluster
+    int e2 = 0;
+    if (bound > T(0)) {
+        frexp(double(Fix<T>::kFixMax) / ((1.0 + 1e-6) * double(bound)), &e2);
+        e2 -= 1;
+    }
+    e2 = max(-Fix<T>::kMaxExp, min(Fix<T>::kMaxExp, e2));       // s and 1/s representable in T
+    const T scale = T(ldexp(1.0, e2)), inv_scale = T(ldexp(1.0, -e2));
 
     // The warp's particles are p0, p0 + stride, ...; lane i loads the i-th of
     // the next 32 of them, so one round of global loads serves 32 particles,
@@ -497,14 +548,29 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
             T wxy[NE];
 #pragma unroll
             for (int e = 0; e < NE; ++e) wxy[e] = qv * w[pdx[e]] * w[P + pdy[e]];
-            T *base = blk + bo;
+            if (fix) {
+                using U = typename std::conditional<sizeof(A) == 4, int, unsigned long long>::type;
 #pragma unroll
-            for (int dz = 0; dz < P; ++dz) {
-                const T wz = w[2 * P + dz];
-                T *row = base + dz * plane;
+                for (int e = 0; e < NE; ++e) wxy[e] *= scale;
+                U *base = reinterpret_cast<U *>(blk + bo);
 #pragma unroll
-                for (int e = 0; e < NE; ++e)
-                    if (pv[e]) atomicAdd(row + poff[e], wxy[e] * wz);
+                for (int dz = 0; dz < P; ++dz) {
+                    const T wz = w[2 * P + dz];
+                    U *row = base + dz * plane;
+#pragma unroll
+                    for (int e = 0; e < NE; ++e)
+                        if (pv[e]) atomicAdd(row + poff[e], U(Fix<T>::to(wxy[e] * wz)));
+                }
+            } else {
+                T *base = reinterpret_cast<T *>(blk + bo);
+#pragma unroll
+                for (int dz = 0; dz < P; ++dz) {
+                    const T wz = w[2 * P + dz];
+                    T *row = base + dz * plane;
+#pragma unroll
+                    for (int e = 0; e < NE; ++e)
+                        if (pv[e]) atomicAdd(row + poff[e], wxy[e] * wz);
+                }
             }
             __syncwarp();
         }
@@ -513,7 +579,7 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     // The cluster's copies are summed row by row (row r = z B1 + y sits at r pitch
     // in shared memory and at r B0 in the compact block); CTA `rank` writes rows
     // [rank R / CL, (rank + 1) R / CL), 32 / B0 rows per warp instruction.
-    const T *src[8];
+    const A *src[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
     T *dst = scratch + size_t(tile) * tg.blk;
@@ -523,11 +589,19 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     if (sub < rpw)
         for (int r = r0 + warp * rpw + sub; r < r1; r += nw * rpw) {
             const int si = r * pitch + x;
-            T v = src[0][si];
+            if (fix) {
+                A v = src[0][si];
 #pragma unroll
-            for (int j = 1; j < 8; ++j)
-                if (j < CL) v += src[j][si];
-            dst[r * B0 + x] = v;
+                for (int j = 1; j < 8; ++j)
+                    if (j < CL) v += src[j][si];
+                dst[r * B0 + x] = T(v) * inv_scale;
+            } else {
+                T v = reinterpret_cast<const T *>(src[0])[si];
+#pragma unroll
+                for (int j = 1; j < 8; ++j)
+                    if (j < CL) v += reinterpret_cast<const T *>(src[j])[si];
+                dst[r * B0 + x] = v;
+            }
         }
     cluster.sync();                                       // no CTA leaves while its block is still read
 }
