@@ -171,8 +171,10 @@ def _config(spec):
 def run_batch(se, wl, dev, flush, steps):
     """64 independent systems, N log-uniform in [1e3, 1e5], D alternating 3, 2,
     xi = 8 (N/1e4)^(1/3), PKB, per-system M and P from the Sec. 6 rules at
-    relative tolerance 1e-5, FP32, phi + F: the batched graph against one plain
-    se_force call per system, both timed with CUDA events after an L2 flush."""
+    relative tolerance 1e-5, FP32, phi + F: the autotuned batched graph (the
+    tuner picks the multi-system or the per-system-branches form) against one
+    plain se_force call per system, both timed with CUDA events after an L2
+    flush; the two graph forms are also timed side by side without tuning."""
     import numpy as np
     import torch
     sysl = wl.batch_systems(64, seed=1)
@@ -203,10 +205,29 @@ def run_batch(se, wl, dev, flush, steps):
         res[name] = {"ms_per_step": ms, "value": ntot / (ms * 1e-3), "unit": "particles/s"}
     Ms = [b.system_info(i)["M"] for i in range(len(specs))]
     Ps = [b.system_info(i)["P"] for i in range(len(specs))]
+    form, kernels = b.form()
     b.close()
     res.update({"systems": len(specs), "particles": ntot, "M_range": [min(Ms), max(Ms)],
                 "P_range": [min(Ps), max(Ps)], "setup_s_incl_autotune": setup_s,
+                "form": form, "library_kernels_per_call": kernels,
                 "speedup_graph_over_per_system": res["per_system"]["ms_per_step"] / res["graph"]["ms_per_step"]})
+    # the two graph forms side by side, default kernel variants
+    for fname in ("fused", "branches"):
+        bf = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, device=dev, autotune=False, form=fname)
+        for _ in range(3):
+            bf.force(x, q, out=out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record()
+            bf.force(x, q, out=out)
+            e1.record()
+        torch.cuda.synchronize(dev)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        res[f"untuned_{fname}"] = {"ms_per_step": ms, "value": ntot / (ms * 1e-3), "unit": "particles/s",
+                                   "library_kernels_per_call": bf.form()[1]}
+        bf.close()
     return res
 
 

@@ -244,16 +244,27 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
  * the absolute tolerance eps_rel * B_i, B_i = sqrt(Q_i) f_c(xi_i L_i) / L_i
  * (Eq. fc-expression; Q = NULL takes Q_i = N_i / 3, the mean for charges
  * uniform in [-1, 1]); M_i is then rounded up to an FFT-friendly size.  The
- * window is w for all systems.  Unless SE_BATCH_NO_AUTOTUNE is given, the first
- * se_batch_force call times the gridding tile (4, 8, 16) and kernel variants
- * per system on the real inputs and keeps the fastest.  Every call replays one
- * CUDA graph (captured on first use and whenever the pointers change) whose
- * parallel branches run the systems concurrently.
+ * window is w for all systems.  Every call replays one CUDA graph (captured on
+ * first use and whenever the pointers change) in one of two forms:
+ *  - multi-system (SE_BATCH_FUSED): binning, gridding, block merge and
+ *    gathering of all systems run as one kernel launch per stage and class of
+ *    systems with equal support P_i (Alg. 4 steps 1 and 5), each system's
+ *    transforms and scaling (steps 2-4) in parallel graph branches;
+ *  - per-system (SE_BATCH_BRANCHES): each system's whole pipeline in parallel
+ *    graph branches.
+ * Unless SE_BATCH_NO_AUTOTUNE is given, the first se_batch_force call times the
+ * gridding tile (4, 8, 16) and kernel variants per system on the real inputs,
+ * then the forms as captured graphs (the multi-system one with 1, 2, 4 or 8
+ * CTAs per gridding tile, also with tiles of edge 4 for FP32 systems of more
+ * than 512 particles per tile), and keeps the fastest; without autotuning the
+ * form is the multi-system one unless SE_BATCH_BRANCHES is given.
  * Arrays x [sum N][3], q [sum N], F [sum N][3], phi [sum N] (may be NULL) are
  * concatenated in system order (device pointers); energy [nsys] (device, may be
  * NULL) receives E_i = 1/2 sum q phi per system.  The first call synchronises
  * (autotuning); later calls are asynchronous on the batch stream. */
 #define SE_BATCH_NO_AUTOTUNE 1u
+#define SE_BATCH_BRANCHES    2u   /* use the per-system form only */
+#define SE_BATCH_FUSED       4u   /* use the multi-system form only */
 typedef struct se_batch_s *se_batch_t;
 se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int *D, const double *L,
                           const double *xi, const double *Q, double eps_rel, se_window w, se_dtype dt,
@@ -267,6 +278,10 @@ se_status se_batch_force_each(se_batch_t batch, const void *x, const void *q, vo
                               double *energy);
 /* Derived parameters of system i. */
 se_status se_batch_get_system(se_batch_t batch, int i, se_plan_info_t *info);
+/* Form of the captured graph (1 per-system, 2 multi-system) and the number of
+ * library kernels one call launches (cuFFT's own kernels excluded; valid after
+ * the first se_batch_force).  Either pointer may be NULL. */
+se_status se_batch_get_form(se_batch_t batch, int *form, int64_t *kernels_per_call);
 
 /* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
  * approximation-error estimates of Sec. 5.2, rounded up to even, with the

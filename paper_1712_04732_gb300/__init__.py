@@ -210,10 +210,15 @@ class Batch:
     """Many independent systems evaluated together (``se_batch_create``): per-system
     M and P from the rules of Sec. 6 for relative tolerance ``eps_rel``, autotuned
     kernel variants and one CUDA graph per call.  ``systems`` is a list of
-    (N, D, L, xi) tuples; ``Q`` optional per-system sums of q^2."""
+    (N, D, L, xi) tuples; ``Q`` optional per-system sums of q^2.  ``form``:
+    "auto" (the tuner chooses), "fused" (binning, gridding, merge and gathering
+    of all systems in one launch per stage and support class) or "branches"
+    (every system's own pipeline in parallel graph branches)."""
+
+    _FORMS = {"auto": 0, "branches": nat.SE_BATCH_BRANCHES, "fused": nat.SE_BATCH_FUSED}
 
     def __init__(self, systems, eps_rel=1e-5, window="pkb", dtype=torch.float32, device=None, Q=None,
-                 autotune=True):
+                 autotune=True, form="auto"):
         self._lib = nat.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.dtype = dtype
@@ -226,9 +231,9 @@ class Batch:
         Qa = (ctypes.c_double * n)(*Q) if Q is not None else None
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
+            flags = (0 if autotune else nat.SE_BATCH_NO_AUTOTUNE) | self._FORMS[form]
             nat.check(self._lib.se_batch_create(ctypes.byref(h), n, Na, Da, La, Xa, Qa, float(eps_rel),
-                                                _WINDOWS[window], _DTYPES[dtype],
-                                                0 if autotune else nat.SE_BATCH_NO_AUTOTUNE))
+                                                _WINDOWS[window], _DTYPES[dtype], flags))
         self._h = h
         self._stream = None
 
@@ -242,6 +247,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def form(self):
+        """("fused" | "branches", library kernels per call) of the captured graph."""
+        f = ctypes.c_int()
+        k = ctypes.c_int64()
+        nat.check(self._lib.se_batch_get_form(self._h, ctypes.byref(f), ctypes.byref(k)))
+        return ("fused" if f.value == 2 else "branches"), int(k.value)
 
     def system_info(self, i):
         inf = nat.Info()

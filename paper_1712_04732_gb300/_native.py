@@ -13,7 +13,7 @@ from . import build as _build
 SE_WIN_GAUSSIAN, SE_WIN_PKB = 0, 1
 SE_F32, SE_F64 = 0, 1
 SE_ADD_SELF, SE_CHECK_NEUTRAL, SE_SYNC_CHECK, SE_HOST_IO = 1, 2, 4, 8
-SE_BATCH_NO_AUTOTUNE = 1
+SE_BATCH_NO_AUTOTUNE, SE_BATCH_BRANCHES, SE_BATCH_FUSED = 1, 2, 4
 SE_ACCUMULATE = 16
 
 STATUS = {0: "SE_OK", 1: "SE_EINVAL", 2: "SE_ENONNEUTRAL", 3: "SE_EOUTOFBOX", 4: "SE_ENOMEM",
@@ -24,7 +24,7 @@ EXPORTS = ["se_opts_default", "se_plan_create", "se_plan_destroy", "se_plan_set_
            "se_plan_get_info", "se_plan_check", "se_potential", "se_force", "se_vjp",
            "se_plan_set_profiling", "se_plan_get_profile", "se_potential_noalloc",
            "se_batch_create", "se_batch_destroy", "se_batch_set_stream", "se_batch_force", "se_batch_force_each",
-           "se_batch_get_system", "se_real_space",
+           "se_batch_get_system", "se_batch_get_form", "se_real_space",
            "se_params_from_tolerance", "se_status_str", "se_last_error"]
 SE_N_STAGES = 8
 STAGES = ["bin", "spread", "merge", "fft_fwd", "scale", "fft_inv", "gather", "energy"]
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "se_batch_force": (ci, [vp, vp, vp, vp, vp, vp]),
         "se_batch_force_each": (ci, [vp, vp, vp, vp, vp, vp]),
         "se_batch_get_system": (ci, [vp, ci, ctypes.POINTER(Info)]),
+        "se_batch_get_form": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(i64)]),
         "se_plan_get_profile": (ci, [vp, ctypes.POINTER(cd), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "se_params_from_tolerance": (ci, [cd, cd, cd, cd, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "se_status_str": (ctypes.c_char_p, [ci]),

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libse_gb300.so")
-SOURCES = ["se_api.cu", "se_plan.cu", "se_kern_f32.cu", "se_kern_f64.cu", "se_noalloc.cu", "se_batch.cu", "se_real.cu"]
+SOURCES = ["se_api.cu", "se_plan.cu", "se_kern_f32.cu", "se_kern_f64.cu", "se_mbatch_f32.cu", "se_mbatch_f64.cu",
+           "se_noalloc.cu", "se_batch.cu", "se_real.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,7 +1,10 @@
 // Batched evaluation of many independent systems (se_batch_*): per-system
 // parameters from the rules of Sec. 6, a timing autotuner over the gridding
-// tile and kernel variants, and one CUDA graph whose parallel branches run the
-// systems' pipelines concurrently.
+// tile, kernel variants and execution form, and one CUDA graph per call.  Two
+// forms: the multi-system pipeline (binning, gridding, merge and gathering of
+// all systems in one launch per stage and window-support class, the transforms
+// of each system in parallel graph branches), or every system's whole pipeline
+// in parallel graph branches.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -29,6 +32,8 @@ struct Variant {
     int tile, spread_mode, split, gather_mode;
 };
 
+enum Form { kFormBranches = 1, kFormFused = 2 };
+
 }  // namespace
 
 struct se_batch_s {
@@ -46,6 +51,12 @@ struct se_batch_s {
     cudaGraphExec_t exec = nullptr;
     const void *key[5] = {};          // pointers the graph was captured with
     bool tuned = false, autotune = true;
+    int form = kFormFused;            // kFormFused or kFormBranches
+    int force_form = 0;               // form fixed by the caller (0: chosen by the tuner)
+    int fused_cl = 0;                 // CTAs per gridding tile of the multi-system form (0: rule)
+    se::MBatch mb;                    // multi-system workspace (form kFormFused)
+    bool mb_built = false;
+    int64_t kernels_per_call = 0;     // library kernels one call launches (cuFFT excluded)
     int64_t graph_launches = 0;
     se_window window = SE_WIN_PKB;
     std::vector<double> L, xi;
@@ -92,6 +103,34 @@ void release_graph(se_batch_s *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
+}
+
+void release_fused(se_batch_s *b)
+{
+    if (!b->mb_built) return;
+    if (b->dtype == SE_F32) se::MOps<float>::release(&b->mb);
+    else se::MOps<double>::release(&b->mb);
+    b->mb_built = false;
+}
+
+se_status build_fused(se_batch_s *b)
+{
+    release_fused(b);
+    se_status st = b->dtype == SE_F32 ? se::MOps<float>::build(&b->mb, b->plans, b->off, b->fused_cl)
+                                      : se::MOps<double>::build(&b->mb, b->plans, b->off, b->fused_cl);
+    if (st == SE_OK) b->mb_built = true;
+    return st;
+}
+
+// Transforms and scaling of system i (Alg. 4 steps 2-4) on stream s, between the
+// multi-system gridding and gathering.
+se_status convolve_system(se_batch_s *b, int i, cudaStream_t s)
+{
+    se_plan_s *p = b->plans[i];
+    se_status st = se_plan_set_stream(p, s);
+    if (st != SE_OK) return st;
+    return b->dtype == SE_F32 ? se::Ops<float>::convolve(p, p->grid_in, p->grid_out)
+                              : se::Ops<double>::convolve(p, p->grid_in, p->grid_out);
 }
 
 // Autotuner: for every system time each candidate variant (median of a few
@@ -148,9 +187,84 @@ se_status autotune(se_batch_s *b, const void *x, const void *q, void *F, void *p
     return SE_OK;
 }
 
-se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
+// Order of the systems over the branches: longest first onto the least-loaded
+// branch (costs from the tuner, else N); returns the branch of every system.
+std::vector<int> assign_branches(const se_batch_s *b)
+{
+    std::vector<int> order(b->nsys), br(b->nsys, 0);
+    for (int i = 0; i < b->nsys; ++i) order[i] = i;
+    auto cost = [&](int i) { return b->cost[i] > 0 ? double(b->cost[i]) : double(b->N[i]); };
+    std::sort(order.begin(), order.end(), [&](int u, int v) { return cost(u) > cost(v); });
+    double load[kBranches] = {};
+    for (int r = 0; r < b->nsys; ++r) {
+        const int i = order[r];
+        const int k = int(std::min_element(load, load + kBranches) - load);
+        load[k] += cost(i);
+        br[i] = k;
+    }
+    return br;
+}
+
+// Capture of the multi-system form: gridding of every system, the transforms
+// of the systems in parallel branches, gathering of every system.
+se_status capture_fused(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    if (!b->mb_built) {
+        se_status st = build_fused(b);
+        if (st != SE_OK) return st;
+    }
+    release_graph(b);
+    const int64_t l0 = b->mb.launches;
+    int64_t lp = 0;
+    for (se_plan_t p : b->plans) lp += p->launches;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return se::cuda_fail(e, "begin capture");
+    se_status st = b->dtype == SE_F32
+                       ? se::MOps<float>::grid(&b->mb, static_cast<const float *>(x), static_cast<const float *>(q), b->cap)
+                       : se::MOps<double>::grid(&b->mb, static_cast<const double *>(x), static_cast<const double *>(q),
+                                                b->cap);
+    if (st == SE_OK) {
+        cudaEventRecord(b->fork, b->cap);
+        for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+        const std::vector<int> br = assign_branches(b);
+        for (int i = 0; i < b->nsys && st == SE_OK; ++i) st = convolve_system(b, i, b->branch[br[i]]);
+        for (int k = 0; k < kBranches; ++k) {
+            cudaEventRecord(b->join[k], b->branch[k]);
+            cudaStreamWaitEvent(b->cap, b->join[k], 0);
+        }
+    }
+    if (st == SE_OK)
+        st = b->dtype == SE_F32 ? se::MOps<float>::gather(&b->mb, static_cast<float *>(phi), static_cast<float *>(F),
+                                                          energy, b->cap)
+                                : se::MOps<double>::gather(&b->mb, static_cast<double *>(phi),
+                                                           static_cast<double *>(F), energy, b->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != SE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return se::cuda_fail(e, "end capture");
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return se::cuda_fail(e, "graph instantiate");
+    int64_t lp1 = 0;
+    for (se_plan_t p : b->plans) lp1 += p->launches;
+    b->kernels_per_call = (b->mb.launches - l0) + (lp1 - lp);
+    b->key[0] = x;
+    b->key[1] = q;
+    b->key[2] = F;
+    b->key[3] = phi;
+    b->key[4] = energy;
+    return SE_OK;
+}
+
+// Capture of the per-system form: every system's whole pipeline in parallel branches.
+se_status capture_branches(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
 {
     release_graph(b);
+    int64_t lp = 0;
+    for (se_plan_t p : b->plans) lp += p->launches;
     // capture from an internal stream (the caller's may be the legacy stream,
     // which cannot be captured); the graph is launched on the caller's stream
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
@@ -158,18 +272,8 @@ se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *ph
     se_status st = SE_OK;
     cudaEventRecord(b->fork, b->cap);
     for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(b->branch[k], b->fork, 0);
-    // longest first onto the least-loaded branch (costs from the tuner, else N)
-    std::vector<int> order(b->nsys);
-    for (int i = 0; i < b->nsys; ++i) order[i] = i;
-    auto cost = [&](int i) { return b->cost[i] > 0 ? double(b->cost[i]) : double(b->N[i]); };
-    std::sort(order.begin(), order.end(), [&](int u, int v) { return cost(u) > cost(v); });
-    double load[kBranches] = {};
-    for (int r = 0; r < b->nsys && st == SE_OK; ++r) {
-        const int i = order[r];
-        const int k = int(std::min_element(load, load + kBranches) - load);
-        load[k] += cost(i);
-        st = run_system(b, i, x, q, F, phi, energy, b->branch[k]);
-    }
+    const std::vector<int> br = assign_branches(b);
+    for (int i = 0; i < b->nsys && st == SE_OK; ++i) st = run_system(b, i, x, q, F, phi, energy, b->branch[br[i]]);
     for (int k = 0; k < kBranches; ++k) {
         cudaEventRecord(b->join[k], b->branch[k]);
         cudaStreamWaitEvent(b->cap, b->join[k], 0);
@@ -184,12 +288,112 @@ se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *ph
     b->graph = g;
     e = cudaGraphInstantiate(&b->exec, g, 0);
     if (e != cudaSuccess) return se::cuda_fail(e, "graph instantiate");
+    int64_t lp1 = 0;
+    for (se_plan_t p : b->plans) lp1 += p->launches;
+    b->kernels_per_call = lp1 - lp;
     b->key[0] = x;
     b->key[1] = q;
     b->key[2] = F;
     b->key[3] = phi;
     b->key[4] = energy;
     return SE_OK;
+}
+
+se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    return b->form == kFormFused ? capture_fused(b, x, q, F, phi, energy) : capture_branches(b, x, q, F, phi, energy);
+}
+
+// Median time of a few replays of the captured graph.
+float time_graph(se_batch_s *b, cudaEvent_t e0, cudaEvent_t e1)
+{
+    float t[5];
+    for (int r = 0; r < 6; ++r) {
+        cudaEventRecord(e0, b->stream);
+        cudaGraphLaunch(b->exec, b->stream);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+    }
+    std::sort(t, t + 5);
+    return t[2];
+}
+
+// Second stage of the autotuner: the execution form, each candidate timed as a
+// captured graph on the real inputs, the fastest kept.  Candidates: the
+// per-system branches, and the multi-system pipeline with the rule's, 1, 2, 4
+// or 8 CTAs per gridding tile, on the current plans and on plans whose dense
+// systems (FP32, more than 512 particles per tile on average) take a gridding
+// tile of edge 4 (smaller tiles keep the integer shared-memory atomics, which
+// run about three times faster than float ones).
+se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
+{
+    struct Cand { int form, cl; bool dense4; };
+    std::vector<se_plan_t> alt(b->nsys, nullptr);
+    bool have_alt = false;
+    if (b->force_form != kFormBranches && b->dtype == SE_F32)
+        for (int i = 0; i < b->nsys; ++i) {
+            const se_plan_s *p = b->plans[i];
+            const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+            const bool big = p->tg.T[0] > 4 || p->tg.T[1] > 4 || p->tg.T[2] > 4;
+            if (!big || b->N[i] <= 512 * int64_t(nt)) continue;
+            Variant v = b->chosen[i];
+            v.tile = 4;
+            if (make_plan(b, i, b->L[i], b->D[i], b->xi[i], b->M[i], b->P[i], b->window, v, &alt[i]) == SE_OK)
+                have_alt = true;
+            else {
+                se_plan_destroy(alt[i]);
+                alt[i] = nullptr;
+            }
+        }
+    auto swap_alt = [&]() {
+        for (int i = 0; i < b->nsys; ++i)
+            if (alt[i]) std::swap(alt[i], b->plans[i]);
+    };
+    std::vector<Cand> cands;
+    if (b->force_form != kFormBranches)
+        for (int d = 0; d < (have_alt ? 2 : 1); ++d)
+            for (int cl : {0, 1, 2, 4, 8}) cands.push_back({kFormFused, cl, d == 1});
+    if (b->force_form != kFormFused) cands.push_back({kFormBranches, 0, false});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick = cands.front();
+    se_status st = SE_OK;
+    bool swapped = false;
+    for (const Cand &c : cands) {
+        if (c.dense4 != swapped) {
+            release_graph(b);
+            release_fused(b);
+            swap_alt();
+            swapped = c.dense4;
+        }
+        b->form = c.form;
+        if (c.form == kFormFused) {
+            b->fused_cl = c.cl;
+            if ((st = build_fused(b)) != SE_OK) break;
+        }
+        if ((st = capture(b, x, q, F, phi, energy)) != SE_OK) break;
+        const float t = time_graph(b, e0, e1);
+        if (t < best) {
+            best = t;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release_graph(b);
+    release_fused(b);
+    if (swapped != pick.dense4) swap_alt();            // the chosen plan set in b->plans
+    for (se_plan_t p : alt) se_plan_destroy(p);        // the other set
+    if (st != SE_OK) return st;
+    b->form = pick.form;
+    b->fused_cl = pick.cl;
+    if (pick.dense4)
+        for (int i = 0; i < b->nsys; ++i)
+            if (b->plans[i]->tg.T[0] == 4) b->chosen[i].tile = 4;
+    return pick.form == kFormFused ? build_fused(b) : SE_OK;
 }
 
 }  // namespace
@@ -208,6 +412,12 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
     b->nsys = nsys;
     b->dtype = dt;
     b->autotune = !(flags & SE_BATCH_NO_AUTOTUNE);
+    if ((flags & SE_BATCH_FUSED) && (flags & SE_BATCH_BRANCHES)) {
+        delete b;
+        return se::fail(SE_EINVAL, "SE_BATCH_FUSED and SE_BATCH_BRANCHES exclude each other");
+    }
+    b->force_form = (flags & SE_BATCH_FUSED) ? kFormFused : (flags & SE_BATCH_BRANCHES) ? kFormBranches : 0;
+    b->form = b->force_form ? b->force_form : kFormFused;
     b->N.assign(N, N + nsys);
     b->off.resize(nsys + 1, 0);
     for (int i = 0; i < nsys; ++i) {
@@ -261,6 +471,7 @@ se_status se_batch_destroy(se_batch_t b)
     if (!b) return SE_OK;
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     release_graph(b);
+    release_fused(b);
     for (se_plan_t p : b->plans) se_plan_destroy(p);
     for (int k = 0; k < kBranches; ++k) {
         if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
@@ -288,8 +499,11 @@ se_status se_batch_force(se_batch_t b, const void *x, const void *q, void *F, vo
     se_status st;
     if (b->autotune && !b->tuned) {
         release_graph(b);
-        // tuning needs the real inputs; it runs each system eagerly a few times
+        release_fused(b);
+        // tuning needs the real inputs; it runs each system eagerly a few times,
+        // then times the execution forms as captured graphs
         if ((st = autotune(b, x, q, F, phi, energy, b->L, b->D, b->xi, b->M, b->P, b->window)) != SE_OK) return st;
+        if ((st = tune_form(b, x, q, F, phi, energy)) != SE_OK) return st;
     }
     const void *k[5] = {x, q, F, phi, energy};
     bool same = b->exec != nullptr;
@@ -309,6 +523,14 @@ se_status se_batch_force_each(se_batch_t b, const void *x, const void *q, void *
         se_status st = run_system(b, i, x, q, F, phi, energy, b->stream);
         if (st != SE_OK) return st;
     }
+    return SE_OK;
+}
+
+se_status se_batch_get_form(se_batch_t b, int *form, int64_t *kernels_per_call)
+{
+    if (!b) return se::fail(SE_EINVAL, "batch is NULL");
+    if (form) *form = b->form;
+    if (kernels_per_call) *kernels_per_call = b->kernels_per_call;
     return SE_OK;
 }
 

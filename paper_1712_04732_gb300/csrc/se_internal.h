@@ -230,4 +230,55 @@ struct Ops {
     static se_status spread_with_scratch(se_plan_s *p, void *dst, void *scratch);
 };
 
+// Multi-system pipeline of a batch (se_mbatch_impl.cuh): binning, gridding,
+// block merge and gathering of every system of the batch each run as one
+// launch per class of systems with the same window support P; the transforms
+// and the scaling stay with each system's own plan.  Systems are processed in
+// class order (their tiles, sorted records and gathering CTAs are numbered
+// consecutively in that order); descriptors and tables are indexed by the
+// system's position in the caller's arrays.
+struct MClass {
+    int P = 0, nu = 0;
+    int tile_begin = 0, ntiles = 0;      // global tiles of the class
+    int cta_begin = 0, ncta = 0;         // gathering CTAs of the class
+    int64_t particles = 0;
+    int CL = 1;                          // CTAs per tile of the gridding cluster
+    int J = 2;                           // tiles per axis whose blocks overlap a grid point
+    size_t spread_smem = 0;              // dynamic shared memory of the gridding launch
+    se_plan_t plan = nullptr;            // a plan of the class (window coefficients)
+};
+
+struct MBatch {
+    int nsys = 0;
+    int64_t ntot = 0;
+    int ntiles = 0, ncta = 0;
+    std::vector<MClass> classes;
+    void *desc = nullptr;                // SysDesc<T>[nsys]
+    int64_t *p0 = nullptr;               // [nsys + 1] first particle of each system (caller's order)
+    int *tile_sys = nullptr;             // [ntiles] system of each global tile
+    int *cta_sys = nullptr;              // [ncta] system of each gathering CTA
+    int *tile_cnt = nullptr, *tile_off = nullptr;   // [ntiles + 1]
+    int2 *tile_rank = nullptr;           // [ntot]
+    Particles prt{};                     // [ntot] sorted records
+    void *scratch = nullptr;             // per-tile gridding blocks of every system
+    double *part = nullptr;              // [ncta] per-CTA energy partial sums
+    int *done = nullptr;                 // [nsys] completion counters (zero between calls)
+    int *err = nullptr;                  // latched input errors
+    int64_t bytes = 0;
+    int64_t launches = 0;                // kernels launched by the multi-system stages
+};
+
+template <typename T>
+struct MOps {
+    // Build the descriptors and workspace for the systems of `plans` whose
+    // particles start at off[i] (off[nsys] = total); cl > 0 forces the CTAs per
+    // gridding tile of every class.
+    static se_status build(MBatch *m, const std::vector<se_plan_t> &plans, const std::vector<int64_t> &off, int cl);
+    // Binning, gridding and merge into every plan's grid_in (stream s).
+    static se_status grid(MBatch *m, const T *x, const T *q, cudaStream_t s);
+    // Gathering of phi and F from every plan's grid_out, energies E[nsys].
+    static se_status gather(MBatch *m, T *phi, T *F, double *energy, cudaStream_t s);
+    static void release(MBatch *m);
+};
+
 }  // namespace se

@@ -446,20 +446,21 @@ template <> struct Fix<double> {
 // The cluster then sums the copies through distributed shared memory, each CTA
 // writing a slice of the compact block, converted back to T, to `scratch`.
 // When g != nullptr the charges are taken from g (original particle order).
+//
+// spread_cl_tile is the work of one CTA of the cluster on tile `tile` (local
+// index in the grid of tg) holding the sorted particles [beg, end); the compact
+// block goes to dst.  Every CTA of the cluster calls it with the same tile.
 template <typename T, int P, int NU>
-__global__ void __launch_bounds__(kThreads)
-k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
-            const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
+__device__ __forceinline__ void spread_cl_tile(const TileGeom &tg, int tile, int beg, int end,
+                                               const typename Vec4<T>::type *__restrict__ fq,
+                                               const int4 *__restrict__ ia, const T *__restrict__ g,
+                                               const WindowArgs<T> &wa, T *__restrict__ dst)
 {
-    pdl_wait();
     using A = typename Fix<T>::type;
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int NE = (P * P + 31) / 32;
     const int CL = int(cluster.num_blocks()), rank = int(cluster.block_rank());
-    const int tile = blockIdx.x / CL;
-    const int beg = off[tile], end = off[tile + 1];
-    if (beg == end) return;                               // the same for every CTA of the cluster
     extern __shared__ __align__(16) unsigned char smraw[];
     A *blk = reinterpret_cast<A *>(smraw);
     T *wb = reinterpret_cast<T *>(blk + align_up_elems<A>(tg.sblk));   // [warp][3P]
@@ -582,7 +583,6 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     const A *src[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
-    T *dst = scratch + size_t(tile) * tg.blk;
     const int B0 = tg.B[0], R = tg.B[1] * tg.B[2];
     const int rpw = 32 / B0, sub = lane / B0, x = lane - sub * B0;
     const int r0 = rank * R / CL, r1 = (rank + 1) * R / CL;
@@ -604,6 +604,18 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
             }
         }
     cluster.sync();                                       // no CTA leaves while its block is still read
+}
+
+template <typename T, int P, int NU>
+__global__ void __launch_bounds__(kThreads)
+k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type *__restrict__ fq,
+            const int4 *__restrict__ ia, const T *__restrict__ g, WindowArgs<T> wa, T *__restrict__ scratch)
+{
+    pdl_wait();
+    const int tile = blockIdx.x / int(cooperative_groups::this_cluster().num_blocks());
+    const int beg = off[tile], end = off[tile + 1];
+    if (beg == end) return;                               // the same for every CTA of the cluster
+    spread_cl_tile<T, P, NU>(tg, tile, beg, end, fq, ia, g, wa, scratch + size_t(tile) * tg.blk);
 }
 
 // Sum of the tile blocks covering each grid point, in a fixed order, written
@@ -1063,13 +1075,15 @@ __global__ void k_unpad_1p(int nl, int Mt1, int Mt2, int s1, int s2, int z1, int
 // the CTA that finishes last (the others have published their partials).
 // Thread 0 of every CTA has written part[blockIdx.x]; it alone fences before
 // taking its ticket.
-__device__ __forceinline__ void finish_energy(double *part, int n, double *energy, int *done)
+// finish_energy_of is the same over `ctas` CTAs that share the counter `done`
+// (a segment of the grid); finish_energy takes the whole grid.
+__device__ __forceinline__ void finish_energy_of(double *part, int n, double *energy, int *done, int ctas)
 {
     __shared__ bool last;
     __shared__ double red[256];
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(done, 1) == int(gridDim.x) - 1;
+        last = atomicAdd(done, 1) == ctas - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -1086,6 +1100,11 @@ __device__ __forceinline__ void finish_energy(double *part, int n, double *energ
         *energy = red[0];
         *done = 0;
     }
+}
+
+__device__ __forceinline__ void finish_energy(double *part, int n, double *energy, int *done)
+{
+    finish_energy_of(part, n, energy, done, int(gridDim.x));
 }
 
 __device__ __forceinline__ void cp_async_elem(float *dst, const float *src)
@@ -1289,25 +1308,27 @@ k_gather(TileGeom tg, int split, const int *__restrict__ off, const typename Vec
 // warps take consecutive groups of G sorted particles and read the grid
 // directly (the sorted order keeps neighbouring stencils in L1).  Per-CTA
 // partial energies go to part[blockIdx.x].
+//
+// gather_flat_cta is the work of one CTA on the sorted particles
+// [pbeg, min(pbeg + 8 G, pend)) of the grid described by tg, v; it returns the
+// lane's share of sum 1/2 q_m phi_m (non-zero on the dx = 0 lanes only).
 template <typename T, int P, int NU, bool GRAD>
-__global__ void __launch_bounds__(kThreads)
-k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__ fq, const int4 *__restrict__ ia,
-              WindowArgs<T> wa, const T *__restrict__ grid, GridView v, T *__restrict__ phi, T *__restrict__ F,
-              double *__restrict__ part, double *energy, int *done, T inv_h, T self_coef)
+__device__ __forceinline__ double gather_flat_cta(int64_t pbeg, int64_t pend, const TileGeom &tg,
+                                                  const typename Vec4<T>::type *__restrict__ fq,
+                                                  const int4 *__restrict__ ia, const WindowArgs<T> &wa,
+                                                  const T *__restrict__ grid, GridView v, T *__restrict__ phi,
+                                                  T *__restrict__ F, T inv_h, T self_coef)
 {
-    pdl_wait();
-
     constexpr int G = LaneMap<P>::G;
     __shared__ T wbs[kThreads / 32][32 * 6];
-    __shared__ double epart[kThreads / 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / P, dx = lane - grp * P;
     const bool lane_on = grp < G;
     LaneCoef<T, NU> cf;
     if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
     T *w = &wbs[warp][(lane_on ? grp : 0) * 6 * P];
-    const int64_t p = (int64_t(blockIdx.x) * nw + warp) * G + grp;
-    const bool has = lane_on && p < N;
+    const int64_t p = pbeg + int64_t(warp) * G + grp;
+    const bool has = lane_on && p < pend;
     typename Vec4<T>::type r;
     int4 a = make_int4(0, 0, 0, 0);
     if (has) {
@@ -1353,15 +1374,37 @@ k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__
         }
         esum = 0.5 * double(qv) * double(phv);
     }
+    return esum;
+}
+
+// Sum of the CTA's per-lane energy shares into *dst (thread 0 writes).
+__device__ __forceinline__ void cta_energy_partial(double esum, double *dst)
+{
+    __shared__ double epart[kThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int s = 16; s > 0; s >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, s);
+    if (lane == 0) epart[warp] = esum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += epart[i];
+        *dst = s;
+    }
+}
+
+template <typename T, int P, int NU, bool GRAD>
+__global__ void __launch_bounds__(kThreads)
+k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__ fq, const int4 *__restrict__ ia,
+              WindowArgs<T> wa, const T *__restrict__ grid, GridView v, T *__restrict__ phi, T *__restrict__ F,
+              double *__restrict__ part, double *energy, int *done, T inv_h, T self_coef)
+{
+    pdl_wait();
+
+    constexpr int G = LaneMap<P>::G;
+    const double esum = gather_flat_cta<T, P, NU, GRAD>(int64_t(blockIdx.x) * (kThreads / 32) * G, N, tg, fq, ia,
+                                                         wa, grid, v, phi, F, inv_h, self_coef);
     if (part) {
-        for (int s = 16; s > 0; s >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, s);
-        if (lane == 0) epart[warp] = esum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < nw; ++i) s += epart[i];
-            part[blockIdx.x] = s;
-        }
+        cta_energy_partial(esum, part + blockIdx.x);
         finish_energy(part, gridDim.x, energy, done);
     }
 }

@@ -118,8 +118,11 @@ static void solve_dense(std::vector<double> A, std::vector<double> b, int n, dou
 // coefficients of 2 d/dxbar, the derivative in grid units.
 static void fit_pkb(se_plan_s *p)
 {
+    // The window depends on x / h only (w = P h / 2), so the fit runs in grid
+    // units (h = 1): every plan with the same P, nu and beta gets the same
+    // coefficients, bit for bit, whatever its grid spacing.
     const int P = p->P, nu = p->nu, n = nu + 1;
-    const double h = p->h, w = P * h / 2.0, beta = p->shape;
+    const double h = 1.0, w = P * h / 2.0, beta = p->shape;
     std::vector<double> nodes(n), V(n * n);
     for (int k = 0; k < n; ++k) {
         nodes[k] = std::cos(M_PI * (k + 0.5) / n);
@@ -675,6 +678,10 @@ static int choose_tile(int n, bool periodic, int pref)
 {
     if (!periodic) return pref;
     if (n % pref == 0) return pref;
+    // a small tile was asked for (dense systems): the nearest divisor above it, up to 8
+    if (pref <= 4)
+        for (int t = pref + 1; t <= 8; ++t)
+            if (n % t == 0) return t;
     for (int t = 16; t >= 4; --t)
         if (n % t == 0) return t;
     for (int t = 3; t >= 1; --t)

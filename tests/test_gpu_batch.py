@@ -2,6 +2,8 @@
 batch matches a standalone plan with the same parameters, the CUDA-graph form
 matches the per-system launches, and the Sec. 6 parameter choice meets the
 requested tolerance against the direct sums."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -71,3 +73,105 @@ def test_batch_parameters_meet_the_tolerance():
         assert _rel(phi[off:off + n].cpu().numpy()[idx], pa) < 5e-5
         off += n
     b.close()
+
+
+def _mixed_systems(n_sys, seed, n_min=300, n_max=4000):
+    """Systems of every periodicity (D = 3, 2, 1, 0 in turn), N log-uniform."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_sys):
+        n = int(10 ** rng.uniform(np.log10(n_min), np.log10(n_max)))
+        x = wl.uniform_positions(n, 1.0, seed * 1000 + i)
+        q = wl.uniform_charges(n, seed * 1000 + i)
+        out.append((x, q, (3, 2, 1, 0)[i % 4]))
+    specs = [(len(q), D, 1.0, 8.0 * (len(q) / 1e4) ** (1.0 / 3.0)) for x, q, D in out]
+    return out, specs, np.concatenate([s[0] for s in out]), np.concatenate([s[1] for s in out])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_fused_form_matches_per_system_calls(dtype):
+    """The multi-system form (one launch per stage over all systems) against one
+    plain se_force per system on the same plans.  FP64 gridding blocks are
+    fixed-point sums (exact in any order), the merge order and the per-particle
+    gathering are the same code, so FP64 potentials and forces are bitwise
+    equal, call after call; the energy sums per-CTA partials over the sorted
+    records, whose order inside a tile follows the atomic ranks of the binning,
+    so it agrees to rounding.  FP32 tiles of more than 512 particles add floats
+    atomically, so FP32 agrees within rounding."""
+    import paper_1712_04732_gb300 as se
+    sysl, specs, x, q = _mixed_systems(12, seed=5)
+    b = se.Batch(specs, eps_rel=1e-5, dtype=dtype, autotune=False, form="fused")
+    Ps = sorted({b.system_info(i)["P"] for i in range(len(specs))})
+    assert len(Ps) >= 2, Ps                          # more than one support class
+    xt = torch.tensor(x, dtype=dtype, device="cuda")
+    qt = torch.tensor(q, dtype=dtype, device="cuda")
+    F, phi, En = b.force(xt, qt)
+    F2, phi2, En2 = b.force(xt, qt)                 # graph replay
+    Fe, phie, Ene = b.force(xt, qt, each=True)
+    torch.cuda.synchronize()
+    assert b.form()[0] == "fused"
+    if dtype == torch.float64:
+        assert torch.equal(phi, phi2) and torch.equal(F, F2)
+        assert torch.equal(phi, phie) and torch.equal(F, Fe)
+        np.testing.assert_allclose(En.cpu().numpy(), Ene.cpu().numpy(), rtol=1e-13)
+        np.testing.assert_allclose(En2.cpu().numpy(), Ene.cpu().numpy(), rtol=1e-13)
+    else:
+        for a, c in ((phi, phi2), (phi, phie), (F, F2), (F, Fe)):
+            assert _rel(a.cpu().numpy(), c.cpu().numpy()) < 1e-6
+        np.testing.assert_allclose(En.cpu().numpy(), Ene.cpu().numpy(), rtol=1e-6)
+        np.testing.assert_allclose(En2.cpu().numpy(), Ene.cpu().numpy(), rtol=1e-6)
+    # every system against the discrete oracle of its own parameters
+    from oracle import se_discrete
+    off = 0
+    for i, (xs, qs, D) in enumerate(sysl):
+        n = len(qs)
+        info = b.system_info(i)
+        ref = se_discrete.SEOracle(D, 1.0, specs[i][3], info["M"], info["P"], "pkb", s_mt=info["s_mt"],
+                                   nl=info["n_l"])
+        pb, gb = ref.potential(xs, qs, grad=True)
+        tol = 1e-10 if dtype == torch.float64 else 2e-5
+        assert _rel(phi[off:off + n].double().cpu().numpy(), pb) < tol
+        assert _rel(F[off:off + n].double().cpu().numpy(), -qs[:, None] * gb) < 10 * tol
+        off += n
+    b.close()
+
+
+def test_fused_form_on_the_batched_workload():
+    """The 64-system workload of the benchmark (more than 1024 tiles, so the
+    tile-count scan runs several rounds): the multi-system graph against the
+    per-system graph and against one se_force per system."""
+    import paper_1712_04732_gb300 as se
+    sysl = wl.batch_systems(64, seed=1)
+    specs = [(len(q), D, 1.0, 8.0 * (len(q) / 1e4) ** (1.0 / 3.0)) for x, q, D in sysl]
+    xt = torch.tensor(np.concatenate([s[0] for s in sysl]), dtype=torch.float32, device="cuda")
+    qt = torch.tensor(np.concatenate([s[1] for s in sysl]), dtype=torch.float32, device="cuda")
+    bf = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False, form="fused")
+    bb = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False, form="branches")
+    F, phi, En = bf.force(xt, qt)
+    Fb, phib, Enb = bb.force(xt, qt)
+    Fe, phie, Ene = bf.force(xt, qt, each=True)
+    torch.cuda.synchronize()
+    assert sum(bf.system_info(i)["n_tiles"] for i in range(64)) > 1024
+    assert bf.form()[0] == "fused" and bb.form()[0] == "branches"
+    assert bf.form()[1] < bb.form()[1]               # fewer library launches per call
+    for a, c in ((phi, phib), (phi, phie), (F, Fb), (F, Fe)):
+        assert _rel(a.cpu().numpy(), c.cpu().numpy()) < 1e-6
+    np.testing.assert_allclose(En.cpu().numpy(), Ene.cpu().numpy(), rtol=1e-6)
+    bf.close()
+    bb.close()
+
+
+def test_batch_form_flags_exclude_each_other():
+    import paper_1712_04732_gb300 as se
+    from paper_1712_04732_gb300 import _native as nat
+    lib = nat.load()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 1)(1000)
+    D = (ctypes.c_int * 1)(3)
+    L = (ctypes.c_double * 1)(1.0)
+    xi = (ctypes.c_double * 1)(8.0)
+    code = lib.se_batch_create(ctypes.byref(h), 1, n, D, L, xi, None, 1e-5, nat.SE_WIN_PKB, nat.SE_F32,
+                               nat.SE_BATCH_FUSED | nat.SE_BATCH_BRANCHES)
+    assert nat.STATUS[code] == "SE_EINVAL"
+    assert not h.value
+    del se
