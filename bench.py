@@ -38,9 +38,9 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the tile kernels on this workload,
-# from one ncu --set full capture (profiles/free_0p_tile_kernels.md); reset to None whenever the
+# from one ncu --set full capture of this benchmark's FP32 step; reset to None whenever the
 # kernel changes
-NCU_TRAFFIC = {"spread": 660736, "gather": 1435648}
+NCU_TRAFFIC = {"spread": 667136, "gather": 1436672}
 
 
 def args_parse():
@@ -51,6 +51,8 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the 64-system batched form (profiling aid; prints its own JSON line)")
     return ap.parse_args()
 
 
@@ -195,12 +197,13 @@ def run_batch(se, wl, dev, flush, steps):
             b.force(x, q, out=out, each=each)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize(dev)
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record()
-            b.force(x, q, out=out, each=each)
-            e1.record()
-        torch.cuda.synchronize(dev)
+        with torch.cuda.nvtx.range(f"batch_{name}"):          # lets a profiler select these launches
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record()
+                b.force(x, q, out=out, each=each)
+                e1.record()
+            torch.cuda.synchronize(dev)
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
         res[name] = {"ms_per_step": ms, "value": ntot / (ms * 1e-3), "unit": "particles/s"}
     Ms = [b.system_info(i)["M"] for i in range(len(specs))]
@@ -301,6 +304,11 @@ def run_ours(a):
     x_np, q_np, spec = wl.make(WORKLOAD, seed=rank + 1)
     N = spec["N"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if a.batch_only:
+        res = run_batch(se, wl, dev, flush, a.steps)
+        if rank == 0:
+            print(json.dumps({"batch_form": res}), flush=True)
+        return
 
     def make_form(dtype, force_method=1):
         plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"], dtype=dtype, device=dev,
