@@ -51,8 +51,9 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-only", action="store_true",
-                    help="time only the 64-system batched form (profiling aid; prints its own JSON line)")
+    ap.add_argument("--only", choices=["batch", "slab_2p", "wire_1p"], default=None,
+                    help="time only the batched form or one of the larger workloads (profiling aid; "
+                         "prints its own JSON line)")
     return ap.parse_args()
 
 
@@ -234,13 +235,13 @@ def run_batch(se, wl, dev, flush, steps):
     return res
 
 
-def run_other_workloads(se, wl, dev, flush, steps):
+def run_other_workloads(se, wl, dev, flush, steps, names=("slab_2p", "wire_1p")):
     """The FP32 step on the larger workloads (slab 1e5 and wire 1.2e6 particles):
     particles/s from graph replays after an L2 flush, and the gridding and
     gathering stages' algorithmic FLOP rate against the derived FP32 peak."""
     import torch
     out = {}
-    for name in ("slab_2p", "wire_1p"):
+    for name in names:
         x_np, q_np, spec = wl.make(name, seed=1)
         n = len(q_np)
         plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"],
@@ -304,10 +305,15 @@ def run_ours(a):
     x_np, q_np, spec = wl.make(WORKLOAD, seed=rank + 1)
     N = spec["N"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    if a.batch_only:
+    if a.only == "batch":
         res = run_batch(se, wl, dev, flush, a.steps)
         if rank == 0:
             print(json.dumps({"batch_form": res}), flush=True)
+        return
+    if a.only is not None:
+        res = run_other_workloads(se, wl, dev, flush, a.steps, names=(a.only,))
+        if rank == 0:
+            print(json.dumps({"other_workloads": res}), flush=True)
         return
 
     def make_form(dtype, force_method=1):

@@ -68,7 +68,12 @@ typedef enum {
 #define SE_SYNC_CHECK    4u  /* synchronise at the end and report device-side input errors */
 #define SE_HOST_IO       8u  /* x, q and the outputs are HOST pointers; the call copies
                                 them to and from the device on the plan's stream and
-                                returns after the results are in host memory */
+                                returns after the results are in host memory.  With
+                                page-locked buffers (and without SE_CHECK_NEUTRAL or
+                                profiling) the call -- copies included -- is captured
+                                into a CUDA graph the first time and replayed while the
+                                same call (N, pointers, flags) repeats; keep such
+                                buffers allocated while the plan may replay them */
 
 /* Optional overrides of the paper's parameter rules (Sec. 6).  A field left at
  * its "unset" value (given in brackets) takes the paper's default. */

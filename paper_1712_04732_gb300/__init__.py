@@ -199,11 +199,18 @@ class Plan:
         return phi, F
 
     def force_host(self, x, q, F, phi=None, energy=None, add_self=False):
-        """``se_force`` with SE_HOST_IO on pinned host tensors (copies inside the call)."""
+        """``se_force`` with SE_HOST_IO on host tensors (copies inside the call;
+        with page-locked tensors a repeated call replays a captured graph)."""
         self._sync_stream()
         flags = nat.SE_HOST_IO | (nat.SE_ADD_SELF if add_self else 0)
         nat.check(self._lib.se_force(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(F), _ptr(phi), _ptr(energy),
                                      flags))
+
+    def potential_host(self, x, q, phi, add_self=False):
+        """``se_potential`` with SE_HOST_IO on host tensors."""
+        self._sync_stream()
+        flags = nat.SE_HOST_IO | (nat.SE_ADD_SELF if add_self else 0)
+        nat.check(self._lib.se_potential(self._h, x.shape[0], _ptr(x), _ptr(q), _ptr(phi), flags))
 
 
 class Batch:

@@ -50,6 +50,9 @@ static int even_up(double v)
     return n + (n & 1);
 }
 
+// Internal call flag: the call is being captured into a graph (no synchronisation).
+constexpr unsigned kInCapture = 1u << 30;
+
 // Pipeline of Alg. 4 for one precision.  HOST_IO stages through the plan's
 // io buffer; the neutrality check and the device-error check synchronise.
 template <typename T>
@@ -115,8 +118,86 @@ static se_status run(se_plan_s *p, int64_t N, const void *x, const void *q, void
             return cuda_fail(e, "copy F");
         if (energy && (e = cudaMemcpyAsync(energy, den, sizeof(double), cudaMemcpyDeviceToHost, p->stream)) != cudaSuccess)
             return cuda_fail(e, "copy energy");
+        if (flags & kInCapture) return SE_OK;
         if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "sync");
     }
+    if (flags & SE_SYNC_CHECK) return se_plan_check(p);
+    return SE_OK;
+}
+
+static void io_graph_release(se_plan_s *p)
+{
+    if (p->io_exec) cudaGraphExecDestroy(p->io_exec);
+    p->io_exec = nullptr;
+    p->io_key = se_plan_s::IoKey{};
+}
+
+// SE_HOST_IO calls: the whole call (copies of x and q in, the pipeline, copies
+// of the results out) is captured into a CUDA graph on an internal stream the
+// first time and replayed on the plan's stream while the same call (N,
+// pointers, flags) repeats, then the plan's stream is synchronised, so the
+// results are in host memory on return exactly as with eager launches.  Calls
+// that synchronise midway (SE_CHECK_NEUTRAL), time their stages, or pass
+// pageable (not page-locked) host buffers run eagerly.
+static bool page_locked(const void *ptr)
+{
+    if (!ptr) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+template <typename T>
+static se_status run_host(se_plan_s *p, int64_t N, const void *x, const void *q, void *phi, void *F, double *energy,
+                          unsigned flags, bool grad)
+{
+    if ((flags & SE_CHECK_NEUTRAL) || p->prof || !page_locked(x) || !page_locked(q) || !page_locked(phi) ||
+        !page_locked(F) || !page_locked(energy))
+        return run<T>(p, N, x, q, phi, F, energy, flags, grad);
+    se_status st;
+    if ((st = plan_reserve(p, N)) != SE_OK) return st;
+    if ((st = plan_io_reserve(p, N)) != SE_OK) return st;
+    se_plan_s::IoKey k;
+    k.N = N; k.x = x; k.q = q; k.phi = phi; k.F = F; k.energy = energy;
+    k.flags = flags & ~SE_SYNC_CHECK; k.grad = grad; k.cap = p->cap; k.io_buf = p->io_buf;
+    cudaError_t e;
+    if (!p->io_exec || !(k == p->io_key)) {
+        io_graph_release(p);
+        if (!p->io_cap && (e = cudaStreamCreateWithFlags(&p->io_cap, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "host-I/O capture stream");
+        cudaStream_t user = p->stream;
+        // the capture stream starts after the work already queued on the plan's stream
+        if ((e = cudaStreamSynchronize(user)) != cudaSuccess) return cuda_fail(e, "sync");
+        p->stream = p->io_cap;
+        if ((st = plan_set_fft_stream(p)) != SE_OK) { p->stream = user; plan_set_fft_stream(p); return st; }
+        if ((e = cudaStreamBeginCapture(p->io_cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            p->stream = user;
+            plan_set_fft_stream(p);
+            return cuda_fail(e, "begin capture");
+        }
+        st = run<T>(p, N, x, q, phi, F, energy, (flags & ~SE_SYNC_CHECK) | kInCapture, grad);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->io_cap, &g);
+        p->stream = user;
+        se_status st2 = plan_set_fft_stream(p);
+        if (st != SE_OK || e != cudaSuccess || st2 != SE_OK) {
+            if (g) cudaGraphDestroy(g);
+            if (st != SE_OK) return st;
+            return e != cudaSuccess ? cuda_fail(e, "end capture") : st2;
+        }
+        e = cudaGraphInstantiate(&p->io_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->io_exec = nullptr;
+            return cuda_fail(e, "graph instantiate");
+        }
+        p->io_key = k;
+    }
+    if ((e = cudaGraphLaunch(p->io_exec, p->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return cuda_fail(e, "sync");
     if (flags & SE_SYNC_CHECK) return se_plan_check(p);
     return SE_OK;
 }
@@ -300,6 +381,8 @@ se_status se_plan_destroy(se_plan_t p)
     if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
     for (int i = 0; i <= SE_N_STAGES; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    io_graph_release(p);
+    if (p->io_cap) cudaStreamDestroy(p->io_cap);
     plan_release(p);
     delete p;
     return SE_OK;
@@ -374,6 +457,9 @@ se_status se_potential(se_plan_t p, int64_t N, const void *x, const void *q, voi
     if (st != SE_OK) return st;
     if (N > 0 && !phi) return fail(SE_EINVAL, "phi is NULL");
     if (N == 0) return SE_OK;
+    if (flags & SE_HOST_IO)
+        return p->dtype == SE_F32 ? run_host<float>(p, N, x, q, phi, nullptr, nullptr, flags, false)
+                                  : run_host<double>(p, N, x, q, phi, nullptr, nullptr, flags, false);
     return p->dtype == SE_F32 ? run<float>(p, N, x, q, phi, nullptr, nullptr, flags, false)
                               : run<double>(p, N, x, q, phi, nullptr, nullptr, flags, false);
 }
@@ -394,6 +480,9 @@ se_status se_force(se_plan_t p, int64_t N, const void *x, const void *q, void *F
         }
         return SE_OK;
     }
+    if (flags & SE_HOST_IO)
+        return p->dtype == SE_F32 ? run_host<float>(p, N, x, q, phi, F, energy, flags, true)
+                                  : run_host<double>(p, N, x, q, phi, F, energy, flags, true);
     return p->dtype == SE_F32 ? run<float>(p, N, x, q, phi, F, energy, flags, true)
                               : run<double>(p, N, x, q, phi, F, energy, flags, true);
 }

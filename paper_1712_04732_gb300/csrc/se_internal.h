@@ -169,6 +169,23 @@ struct se_plan_s {
     void *spec_d = nullptr, *U_d = nullptr, *Z_d = nullptr, *grid_d = nullptr;
     se::IkBox<float> ib_spec_f{}, ib_U_f{}, ib_Z_f{};
     se::IkBox<double> ib_spec_d{}, ib_U_d{}, ib_Z_d{};
+    // SE_HOST_IO calls replayed from a captured graph (se_api.cu): the call that
+    // was captured (sizes, pointers, flags, and the workspace it used)
+    struct IoKey {
+        int64_t N = -1;
+        const void *x = nullptr, *q = nullptr, *phi = nullptr, *F = nullptr, *energy = nullptr;
+        unsigned flags = 0;
+        bool grad = false;
+        int64_t cap = 0;
+        void *io_buf = nullptr;
+        bool operator==(const IoKey &o) const
+        {
+            return N == o.N && x == o.x && q == o.q && phi == o.phi && F == o.F && energy == o.energy &&
+                   flags == o.flags && grad == o.grad && cap == o.cap && io_buf == o.io_buf;
+        }
+    } io_key;
+    cudaStream_t io_cap = nullptr;       // internal stream the host-I/O graph is captured on
+    cudaGraphExec_t io_exec = nullptr;
     // D = 0 column stage (used when 2 M~ is a power of two in [16, 1024])
     bool zcol = false;
     bool zcol_allowed = true;            // se_opts.fft_mode != 1

@@ -80,13 +80,18 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
     if (off[nsys] > std::numeric_limits<int>::max()) return fail(SE_EINVAL, "batch: more than 2^31 - 1 particles");
     m->nsys = nsys;
     m->ntot = off[nsys];
-    // classes of systems with the same window (support, degree, kind, shape): one
-    // gridding and one gathering launch each; caller's order inside a class
-    std::map<std::tuple<int, int, int, double>, std::vector<int>> by_win;
+    // classes of systems with the same window (support, degree, kind, shape) and
+    // the same gridding residency (CTAs per SM that the shared-memory block
+    // allows, so that small blocks are not launched with the largest one's
+    // reservation): one gridding and one gathering launch each; caller's order
+    // inside a class
+    std::map<std::tuple<int, int, int, double, int>, std::vector<int>> by_win;
     for (int i = 0; i < nsys; ++i) {
         const se_plan_s *p = plans[i];
         if (p->dtype != (sizeof(T) == 4 ? SE_F32 : SE_F64)) return fail(SE_EINVAL, "batch: mixed precisions");
-        by_win[std::make_tuple(p->P, p->nu, p->window, p->shape)].push_back(i);
+        const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
+        const int resident = int(std::min<size_t>(8, (228 * 1024) / (sm + 1024)));
+        by_win[std::make_tuple(p->P, p->nu, p->window, p->shape, -resident)].push_back(i);
     }
     std::vector<SysDesc<T>> d(nsys);
     std::vector<int> tile_sys, cta_sys;

@@ -227,6 +227,46 @@ def test_host_io_path_equals_device_path():
     assert eh.item() == pytest.approx(En, rel=1e-6)
 
 
+def test_host_io_graph_replay_follows_new_contents_and_buffers():
+    """Repeated SE_HOST_IO calls on the same page-locked buffers replay a captured
+    graph: new contents written into the buffers between calls must be read
+    again; new buffers, pageable buffers and a potential-only call (other
+    flags) must give the same results as the device path."""
+    se = _se()
+    N = 1500
+    plan = se.Plan(0, 1.0, 6.0, 24, 8, "pkb", dtype=torch.float32)
+    xh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    qh = torch.empty(N, dtype=torch.float32).pin_memory()
+    Fh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    ph = torch.empty(N, dtype=torch.float32).pin_memory()
+    eh = torch.empty((), dtype=torch.float64).pin_memory()
+    for seed in (31, 32, 33):                       # same buffers, new contents
+        x = wl.uniform_positions(N, 1.0, seed)
+        q = wl.uniform_charges(N, seed)
+        xh.copy_(torch.tensor(x, dtype=torch.float32))
+        qh.copy_(torch.tensor(q, dtype=torch.float32))
+        plan.force_host(xh, qh, Fh, ph, eh)
+        F, phi, En = _run(plan, x, q)
+        assert _rel(ph.double().numpy(), phi) < 1e-6
+        assert _rel(Fh.double().numpy(), F) < 1e-6
+        assert eh.item() == pytest.approx(En, rel=1e-6)
+    # other buffers (pinned and pageable), then the potential alone
+    x = wl.uniform_positions(N, 1.0, 34)
+    q = wl.uniform_charges(N, 34)
+    F, phi, En = _run(plan, x, q)
+    for pin in (True, False):
+        mk = (lambda t: t.pin_memory()) if pin else (lambda t: t)
+        xh2, qh2 = mk(torch.tensor(x, dtype=torch.float32)), mk(torch.tensor(q, dtype=torch.float32))
+        Fh2, ph2 = mk(torch.empty((N, 3), dtype=torch.float32)), mk(torch.empty(N, dtype=torch.float32))
+        eh2 = mk(torch.empty((), dtype=torch.float64))
+        plan.force_host(xh2, qh2, Fh2, ph2, eh2)
+        assert _rel(ph2.double().numpy(), phi) < 1e-6 and _rel(Fh2.double().numpy(), F) < 1e-6
+        assert eh2.item() == pytest.approx(En, rel=1e-6)
+        pp = mk(torch.empty(N, dtype=torch.float32))
+        plan.potential_host(xh2, qh2, pp)
+        assert _rel(pp.double().numpy(), phi) < 1e-6
+
+
 def test_vjp_matches_oracle_and_linearity():
     """g_q = A g and g_x = g grad(A q) + q grad(A g) (operator symmetry)."""
     se = _se()
