@@ -108,14 +108,17 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
     prof_mark(p, 2);
     const int t01 = p->tg.T[0] * p->tg.T[1];
     dim3 mb(p->tg.T[0], p->tg.T[1], std::max(1, std::min(p->tg.T[2], 256 / t01)));
-    bool two = true;                                  // at most two tiles overlap a point per axis
-    for (int a = 0; a < 3; ++a) two = two && (p->tg.B[a] - 1) / p->tg.T[a] + 1 <= 2;
+    int J = 1;                                        // most tiles overlapping a point along an axis
+    for (int a = 0; a < 3; ++a) J = std::max(J, (p->tg.B[a] - 1) / p->tg.T[a] + 1);
     {
-        cudaError_t e = two ? launch_pdl(k_merge<T, 2>, dim3(nt), mb, 0, p->stream, 1, p->tg, (const int *)p->tile_off,
-                                         reinterpret_cast<const T *>(scratch), reinterpret_cast<T *>(dst), p->gin)
-                            : launch_pdl(k_merge<T, kMergeJ>, dim3(nt), mb, 0, p->stream, 1, p->tg,
-                                         (const int *)p->tile_off, reinterpret_cast<const T *>(scratch),
-                                         reinterpret_cast<T *>(dst), p->gin);
+        const int *off = p->tile_off;
+        const T *src = reinterpret_cast<const T *>(scratch);
+        T *out = reinterpret_cast<T *>(dst);
+        cudaError_t e;
+        if (J <= 2) e = launch_pdl(k_merge<T, 2>, dim3(nt), mb, 0, p->stream, 1, p->tg, off, src, out, p->gin);
+        else if (J == 3) e = launch_pdl(k_merge<T, 3>, dim3(nt), mb, 0, p->stream, 1, p->tg, off, src, out, p->gin);
+        else if (J == 4) e = launch_pdl(k_merge<T, 4>, dim3(nt), mb, 0, p->stream, 1, p->tg, off, src, out, p->gin);
+        else e = launch_pdl(k_merge<T, kMergeJ>, dim3(nt), mb, 0, p->stream, 1, p->tg, off, src, out, p->gin);
         if (e != cudaSuccess) return cuda_fail(e, "merge launch");
     }
     SE_LAUNCH_CHECK("merge");
