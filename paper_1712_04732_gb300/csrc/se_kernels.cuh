@@ -498,17 +498,24 @@ __device__ __forceinline__ void spread_cl_tile(const TileGeom &tg, int tile, int
     }
     __syncthreads();
     // s = 2^e, e the largest with s (1 + 1e-6) sum|q| <= kFixMax (the PKB fit
-    // stays within 1e-6 of the window's maximum 1)
-    T bound = T(0);
-    for (int i = 0; i < nw; ++i) bound += qsum[i];
-    const bool fix = end - beg <= Fix<T>::kFixTile;           // the same in every CTA of the cluster
-    int e2 = 0;
-    if (bound > T(0)) {
-        frexp(double(Fix<T>::kFixMax) / ((1.0 + 1e-6) * double(bound)), &e2);
-        e2 -= 1;
+    // stays within 1e-6 of the window's maximum 1).  One thread computes it
+    // (FP64 arithmetic is slow on this GPU) and shares it through shared memory.
+    __shared__ T sscale[2];
+    if (threadIdx.x == 0) {
+        T bound = T(0);
+        for (int i = 0; i < nw; ++i) bound += qsum[i];
+        int e2 = 0;
+        if (bound > T(0)) {
+            frexp(double(Fix<T>::kFixMax) / ((1.0 + 1e-6) * double(bound)), &e2);
+            e2 -= 1;
+        }
+        e2 = max(-Fix<T>::kMaxExp, min(Fix<T>::kMaxExp, e2));   // s and 1/s representable in T
+        sscale[0] = T(ldexp(1.0, e2));
+        sscale[1] = T(ldexp(1.0, -e2));
     }
-    e2 = max(-Fix<T>::kMaxExp, min(Fix<T>::kMaxExp, e2));       // s and 1/s representable in T
-    const T scale = T(ldexp(1.0, e2)), inv_scale = T(ldexp(1.0, -e2));
+    const bool fix = end - beg <= Fix<T>::kFixTile;           // the same in every CTA of the cluster
+    __syncthreads();
+    const T scale = sscale[0], inv_scale = sscale[1];
 
     // The warp's particles are p0, p0 + stride, ...; lane i loads the i-th of
     // the next 32 of them, so one round of global loads serves 32 particles,
