@@ -419,12 +419,24 @@ k_spread(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::type 
 // values for charges of both signs, so FP32 tiles with more than kFixTile
 // particles keep float atomics (their rounding then stays below float's).
 template <typename T> struct Fix;
+// scale_exp(b) is the largest e with 2^e (1 + 1e-6) b <= kFixMax (b > 0).
 template <> struct Fix<float> {
     using type = int;
     static constexpr double kFixMax = 2147418112.0;                 // 2^31 - 2^16
     static constexpr int kMaxExp = 120;
     static constexpr int kFixTile = 512;
     __device__ static int to(float v) { return __float2int_rn(v); }
+    // In float arithmetic only: with b = m 2^E, m in [0.5, 1), e = 31 - E when
+    // m <= kFixMax / (1 + 1e-6) / 2^31 (0x3f7ffdef is the largest float below it),
+    // else 30 - E -- the exponent of the FP64 quotient kFixMax / ((1 + 1e-6) b),
+    // less one, for every float b (checked over all float mantissas).
+    __device__ static int scale_exp(float b)
+    {
+        int E;
+        const float m = frexpf(b, &E);
+        return (m <= __int_as_float(0x3f7ffdef) ? 31 : 30) - E;
+    }
+    __device__ static float pow2(int e) { return ldexpf(1.0f, e); }
 };
 template <> struct Fix<double> {
     using type = long long;
@@ -432,6 +444,13 @@ template <> struct Fix<double> {
     static constexpr int kMaxExp = 1000;
     static constexpr int kFixTile = 1 << 30;
     __device__ static long long to(double v) { return __double2ll_rn(v); }
+    __device__ static int scale_exp(double b)
+    {
+        int e2;
+        frexp(kFixMax / ((1.0 + 1e-6) * b), &e2);
+        return e2 - 1;
+    }
+    __device__ static double pow2(int e) { return ldexp(1.0, e); }
 };
 
 // Eq. (gridding) with shared-memory atomics, one tile per thread-block cluster
@@ -498,20 +517,17 @@ __device__ __forceinline__ void spread_cl_tile(const TileGeom &tg, int tile, int
     }
     __syncthreads();
     // s = 2^e, e the largest with s (1 + 1e-6) sum|q| <= kFixMax (the PKB fit
-    // stays within 1e-6 of the window's maximum 1).  One thread computes it
-    // (FP64 arithmetic is slow on this GPU) and shares it through shared memory.
+    // stays within 1e-6 of the window's maximum 1).  One thread computes it and
+    // shares it through shared memory (for FP32 without FP64 arithmetic, which
+    // is slow on this GPU).
     __shared__ T sscale[2];
     if (threadIdx.x == 0) {
         T bound = T(0);
         for (int i = 0; i < nw; ++i) bound += qsum[i];
-        int e2 = 0;
-        if (bound > T(0)) {
-            frexp(double(Fix<T>::kFixMax) / ((1.0 + 1e-6) * double(bound)), &e2);
-            e2 -= 1;
-        }
+        int e2 = bound > T(0) ? Fix<T>::scale_exp(bound) : 0;
         e2 = max(-Fix<T>::kMaxExp, min(Fix<T>::kMaxExp, e2));   // s and 1/s representable in T
-        sscale[0] = T(ldexp(1.0, e2));
-        sscale[1] = T(ldexp(1.0, -e2));
+        sscale[0] = Fix<T>::pow2(e2);
+        sscale[1] = Fix<T>::pow2(-e2);
     }
     const bool fix = end - beg <= Fix<T>::kFixTile;           // the same in every CTA of the cluster
     __syncthreads();
