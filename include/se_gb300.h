@@ -260,8 +260,8 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
  * Unless SE_BATCH_NO_AUTOTUNE is given, the first se_batch_force call times the
  * gridding tile (4, 8, 16) and kernel variants per system on the real inputs,
  * then the forms as captured graphs (the multi-system one with 1, 2, 4 or 8
- * CTAs per gridding tile, also with tiles of edge 4 for FP32 systems of more
- * than 512 particles per tile), and keeps the fastest; without autotuning the
+ * CTAs per gridding tile, also with tiles of edge 4 for systems of more than
+ * 512 particles per tile), and keeps the fastest; without autotuning the
  * form is the multi-system one unless SE_BATCH_BRANCHES is given.
  * Arrays x [sum N][3], q [sum N], F [sum N][3], phi [sum N] (may be NULL) are
  * concatenated in system order (device pointers); energy [nsys] (device, may be

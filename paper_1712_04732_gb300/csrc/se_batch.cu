@@ -323,15 +323,14 @@ float time_graph(se_batch_s *b, cudaEvent_t e0, cudaEvent_t e1)
 // captured graph on the real inputs, the fastest kept.  Candidates: the
 // per-system branches, and the multi-system pipeline with the rule's, 1, 2, 4
 // or 8 CTAs per gridding tile, on the current plans and on plans whose dense
-// systems (FP32, more than 512 particles per tile on average) take a gridding
-// tile of edge 4 (smaller tiles keep the integer shared-memory atomics, which
-// run about three times faster than float ones).
+// systems (more than 512 particles per tile on average) take a gridding tile of
+// edge 4 (more, lighter tiles: more CTAs share a dense system's updates).
 se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
 {
     struct Cand { int form, cl; bool dense4; };
     std::vector<se_plan_t> alt(b->nsys, nullptr);
     bool have_alt = false;
-    if (b->force_form != kFormBranches && b->dtype == SE_F32)
+    if (b->force_form != kFormBranches)
         for (int i = 0; i < b->nsys; ++i) {
             const se_plan_s *p = b->plans[i];
             const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
