@@ -236,16 +236,18 @@ def run_batch(se, wl, dev, flush, steps):
 
 
 def run_other_workloads(se, wl, dev, flush, steps, names=("slab_2p", "wire_1p")):
-    """The FP32 step on the larger workloads (slab 1e5 and wire 1.2e6 particles):
-    particles/s from graph replays after an L2 flush, and the gridding and
-    gathering stages' algorithmic FLOP rate against the derived FP32 peak."""
+    """The FP32 step on the larger workloads (slab 1e5 and wire 1.2e6 particles),
+    with the free-direction transform lengths rounded up to 2-3-5-7-smooth sizes
+    (plan option fft_sizes): particles/s from graph replays after an L2 flush,
+    and the gridding and gathering stages' algorithmic FLOP rate against the
+    derived FP32 peak."""
     import torch
     out = {}
     for name in names:
         x_np, q_np, spec = wl.make(name, seed=1)
         n = len(q_np)
         plan = se.Plan(spec["D"], spec["L"], spec["xi"], spec["M"], spec["P"], spec["window"],
-                       dtype=torch.float32, device=dev, lam=spec.get("lam"))
+                       dtype=torch.float32, device=dev, lam=spec.get("lam"), fft_sizes=1)
         plan.reserve(n)
         x = torch.tensor(x_np, dtype=torch.float32, device=dev)
         q = torch.tensor(q_np, dtype=torch.float32, device=dev)
@@ -281,8 +283,12 @@ def run_other_workloads(se, wl, dev, flush, steps, names=("slab_2p", "wire_1p"))
         for k in ("spread", "gather"):
             tf = 2.0 * cnt[k] * n / (st[k] * 1e-3) / 1e12
             frac[k] = {"tflops": tf, "frac_of_fp32_peak": tf / FP32_PEAK_TFLOPS}
+        inf = plan.info()
         out[name] = {"particles": n, "ms_per_step": ms, "value": n / (ms * 1e-3), "unit": "particles/s",
-                     "stage_ms": st, "alu": frac}
+                     "stage_ms": st, "alu": frac,
+                     "transform_lengths": {"Mt": list(inf["Mt_v"]), "s0Mt": list(inf["s0_mt_v"]),
+                                           "sMt": list(inf["s_mt_v"]),
+                                           "rule": "free-direction lengths rounded up to 2-3-5-7-smooth sizes"}}
         plan.close()
     return out
 

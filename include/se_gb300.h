@@ -102,6 +102,10 @@ typedef struct {
     int    fft_mode;    /* [<= 0] D = 0 transform: the z-direction FFT, scaling and inverse
                            FFT fused into one kernel per column when 2 M~ is a power of two
                            from 16 to 1024 (cuFFT otherwise); 1 cuFFT for every stage */
+    int    fft_sizes;   /* [<= 0] free-direction transform lengths: the smallest the rules of
+                           Sec. 3.3 and Sec. 6 allow; 1 each of M~_i, s0 M~_i and s M~_i rounded
+                           up to the next even length whose prime factors are 2, 3, 5 and 7
+                           (more extension and upsampling, never less; faster FFTs) */
 } se_opts;
 
 /* Derived parameters of a plan (read-only report). */

@@ -40,13 +40,14 @@ class Plan:
     Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
     shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants),
     force_method (1: gradient of the window, 2: i k in the scaling; Sec. 7.2),
-    fft_mode (1: cuFFT for every transform stage).
+    fft_mode (1: cuFFT for every transform stage), fft_sizes (1: free-direction
+    transform lengths rounded up to 2-3-5-7-smooth sizes).
     """
 
     def __init__(self, D: int, L, xi: float, M: int, P: int, window: str = "pkb",
                  dtype=torch.float32, device=None, lam=None, s0=None, s_mt=None, n_l=None, nu=None,
                  shape=None, aft_eps=None, tile=None, spread_mode=None, gather_mode=None, split=None,
-                 force_method=None, fft_mode=None):
+                 force_method=None, fft_mode=None, fft_sizes=None):
         self._lib = nat.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if self.device.type != "cuda":
@@ -73,6 +74,7 @@ class Plan:
         if split is not None: o.split = split
         if force_method is not None: o.force_method = force_method
         if fft_mode is not None: o.fft_mode = fft_mode
+        if fft_sizes is not None: o.fft_sizes = fft_sizes
         box = (ctypes.c_double * 3)(*self.box)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

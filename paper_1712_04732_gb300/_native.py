@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("n_l", ctypes.c_int), ("nu", ctypes.c_int), ("shape", ctypes.c_double),
                 ("aft_eps", ctypes.c_double), ("tile", ctypes.c_int), ("spread_mode", ctypes.c_int),
                 ("gather_mode", ctypes.c_int), ("split", ctypes.c_int),
-                ("force_method", ctypes.c_int), ("fft_mode", ctypes.c_int)]
+                ("force_method", ctypes.c_int), ("fft_mode", ctypes.c_int), ("fft_sizes", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

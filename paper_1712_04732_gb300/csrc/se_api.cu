@@ -50,6 +50,17 @@ static int even_up(double v)
     return n + (n & 1);
 }
 
+// Smallest even length >= n whose prime factors are 2, 3, 5 and 7.
+static int smooth_even_up(int n)
+{
+    for (int m = n + (n & 1);; m += 2) {
+        int r = m;
+        for (int f : {2, 3, 5, 7})
+            while (r % f == 0) r /= f;
+        if (r == 1) return m;
+    }
+}
+
 // Internal call flag: the call is being captured into a graph (no synchronisation).
 constexpr unsigned kInCapture = 1u << 30;
 
@@ -258,6 +269,7 @@ void se_opts_default(se_opts *o)
     o->split = 0;
     o->force_method = 0;
     o->fft_mode = 0;
+    o->fft_sizes = 0;
 }
 
 se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, int M, int P, se_window w,
@@ -308,6 +320,8 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     if (o.force_method > 2) { delete p; return fail(SE_EINVAL, "force_method must be 1 or 2 (Sec. 7.2)"); }
     p->force_method = o.force_method == 2 ? 2 : 1;
     if (o.fft_mode > 1) { delete p; return fail(SE_EINVAL, "fft_mode must be 0 or 1"); }
+    if (o.fft_sizes > 1) { delete p; return fail(SE_EINVAL, "fft_sizes must be 0 or 1"); }
+    const bool smooth = o.fft_sizes == 1;
     p->zcol_allowed = o.fft_mode != 1;
     // Sec. 6: shape parameters and PKB degree
     p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
@@ -328,6 +342,7 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
         double R2 = 0.0;
         for (int a = D; a < 3; ++a) {
             p->Mtv[a] = 2 * int(std::ceil((p->Mv[a] + lam * P) / 2.0 - 1e-12));
+            if (smooth) p->Mtv[a] = smooth_even_up(p->Mtv[a]);
             p->Ltv[a] = p->h * p->Mtv[a];
             R2 += p->Ltv[a] * p->Ltv[a];
         }
@@ -340,7 +355,10 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
         p->s0 = o.s0 > 0 ? o.s0 : s0d[D];
         if (p->s0 < 2.0) { delete p; return fail(SE_EINVAL, "s0 must be >= 2"); }
         // the oversampled free grid must hold the truncated kernel: s0_i >= 1 + R / L~_i
-        for (int a = D; a < 3; ++a) p->s0v[a] = even_up(std::max(p->s0, 1.0 + p->R / p->Ltv[a]) * p->Mtv[a]);
+        for (int a = D; a < 3; ++a) {
+            p->s0v[a] = even_up(std::max(p->s0, 1.0 + p->R / p->Ltv[a]) * p->Mtv[a]);
+            if (smooth) p->s0v[a] = smooth_even_up(p->s0v[a]);
+        }
         p->s0Mt = p->s0v[D];
         if (D != 0) {
             const double lg = std::log(1.0 / (2.0 * p->aft_eps)) / (2.0 * M_PI);
@@ -349,6 +367,7 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
             for (int a = D; a < 3; ++a) {
                 int sm = o.s_mt > 0 ? o.s_mt : even_up(p->Mv[a] * (1.0 + lg));
                 if (sm < p->Mtv[a]) sm = p->Mtv[a];
+                if (smooth && o.s_mt <= 0) sm = smooth_even_up(sm);
                 if (sm % 2) { delete p; return fail(SE_EINVAL, "s M~ must be even"); }
                 p->sv[a] = sm;
                 const int nl = std::max(0, int(std::ceil(double(p->Mv[a]) / (p->Mtv[a] - p->Mv[a]) * lg - 1.0 - 1e-12)));

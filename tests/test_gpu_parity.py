@@ -210,6 +210,40 @@ def test_self_term_flag():
     assert np.allclose(p1 - p0, -2 * 6.0 / np.sqrt(np.pi) * q, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("D,M,P", [(2, 24, 8), (1, 24, 8), (0, 36, 6)])
+def test_fft_friendly_sizes_match_discrete_oracle(D, M, P):
+    """fft_sizes = 1 rounds the free-direction lengths M~, s0 M~ and s M~ up to
+    2-3-5-7-smooth sizes (here M~ = 44 -> 48): the discrete oracle given the
+    same extension and upsampling (lambda = (M~ - M) / P, s0 = s0 M~ / M~, the
+    same s M~ and n_l) agrees to FP64 rounding, and the result stays within the
+    method's error of the default plan's."""
+    se = _se()
+    N = 500
+    x = wl.uniform_positions(N, 1.0, 41)
+    q = wl.uniform_charges(N, 41)
+    plan = se.Plan(D, 1.0, 6.0, M, P, "pkb", dtype=torch.float64, fft_sizes=1)
+    base = se.Plan(D, 1.0, 6.0, M, P, "pkb", dtype=torch.float64)
+    info, binfo = plan.info(), base.info()
+    assert info["Mt"] == 48 and binfo["Mt"] == 44
+    for n in (info["Mt"], info["s0_mt"], info["s_mt"]):
+        if n == 0:                                  # no set-I transform (D = 0)
+            continue
+        r = n
+        for f in (2, 3, 5, 7):
+            while r % f == 0:
+                r //= f
+        assert r == 1 and n % 2 == 0
+    F, phi, _ = _run(plan, x, q)
+    o = S.SEOracle(D, 1.0, 6.0, M, P, "pkb", lam=(info["Mt"] - M) / P, s0=info["s0_mt"] / info["Mt"],
+                   s_mt=info["s_mt"], nl=info["n_l"])
+    assert o.Mt == info["Mt"] and o.g["s0Mt"] == info["s0_mt"]
+    pb, gb = o.potential(x, q, grad=True)
+    assert _rel(phi, pb) < 1e-11
+    assert _rel(F, -q[:, None] * gb) < 1e-10
+    F0, phi0, _ = _run(base, x, q)
+    assert _rel(phi, phi0) < 1e-4
+
+
 def test_host_io_path_equals_device_path():
     se = _se()
     x = wl.uniform_positions(1000, 1.0, 12)
