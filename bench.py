@@ -40,7 +40,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the tile kernels on this workload,
 # from one ncu --set full capture of this benchmark's FP32 step; reset to None whenever the
 # kernel changes
-NCU_TRAFFIC = {"spread": 664064, "gather": 1436160}
+NCU_TRAFFIC = {"spread": 664576, "gather": 1436160}
 
 
 def args_parse():
