@@ -128,6 +128,26 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer
+    and part codes), else the platform's processor string."""
+    import platform
+    try:
+        info = {}
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+        if info.get("model name"):
+            return info["model name"]
+        if info.get("CPU implementer"):
+            return f"implementer {info['CPU implementer']} part {info.get('CPU part', '?')} ({platform.machine()})"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_sample(x, q, targets, L, xi):
     """The FP64 oracle (direct free-space Ewald sum with forces) on the given targets."""
     from oracle import ewald
@@ -159,6 +179,7 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(spec),
             "cpu_baseline": {"value": v, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(),
                              "sample": f"phi+F at {ns} of {spec['N']} targets (all sources) per step, direct FP64 sum"},
             "e2e": {"value": v, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -470,7 +491,7 @@ def run_ours(a):
         pa, ga = cpu_oracle_sample(x_np, q_np, idx, spec["L"], spec["xi"])
         tc = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": len(idx) / tc, "unit": "particles/s",
-                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle", "cpu": cpu_model(),
                                 "sample": f"phi+F at all {N} targets, one pass of the direct FP64 sum (oracle A)"}
         acc = {}
         for name, out in (("fp32", out32), ("fp64", out64), ("fp32_method2", outm2)):
