@@ -204,3 +204,43 @@ def test_uniform_charges_give_the_printed_Q():
     for n, qv in zip(g["N"], g["Q"]):
         qs = wl.uniform_charges(n, seed=1, neutral=False)
         assert float(qs @ qs) == pytest.approx(qv, rel=0.12 if n == 100 else 0.02)
+
+
+# ---------------------------------------------------------------- Poisson's equation
+
+@pytest.mark.parametrize("D", [3, 2, 1, 0])
+def test_fourier_part_solves_poisson_with_screened_charges(D):
+    """phi^F is the potential of the Gaussian-screened charges (Eq. split_rhs with
+    gamma of Eq. gamma), periodised along the D periodic axes:
+    -Laplacian phi^F = 4 pi sum_n sum_p q_n gamma(x - x_n - p).  The Laplacian is
+    taken by a fourth-order central difference of the oracle's closed forms
+    (k-sums, the 2P/1P zero modes, the 0P erf sum), so a dropped term or a
+    wrong sign in any of them fails; the charges are neutral (3P drops k = 0)."""
+    L, xi, h = 1.0, 4.0, 2e-3
+    x = wl.uniform_positions(6, L, 91)
+    q = wl.uniform_charges(6, 91)
+    pts = np.array([[0.37, 0.52, 0.61], [0.81, 0.13, 0.45], [0.5, 0.5, 0.2]])
+    # fourth-order stencil along each axis: -f(2h) + 16 f(h) - 30 f(0) + 16 f(-h) - f(-2h)
+    offs = [(a, s) for a in range(3) for s in (-2, -1, 1, 2)]
+    xt = [pts]
+    for a, s in offs:
+        d = np.zeros(3)
+        d[a] = s * h
+        xt.append(pts + d)
+    phi, _ = E.fourier(D, x, q, L, xi, xt=np.concatenate(xt))
+    phi = phi.reshape(len(xt), len(pts))
+    c = {(-2,): -1.0, (-1,): 16.0, (1,): 16.0, (2,): -1.0}
+    lap = np.zeros(len(pts))
+    for i, (a, s) in enumerate(offs):
+        lap += c[(s,)] * phi[1 + i]
+    lap = (lap - 3 * 30.0 * phi[0]) / (12.0 * h * h)
+    # screened charge density, images along the periodic axes
+    rho = np.zeros(len(pts))
+    rng = range(-3, 4)
+    for p0 in (rng if D >= 1 else [0]):
+        for p1 in (rng if D >= 2 else [0]):
+            for p2 in (rng if D >= 3 else [0]):
+                shift = np.array([p0, p1, p2]) * L
+                r2 = ((pts[:, None, :] - x[None, :, :] - shift) ** 2).sum(-1)
+                rho += (q[None, :] * (xi / math.sqrt(math.pi)) ** 3 * np.exp(-xi * xi * r2)).sum(1)
+    np.testing.assert_allclose(-lap, 4 * math.pi * rho, rtol=1e-7, atol=1e-7 * np.abs(4 * math.pi * rho).max())
