@@ -441,10 +441,18 @@ def run_ours(a):
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "traffic": None}
-    # spread/gather GB/s on algorithmic bytes (16 B in per particle, 16 B out, grid once)
+    # spread/gather GB/s on algorithmic bytes (16 B in per particle, 16 B out, grid once),
+    # and as a fraction of the measured copy bandwidth (these stages are compute kernels:
+    # 58 and 120 flop per algorithmic byte, so the fraction is small by construction)
     grid_bytes = 4 * info["Mt"] ** 3
     sg_bytes = N * (16 + 16 + 8) + 2 * grid_bytes
     sg_gbs = sg_bytes / ((stage_ms["spread"] + stage_ms["merge"] + stage_ms["gather"]) * 1e-3) / 1e9
+    hbm_gbs = 6800.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm_gbs = float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
 
     # ---- end to end through the C ABI with host buffers ---------------------------
     xh = torch.tensor(x_np, dtype=torch.float32).pin_memory()
@@ -473,6 +481,8 @@ def run_ours(a):
             "roofline": roof,
             "stage_ms": stage_ms,
             "spread_gather_gbs": sg_gbs,
+            "spread_gather_hbm_frac": {"value": sg_gbs / hbm_gbs, "peak_gbs": hbm_gbs,
+                                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), else 6800 GB/s"},
             "e2e": {"value": aggregate_throughput(N, world, e2e_s), "unit": "particles/s", "h2d_bytes_per_step": N * 16,
                     "d2h_bytes_per_step": N * 16 + 8, "api": "se_force with SE_HOST_IO (pinned host buffers)"},
             "gpu_launches": int(round(launches_per_step * a.steps)),
