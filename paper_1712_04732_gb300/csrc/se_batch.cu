@@ -360,7 +360,7 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
     float best = 1e30f;
     Cand pick = cands.front();
     se_status st = SE_OK;
-    bool swapped = false;
+    bool swapped = false, found = false;
     for (const Cand &c : cands) {
         if (c.dense4 != swapped) {
             release_graph(b);
@@ -369,17 +369,27 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
             swapped = c.dense4;
         }
         b->form = c.form;
+        // a candidate that cannot be built or captured (workspace, capture errors)
+        // is skipped; the call fails only if none can
+        se_status cs = SE_OK;
         if (c.form == kFormFused) {
             b->fused_cl = c.cl;
-            if ((st = build_fused(b)) != SE_OK) break;
+            cs = build_fused(b);
         }
-        if ((st = capture(b, x, q, F, phi, energy)) != SE_OK) break;
+        if (cs == SE_OK) cs = capture(b, x, q, F, phi, energy);
+        if (cs != SE_OK) {
+            st = cs;
+            release_graph(b);
+            continue;
+        }
         const float t = time_graph(b, e0, e1);
         if (t < best) {
             best = t;
             pick = c;
+            found = true;
         }
     }
+    if (found) st = SE_OK;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     release_graph(b);
