@@ -289,7 +289,9 @@ se_status se_batch_force_each(se_batch_t batch, const void *x, const void *q, vo
 se_status se_batch_get_system(se_batch_t batch, int i, se_plan_info_t *info);
 /* Form of the captured graph (1 per-system, 2 multi-system) and the number of
  * library kernels one call launches (cuFFT's own kernels excluded; valid after
- * the first se_batch_force).  Either pointer may be NULL. */
+ * the first se_batch_force).  Batching has no counterpart in the paper.  Either
+ * pointer (host memory, written by the call) may be NULL.  Errors: SE_EINVAL
+ * for a NULL batch. */
 se_status se_batch_get_form(se_batch_t batch, int *form, int64_t *kernels_per_call);
 
 /* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
