@@ -3,8 +3,9 @@
  *
  * The library computes the Fourier-space part of the Ewald potential,
  * phi~^{DP,F} of Eq. (fourier_space_ewald), and its gradient, for N point
- * charges in a cubic box [0, L)^3 that is periodic in its first D directions
- * (D = 3: x, y, z; D = 2: x, y; D = 1: x; D = 0: none), by the unified
+ * charges in a box [0, L_x) x [0, L_y) x [0, L_z) (Sec. 2: the box need not be
+ * a cube) that is periodic in its first D directions (D = 3: x, y, z; D = 2:
+ * x, y; D = 1: x; D = 0: none), by the unified
  * Spectral Ewald method of Shamshirgar, Bagge & Tornberg, Alg. 4:
  *   1. gridding (Eq. gridding) with a truncated Gaussian (Eq. gaussian) or a
  *      polynomial Kaiser-Bessel window (PKB, Sec. 4.1) of P^3 support,
@@ -220,8 +221,11 @@ se_status se_plan_get_profile(se_plan_t plan, double *ms, int64_t *calls, int64_
  * allocates nothing.  The per-tile gridding blocks live in a fixed array of
  * SE_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
  * library holds until the process exits.
- *  - The first call on a device looks up that array's device address (once per
- *    device); make that first call before any CUDA stream capture.
+ *  - se_plan_reserve looks up that array's device address on the plan's device
+ *    (the first lookup on a device is when the driver allocates the array).  A
+ *    plan whose workspace grew through other calls, without se_plan_reserve,
+ *    does that lookup in its first call here instead: make that first call
+ *    before any CUDA stream capture.
  *  - All calls share the array and it keeps the last call's contents; calls
  *    whose work overlaps on the GPU (several streams or plans at once) race.
  *  - Arguments as se_potential (device pointers; SE_ADD_SELF, SE_CHECK_NEUTRAL,
@@ -296,10 +300,42 @@ se_status se_batch_get_form(se_batch_t batch, int *form, int64_t *kernels_per_ca
 
 /* Sec. 6: grid size M (= 2 k_inf, Eq. KP_kinf) and window support P (from the
  * approximation-error estimates of Sec. 5.2, rounded up to even, with the
- * error-pollution rule of Eq. error_pollution) for an absolute rms tolerance
- * eps, splitting parameter xi, box side L and Q = sum q^2. */
-se_status se_params_from_tolerance(double eps, double xi, double L, double Q, se_window w,
-                                   int *M, int *P);
+ * error-pollution rule of Eq. error_pollution: M up 5 % and P + 4 when
+ * P > f_W(M / (xi L))) for the relative rms tolerance eps_rel, i.e. the
+ * absolute tolerance eps_rel B with B = sqrt(Q) f_c(xi L) / L
+ * (Eq. fc-expression).  Q = sum q^2; Q <= 0 takes N / 3 (the mean for charges
+ * uniform in [-1, 1]).  box[3] = the sides (host memory); the estimates are the
+ * cube's, taken with L = box[0], whose M intervals set the spacing h of every
+ * axis; M is then raised to the smallest even value (up to 4x) for which every
+ * side is an even multiple of h, as se_plan_create requires.  D (0..3) is
+ * checked; the rules of Sec. 6 for M and P are the same for every D (the AFT
+ * sizes that depend on D are set by se_plan_create).  The result may exceed
+ * the plan limits (P <= 16).  *M, *P: host outputs.  Errors: SE_EINVAL
+ * (arguments, or no admissible M for the box). */
+se_status se_params_from_tolerance(double eps_rel, double xi, int64_t N, double Q, const double box[3], int D,
+                                   se_window w, int *M, int *P);
+
+/* Measured throughput ceilings of the units the gridding and gathering kernels
+ * run on, for roofline reports (a measurement aid; the paper has no
+ * counterpart).  kind: 0 FP32 fused multiply-add, 1 FP64 fused multiply-add
+ * (*ops_per_s in flop/s, 2 flop per FMA, 8 independent chains per thread);
+ * 2 shared-memory 32-bit integer atomic adds, 3 shared-memory FP32 atomic
+ * adds (*ops_per_s in updates/s; every lane of a warp on its own word and bank).
+ * One kernel fills every SM of the current device with resident warps and runs
+ * `iters` iterations of its loop (128 FMA or 16 atomic adds per thread each);
+ * *ms (may be NULL) receives its CUDA-event duration.  Synchronises the
+ * device; allocates 1 MiB for the duration of the call.  Errors: SE_EINVAL,
+ * SE_ECUDA. */
+se_status se_measure_peak(int kind, int64_t iters, double *ops_per_s, double *ms);
+
+/* Testing aid for callers' error paths (the paper has no counterpart): arm a
+ * host-side allocation failure.  From this call on, the k-th device allocation
+ * the library makes itself (plan grids, tables and workspace, batch workspace;
+ * in any plan or batch and any thread; cuFFT's own work areas are not counted)
+ * fails with SE_ENOMEM without calling cudaMalloc, exactly as a real
+ * out-of-memory would be reported; later allocations proceed normally.
+ * k <= 0 disarms.  Nothing on the GPU is touched.  Always returns SE_OK. */
+se_status se_debug_fail_alloc(int64_t k);
 
 /* Name of a status code; text of the last error raised in this thread. */
 const char *se_status_str(se_status s);

@@ -20,7 +20,7 @@ import torch
 from . import _native as nat
 from ._native import SEError
 
-__all__ = ["Plan", "Batch", "SEError", "potential", "energy", "params_from_tolerance"]
+__all__ = ["Plan", "Batch", "SEError", "potential", "energy", "params_from_tolerance", "measure_peak"]
 
 _WINDOWS = {"gaussian": nat.SE_WIN_GAUSSIAN, "pkb": nat.SE_WIN_PKB}
 _DTYPES = {torch.float32: nat.SE_F32, torch.float64: nat.SE_F64}
@@ -330,9 +330,27 @@ def energy(plan: Plan, x, q, add_self: bool = False):
     return _EnergyFn.apply(plan, x, q, add_self)
 
 
-def params_from_tolerance(eps: float, xi: float, L: float, Q: float, window: str = "pkb"):
-    """(M, P) from the rules of Sec. 6 (``se_params_from_tolerance``)."""
+def params_from_tolerance(eps_rel: float, xi: float, L, Q: float = 0.0, window: str = "pkb", N: int = 0,
+                          D: int = 3):
+    """(M, P) from the rules of Sec. 6 for the relative rms tolerance eps_rel
+    (``se_params_from_tolerance``).  ``L`` is the box side or the three sides;
+    ``Q`` = sum q^2 (0: N / 3)."""
     lib = nat.load()
+    box = (ctypes.c_double * 3)(*([float(L)] * 3 if isinstance(L, (int, float)) else [float(v) for v in L]))
     M, P = ctypes.c_int(), ctypes.c_int()
-    nat.check(lib.se_params_from_tolerance(eps, xi, L, Q, _WINDOWS[window], ctypes.byref(M), ctypes.byref(P)))
+    nat.check(lib.se_params_from_tolerance(eps_rel, xi, int(N), Q, box, int(D), _WINDOWS[window], ctypes.byref(M),
+                                           ctypes.byref(P)))
     return M.value, P.value
+
+
+_PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "smem_atomic_i32": 2, "smem_atomic_f32": 3}
+
+
+def measure_peak(kind: str, iters: int):
+    """Measured ceiling on the current device (``se_measure_peak``): flop/s for
+    "fp32_fma" / "fp64_fma", shared-memory atomic updates/s for
+    "smem_atomic_i32" / "smem_atomic_f32"; returns (rate, kernel ms)."""
+    lib = nat.load()
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    nat.check(lib.se_measure_peak(_PEAK_KINDS[kind], int(iters), ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value

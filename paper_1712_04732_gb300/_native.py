@@ -25,7 +25,7 @@ EXPORTS = ["se_opts_default", "se_plan_create", "se_plan_destroy", "se_plan_set_
            "se_plan_set_profiling", "se_plan_get_profile", "se_potential_noalloc",
            "se_batch_create", "se_batch_destroy", "se_batch_set_stream", "se_batch_force", "se_batch_force_each",
            "se_batch_get_system", "se_batch_get_form", "se_real_space",
-           "se_params_from_tolerance", "se_status_str", "se_last_error"]
+           "se_params_from_tolerance", "se_measure_peak", "se_debug_fail_alloc", "se_status_str", "se_last_error"]
 SE_N_STAGES = 8
 STAGES = ["bin", "spread", "merge", "fft_fwd", "scale", "fft_inv", "gather", "energy"]
 
@@ -98,7 +98,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "se_batch_get_system": (ci, [vp, ci, ctypes.POINTER(Info)]),
         "se_batch_get_form": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(i64)]),
         "se_plan_get_profile": (ci, [vp, ctypes.POINTER(cd), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
-        "se_params_from_tolerance": (ci, [cd, cd, cd, cd, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
+        "se_params_from_tolerance": (ci, [cd, cd, ctypes.c_int64, cd, ctypes.POINTER(cd), ci, ci,
+                                          ctypes.POINTER(ci), ctypes.POINTER(ci)]),
+        "se_measure_peak": (ci, [ci, i64, ctypes.POINTER(cd), ctypes.POINTER(cd)]),
+        "se_debug_fail_alloc": (ci, [i64]),
         "se_status_str": (ctypes.c_char_p, [ci]),
         "se_last_error": (ctypes.c_char_p, []),
     }

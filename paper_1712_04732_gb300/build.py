@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libse_gb300.so")
 SOURCES = ["se_api.cu", "se_plan.cu", "se_kern_f32.cu", "se_kern_f64.cu", "se_mbatch_f32.cu", "se_mbatch_f64.cu",
-           "se_noalloc.cu", "se_batch.cu", "se_real.cu"]
+           "se_noalloc.cu", "se_batch.cu", "se_real.cu", "se_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -418,7 +418,12 @@ se_status se_plan_reserve(se_plan_t p, int64_t n)
 {
     if (!p) return fail(SE_EINVAL, "plan is NULL");
     if (n < 0) return fail(SE_EINVAL, "negative size");
-    return plan_reserve(p, n);
+    se_status st = plan_reserve(p, n);
+    if (st != SE_OK) return st;
+    // set-up of se_potential_noalloc: its fixed scratch is made resident on the
+    // plan's device here, so that the entry point itself allocates nothing
+    void *scratch = nullptr;
+    return noalloc_scratch_address(p->dev, &scratch);
 }
 
 se_status se_plan_get_info(se_plan_t p, se_plan_info_t *info)
@@ -540,14 +545,34 @@ se_status se_plan_get_profile(se_plan_t p, double *ms, int64_t *calls, int64_t *
     return SE_OK;
 }
 
-se_status se_params_from_tolerance(double eps, double xi, double L, double Q, se_window w, int *M, int *P)
+se_status se_debug_fail_alloc(int64_t k)
 {
-    if (!M || !P) return fail(SE_EINVAL, "NULL output");
-    if (!(eps > 0) || !(xi > 0) || !(L > 0) || !(Q > 0)) return fail(SE_EINVAL, "arguments must be positive");
-    // B = sqrt(Q) f_c(xi L) / L, Eq. (fc-expression)
+    alloc_injection_arm(k);
+    return SE_OK;
+}
+
+se_status se_params_from_tolerance(double eps_rel, double xi, int64_t N, double Q, const double box[3], int D,
+                                   se_window w, int *M, int *P)
+{
+    if (!M || !P || !box) return fail(SE_EINVAL, "NULL argument");
+    if (D < 0 || D > 3) return fail(SE_EINVAL, "D must be 0, 1, 2 or 3");
+    if (w != SE_WIN_GAUSSIAN && w != SE_WIN_PKB) return fail(SE_EINVAL, "unknown window");
+    if (!(eps_rel > 0) || !(eps_rel < 1) || !(xi > 0)) return fail(SE_EINVAL, "need 0 < eps_rel < 1 and xi > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0) || !std::isfinite(box[a])) return fail(SE_EINVAL, "box sides must be positive");
+    if (!(Q > 0)) {
+        if (N <= 0) return fail(SE_EINVAL, "give Q = sum q^2 > 0 or N > 0");
+        Q = double(N) / 3.0;                  // the mean of sum q^2 for q uniform in [-1, 1]
+    }
+    // the estimates are written for the cube of side L; the box uses L = L_x,
+    // whose M intervals set the spacing h of every axis
+    const double L = box[0];
+    // B = sqrt(Q) f_c(xi L) / L, Eq. (fc-expression); absolute tolerance eps = eps_rel B
     const double xl = xi * L;
     const double fc = std::exp(-12.62 / (xl * xl)) * (0.8909 + 0.01411 * xl + 4.315e-5 * xl * xl);
     const double B = std::sqrt(Q) * fc / L;
+    const double eps = eps_rel * B;
+    if (!(eps > 0)) return fail(SE_EINVAL, "eps_rel B underflows (xi L too small)");
     // M = 2 k_inf with k_inf from Eq. (KP_kinf)
     const double arg = 4.0 / 3.0 * std::pow(Q / (M_PI * xi * L * L * L * eps * eps), 2.0 / 3.0);
     const double kinf = std::sqrt(3.0) * xi * L / (2.0 * M_PI) * std::sqrt(lambert_w(arg));
@@ -556,14 +581,27 @@ se_status se_params_from_tolerance(double eps, double xi, double L, double Q, se
     double pr = (w == SE_WIN_GAUSSIAN) ? std::log(2.0 * B / eps) / (M_PI / 2.0 * std::sqrt(0.91))
                                        : std::log(10.0 * B / eps) / 2.5;
     int pp = std::max(2, even_up(pr));
-    // Eq. (error_pollution)
+    // Eq. (error_pollution): M up 5 %, P + 4 when P > f_W(M / (xi L))
     const double xx = m / (xi * L);
     const double fw = (w == SE_WIN_GAUSSIAN) ? xx * xx + 0.2 * xx + 2.25 : 0.7 * xx * xx + 0.2 * xx + 1.8;
     if (pp > fw) {
         m = even_up(1.05 * m);
         pp += 4;
     }
-    *M = m;
+    // a box that is not a cube: the smallest even M' >= M for which every side is an
+    // even multiple of h = L_x / M' (se_plan_create's condition), up to 4 M
+    int m2 = m;
+    for (; m2 <= 4 * m; m2 += 2) {
+        bool ok = true;
+        for (int a = 0; a < 3 && ok; ++a) {
+            const double r = box[a] * m2 / L;
+            const long long k = std::llround(r);
+            ok = k >= 2 && (k & 1) == 0 && std::fabs(double(k) - r) <= 1e-9 * r;
+        }
+        if (ok) break;
+    }
+    if (m2 > 4 * m) return fail(SE_EINVAL, "no M up to 4x the estimate makes every box side an even multiple of h");
+    *M = m2;
     *P = pp;
     return SE_OK;
 }

@@ -305,18 +305,23 @@ se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *ph
 }
 
 // Median time of a few replays of the captured graph.
-float time_graph(se_batch_s *b, cudaEvent_t e0, cudaEvent_t e1)
+// Median of five timed replays of the captured graph (one untimed replay first).
+// Every CUDA call is checked: a candidate whose graph cannot run reports the
+// error instead of a time.
+se_status time_graph(se_batch_s *b, cudaEvent_t e0, cudaEvent_t e1, float *median)
 {
     float t[5];
     for (int r = 0; r < 6; ++r) {
-        cudaEventRecord(e0, b->stream);
-        cudaGraphLaunch(b->exec, b->stream);
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+        cudaError_t e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess && r > 0) e = cudaEventElapsedTime(&t[r - 1], e0, e1);
+        if (e != cudaSuccess) return se::cuda_fail(e, "timing a candidate graph");
     }
     std::sort(t, t + 5);
-    return t[2];
+    *median = t[2];
+    return SE_OK;
 }
 
 // Second stage of the autotuner: the execution form, each candidate timed as a
@@ -354,9 +359,16 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
         for (int d = 0; d < (have_alt ? 2 : 1); ++d)
             for (int cl : {0, 1, 2, 4, 8}) cands.push_back({kFormFused, cl, d == 1});
     if (b->force_form != kFormFused) cands.push_back({kFormBranches, 0, false});
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    {
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            for (se_plan_t p : alt) se_plan_destroy(p);
+            return se::cuda_fail(e, "tuner events");
+        }
+    }
     float best = 1e30f;
     Cand pick = cands.front();
     se_status st = SE_OK;
@@ -382,7 +394,21 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
             release_graph(b);
             continue;
         }
-        const float t = time_graph(b, e0, e1);
+        float t = 0.f;
+        cs = time_graph(b, e0, e1, &t);
+        if (cs != SE_OK) {
+            // skipped like a candidate that cannot be captured; a sticky error
+            // (the context is unusable) ends the tuning with that error
+            st = cs;
+            release_graph(b);
+            const cudaError_t sticky = cudaDeviceSynchronize();
+            cudaGetLastError();
+            if (sticky != cudaSuccess) {
+                found = false;
+                break;
+            }
+            continue;
+        }
         if (t < best) {
             best = t;
             pick = c;
@@ -446,10 +472,9 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
     for (int i = 0; i < nsys && st == SE_OK; ++i) {
         // Sec. 6: M from Eq. (KP_kinf) and P from the approximation error for eps = eps_rel * B
         const double Qi = Q ? Q[i] : N[i] / 3.0;
-        const double xl = xi[i] * L[i];
-        const double B = std::sqrt(Qi) * std::exp(-12.62 / (xl * xl)) * (0.8909 + 0.01411 * xl + 4.315e-5 * xl * xl) / L[i];
+        const double box[3] = {L[i], L[i], L[i]};
         int M = 0, P = 0;
-        st = se_params_from_tolerance(eps_rel * B, xi[i], L[i], Qi, w, &M, &P);
+        st = se_params_from_tolerance(eps_rel, xi[i], N[i], Qi, box, D[i], w, &M, &P);
         if (st != SE_OK) break;
         P = std::min(std::max(P, 2), 16);
         M = fft_friendly(std::max(M, P));

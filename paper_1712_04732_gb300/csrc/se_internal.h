@@ -210,6 +210,10 @@ se_status cufft_fail(cufftResult r, const char *where);
 
 // allocation with accounting (se_plan.cu)
 se_status dev_alloc(se_plan_s *p, void **ptr, size_t bytes);
+// host-side allocation-failure injection (se_debug_fail_alloc): true when the
+// allocation about to be made is the one armed to fail
+bool alloc_injected_failure();
+void alloc_injection_arm(int64_t k);
 void dev_free(se_plan_s *p, void **ptr);
 
 // plan construction (se_plan.cu)
@@ -220,6 +224,9 @@ se_status plan_second_grid(se_plan_s *p);
 se_status plan_set_fft_stream(se_plan_s *p);
 void plan_release(se_plan_s *p);
 void real_release(se_plan_s *p);         // se_real.cu
+// make the fixed scratch of se_potential_noalloc resident on device `dev` and
+// record its address (se_noalloc.cu; called by se_plan_reserve)
+se_status noalloc_scratch_address(int dev, void **out);
 
 // per-precision launchers (se_kern_f32.cu / se_kern_f64.cu)
 template <typename T>
@@ -243,8 +250,9 @@ struct Ops {
                                 const void *grid_g, T *gx, T *gq);
     // device reduction of sum q and sum |q| into p->red[0..1]
     static se_status charge_sums(se_plan_s *p, int64_t N, const T *q);
-    // as spread(), with the per-tile gridding blocks in caller-provided device memory
-    static se_status spread_with_scratch(se_plan_s *p, void *dst, void *scratch);
+    // as spread() for the call's N particles, with the per-tile gridding blocks in
+    // caller-provided device memory
+    static se_status spread_with_scratch(se_plan_s *p, int64_t N, void *dst, void *scratch);
 };
 
 // Multi-system pipeline of a batch (se_mbatch_impl.cuh): binning, gridding,

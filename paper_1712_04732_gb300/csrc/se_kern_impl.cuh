@@ -511,9 +511,9 @@ se_status Ops<T>::charge_sums(se_plan_s *p, int64_t N, const T *q)
 // Gridding with the per-tile blocks in caller-provided device memory of at least
 // n_tiles * block * sizeof(T) bytes (used by the allocation-free entry point).
 template <typename T>
-se_status Ops<T>::spread_with_scratch(se_plan_s *p, void *dst, void *scratch)
+se_status Ops<T>::spread_with_scratch(se_plan_s *p, int64_t N, void *dst, void *scratch)
 {
-    return spread_impl<T>(p, p->cap, nullptr, dst, scratch);
+    return spread_impl<T>(p, N, nullptr, dst, scratch);
 }
 
 template struct Ops<T_INST>;

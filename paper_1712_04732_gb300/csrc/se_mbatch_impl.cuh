@@ -40,6 +40,8 @@ static se_status m_alloc(MBatch *m, void **ptr, size_t bytes)
 {
     *ptr = nullptr;
     if (bytes == 0) return SE_OK;
+    if (alloc_injected_failure())
+        return fail(SE_ENOMEM, "batch workspace: cudaMalloc of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;

@@ -6,9 +6,10 @@
 // loop where cudaMalloc's implicit device synchronisation is not acceptable,
 // or a framework whose own allocator owns all device memory during a step.
 // Such a caller creates the plan and reserves its particle capacity once at
-// set-up (those calls allocate), and then calls this entry point as often as it
-// likes: it allocates nothing.  The gridding step, whose per-tile blocks are
-// the scratch memory of the path, takes them from the fixed array below
+// set-up (those calls allocate; se_plan_reserve also makes the fixed array
+// below resident on the plan's device), and then calls this entry point as
+// often as it likes: it allocates nothing.  The gridding step, whose per-tile
+// blocks are the scratch memory of the path, takes them from the fixed array
 // instead of from the plan.
 #include <cmath>
 #include <mutex>
@@ -30,10 +31,15 @@ constexpr int kMaxDevices = 128;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
+}  // namespace
+
 // Device address of g_scratch on device `dev`, looked up once per device with
 // that device current.  In host code `g_scratch` names a host-side stand-in,
-// not device memory, so kernels must be handed this address instead.
-se_status scratch_address(int dev, void **out)
+// not device memory, so kernels must be handed this address instead.  The
+// first lookup on a device loads this file's module there, which is when the
+// driver allocates the array: se_plan_reserve calls this at set-up for that
+// reason.
+se_status se::noalloc_scratch_address(int dev, void **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return se::fail(SE_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_mu);
@@ -52,6 +58,8 @@ se_status scratch_address(int dev, void **out)
     return SE_OK;
 }
 
+namespace {
+
 template <typename T>
 se_status run_noalloc(se_plan_s *p, int64_t N, const T *x, const T *q, T *phi, unsigned flags, void *scratch)
 {
@@ -64,10 +72,20 @@ se_status run_noalloc(se_plan_s *p, int64_t N, const T *x, const T *q, T *phi, u
         if (e != cudaSuccess) return se::cuda_fail(e, "charge sums");
         if (std::fabs(sums[0]) > 1e-12 * sums[1]) return se::fail(SE_ENONNEUTRAL, "sum of charges is not zero");
     }
+    se::prof_mark(p, 0);
     if ((st = se::Ops<T>::bin(p, N, x, q)) != SE_OK) return st;
-    if ((st = se::Ops<T>::spread_with_scratch(p, p->grid_in, scratch)) != SE_OK) return st;
+    if ((st = se::Ops<T>::spread_with_scratch(p, N, p->grid_in, scratch)) != SE_OK) return st;
     if ((st = se::Ops<T>::convolve(p, p->grid_in, p->grid_out)) != SE_OK) return st;
     if ((st = se::Ops<T>::gather(p, N, q, phi, nullptr, nullptr, flags & SE_ADD_SELF, false)) != SE_OK) return st;
+    if (p->prof) {
+        cudaError_t e = cudaEventSynchronize(p->ev[SE_N_STAGES]);
+        if (e != cudaSuccess) return se::cuda_fail(e, "profile sync");
+        for (int i = 0; i < SE_N_STAGES; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]) == cudaSuccess) p->prof_ms[i] += ms;
+        }
+        ++p->prof_calls;
+    }
     if (flags & SE_SYNC_CHECK) return se_plan_check(p);
     return SE_OK;
 }
@@ -90,8 +108,9 @@ extern "C" se_status se_potential_noalloc(se_plan_t p, int64_t N, const void *x,
         return se::fail(SE_ECAPACITY, "the plan's gridding blocks need " + std::to_string(need) +
                                           " bytes, more than the fixed scratch of " +
                                           std::to_string(size_t(SE_NOALLOC_SCRATCH_BYTES)) + " bytes");
+    cudaGetLastError();                   // a pending error of an earlier, unrelated call is not this call's
     void *scratch = nullptr;
-    se_status st = scratch_address(p->dev, &scratch);
+    se_status st = se::noalloc_scratch_address(p->dev, &scratch);
     if (st != SE_OK) return st;
     return p->dtype == SE_F32
                ? run_noalloc<float>(p, N, static_cast<const float *>(x), static_cast<const float *>(q),

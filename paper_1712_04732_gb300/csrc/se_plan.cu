@@ -3,6 +3,7 @@
 // functions, the FP64 precomputation of Alg. 3 (D = 0), device buffers and
 // cuFFT plans.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -13,10 +14,27 @@ namespace se {
 
 // ------------------------------------------------------------ allocation
 
+// Allocation-failure injection (se_debug_fail_alloc): while the countdown is
+// positive, each device allocation decrements it, and the one that brings it
+// to zero fails as if cudaMalloc had run out of memory.
+static std::atomic<int64_t> g_alloc_countdown{0};
+
+bool alloc_injected_failure()
+{
+    int64_t c = g_alloc_countdown.load();
+    while (c > 0)
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
+void alloc_injection_arm(int64_t k) { g_alloc_countdown.store(k > 0 ? k : 0); }
+
 se_status dev_alloc(se_plan_s *p, void **ptr, size_t bytes)
 {
     *ptr = nullptr;
     if (bytes == 0) return SE_OK;
+    if (alloc_injected_failure())
+        return fail(SE_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

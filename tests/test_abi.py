@@ -73,14 +73,66 @@ def test_calls_reject_null_plan(lib):
     assert lib.se_plan_destroy(None) == 0
 
 
-@pytest.mark.parametrize("eps,xi,L,Q,win", [
+@pytest.mark.parametrize("eps_rel,xi,L,Q,win", [
     (1e-5, 8.0, 1.0, 3.32e4, "pkb"), (1e-10, 8.0, 1.0, 3.32e4, "pkb"), (1e-3, 3.0, 10.0, 3.32e4, "pkb"),
-    (1e-8, 6.0, 5.0, 334.0, "gaussian"), (1e-12, 17.0, 3.0, 3.32e4, "pkb"),
+    (1.6e-8, 6.0, 5.0, 334.0, "gaussian"), (1e-12, 17.0, 3.0, 3.32e4, "pkb"), (1e-5, 2.0, 1.0, 100.0, "pkb"),
 ])
-def test_parameter_rules_agree_with_the_oracle(lib, eps, xi, L, Q, win):
+@pytest.mark.parametrize("D", [3, 0])
+def test_parameter_rules_agree_with_the_oracle(lib, eps_rel, xi, L, Q, win, D):
     """se_params_from_tolerance (C++) and the oracle's Sec. 6 rules (Python) are
-    written independently; they must give the same (M, P)."""
+    written independently; they must give the same (M, P) for the absolute
+    tolerance eps_rel B (the rules do not depend on D)."""
     M, P = ctypes.c_int(), ctypes.c_int()
     w = nat.SE_WIN_GAUSSIAN if win == "gaussian" else nat.SE_WIN_PKB
-    assert lib.se_params_from_tolerance(eps, xi, L, Q, w, ctypes.byref(M), ctypes.byref(P)) == 0
+    box = (ctypes.c_double * 3)(L, L, L)
+    assert lib.se_params_from_tolerance(eps_rel, xi, 0, Q, box, D, w, ctypes.byref(M), ctypes.byref(P)) == 0
+    eps = eps_rel * prm.scale_B(Q, xi, L)
     assert (M.value, P.value) == prm.from_tolerance(eps, xi, L, Q, win)
+
+
+def test_parameter_rules_take_Q_from_N(lib):
+    """Q <= 0: Q = N / 3, the mean of sum q^2 for charges uniform in [-1, 1]."""
+    M, P = ctypes.c_int(), ctypes.c_int()
+    box = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    assert lib.se_params_from_tolerance(1e-6, 8.0, 30000, 0.0, box, 2, nat.SE_WIN_PKB,
+                                        ctypes.byref(M), ctypes.byref(P)) == 0
+    Q = 30000 / 3.0
+    assert (M.value, P.value) == prm.from_tolerance(1e-6 * prm.scale_B(Q, 8.0, 1.0), 8.0, 1.0, Q, "pkb")
+
+
+@pytest.mark.parametrize("sides", [(1.0, 0.75, 1.5), (1.0, 1.0, 2.0), (2.0, 1.0, 1.0), (1.0, 0.6, 1.2)])
+def test_parameter_rules_fit_the_box(lib, sides):
+    """A box that is not a cube: M is the smallest even value at or above the
+    cube's rule for which every side is an even multiple of h = L_x / M (the
+    oracle's box_grid accepts it, and it rejects every smaller even M)."""
+    M, P = ctypes.c_int(), ctypes.c_int()
+    box = (ctypes.c_double * 3)(*sides)
+    Q, xi, eps_rel = 3000.0, 8.0, 1e-5
+    assert lib.se_params_from_tolerance(eps_rel, xi, 0, Q, box, 3, nat.SE_WIN_PKB,
+                                        ctypes.byref(M), ctypes.byref(P)) == 0
+    M0, P0 = prm.from_tolerance(eps_rel * prm.scale_B(Q, xi, sides[0]), xi, sides[0], Q, "pkb")
+    assert P.value == P0 and M.value >= M0 and M.value % 2 == 0
+    prm.box_grid(sides, M.value)
+    for m in range(M0 + (M0 & 1), M.value, 2):
+        with pytest.raises(ValueError):
+            prm.box_grid(sides, m)
+
+
+@pytest.mark.parametrize("args", [
+    dict(eps_rel=0.0), dict(eps_rel=1.5), dict(xi=-1.0), dict(D=4), dict(D=-1), dict(win=7),
+    dict(Q=0.0, N=0), dict(box=(1.0, 0.0, 1.0)), dict(box=(1.0, 1.0 / 3.0 + 1e-7, 1.0)),
+])
+def test_parameter_rules_reject_bad_arguments(lib, args):
+    a = dict(eps_rel=1e-5, xi=8.0, N=100, Q=30.0, box=(1.0, 1.0, 1.0), D=3, win=nat.SE_WIN_PKB)
+    a.update(args)
+    M, P = ctypes.c_int(), ctypes.c_int()
+    box = (ctypes.c_double * 3)(*a["box"])
+    assert lib.se_params_from_tolerance(a["eps_rel"], a["xi"], a["N"], a["Q"], box, a["D"], a["win"],
+                                        ctypes.byref(M), ctypes.byref(P)) == 1
+    assert lib.se_last_error()
+
+
+def test_allocation_failure_hook_is_host_only(lib):
+    """Arming and disarming the injected allocation failure touches no GPU."""
+    assert lib.se_debug_fail_alloc(3) == 0
+    assert lib.se_debug_fail_alloc(0) == 0

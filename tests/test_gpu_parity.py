@@ -452,19 +452,52 @@ def test_lattice_workload_gaussian():
     assert _rel(phi, pb) < 1e-11
 
 
-@pytest.mark.parametrize("dtype,P", [(torch.float32, 6), (torch.float64, 10)])
+def _tile_ids(plan, x):
+    """Gridding tile of each particle: the tile holding its lowest support point
+    floor(t) - P/2 + 1 (t = (x + offset)/h, wrapped along periodic axes)."""
+    info = plan.info()
+    h, D, P = info["h"], plan.D, plan.P
+    n = np.array(info["grid"])
+    T = np.array(info["tile"])
+    off = np.array([0.0 if a < D else (info["Mt_v"][a] - info["M_v"][a]) * h / 2 for a in range(3)])
+    anc = np.floor((x + off) / h).astype(np.int64) - P // 2 + 1
+    for a in range(D):
+        anc[:, a] %= n[a]
+    t = anc // T
+    nt = -(-n // T)
+    return (t[:, 2] * nt[1] + t[:, 1]) * nt[0] + t[:, 0]
+
+
+def _stratified(plan, x, k_random, seed):
+    """One target in every non-empty gridding tile, plus k_random drawn at random."""
+    _, first = np.unique(_tile_ids(plan, x), return_index=True)
+    extra = np.random.default_rng(seed).choice(len(x), size=min(k_random, len(x)), replace=False)
+    return np.unique(np.concatenate([first, extra]))
+
+
+def _assert_elementwise(a, b, tol):
+    """Every element within tol times the rms of the reference."""
+    err = np.abs(np.asarray(a) - b).max()
+    assert err <= tol * np.sqrt(np.mean(np.asarray(b) ** 2)), err
+
+
+@pytest.mark.parametrize("dtype,P", [(torch.float32, 6), (torch.float32, 8), (torch.float64, 10)])
 def test_slab_workload_full_size(dtype, P):
-    """2P, N = 100000, M = 64, xi = 16, PKB P = 6 (FP32) / 10 (FP64): the GPU
-    against oracle B (same discretisation) on 300 sampled targets at full size."""
+    """2P, N = 100000, M = 64, xi = 16, PKB P = 6, 8 (FP32) / 10 (FP64): the GPU
+    against oracle B (same discretisation) at full size, on one target in every
+    non-empty gridding tile plus 300 at random: rms and element-wise."""
     se = _se()
     x, q, spec = wl.make("slab_2p", seed=1)
     plan = se.Plan(2, 1.0, spec["xi"], spec["M"], P, "pkb", dtype=dtype)
     F, phi, _ = _run(plan, x, q)
-    idx = _sample(len(q), 300, 1)
+    idx = _stratified(plan, x, 300, 1)
+    assert len(idx) >= plan.info()["n_tiles"] // 2
     pb, gb = _oracle_for(plan).potential(x, q, xt=x[idx], grad=True)
     tp, tf = TOL[dtype]
     assert _rel(phi[idx], pb) < tp
     assert _rel(F[idx], -q[idx, None] * gb) < tf
+    _assert_elementwise(phi[idx], pb, 10 * tp)
+    _assert_elementwise(F[idx], -q[idx, None] * gb, 10 * tf)
 
 
 @pytest.mark.parametrize("dtype,P,tol_phi,tol_F", [(torch.float32, 6, 1e-5, 3e-4), (torch.float32, 8, 1e-5, 1e-5),
@@ -483,17 +516,51 @@ def test_slab_parameters_accuracy_against_direct_sum(dtype, P, tol_phi, tol_F):
     assert _rel(F[idx], -q[idx, None] * ga) < tol_F
 
 
-def test_wire_workload_full_size():
+@pytest.mark.parametrize("fft_sizes", [0, 1])
+def test_wire_workload_full_size(fft_sizes):
     """1P, N = 1.2e6 (a sixth of them in ten Gaussian clouds), M = 128, xi = 32,
-    PKB P = 8, FP32: the GPU against oracle B on 200 sampled targets at full size."""
+    PKB P = 8, FP32, with the paper's minimal transform lengths and with the
+    2-3-5-7-smooth lengths the benchmark times (fft_sizes = 1; the oracle given
+    the same extension and upsampling): the GPU against oracle B at full size on
+    one target in every non-empty gridding tile (every tile of the clouds
+    included) plus 200 at random, rms and element-wise."""
     se = _se()
     x, q, spec = wl.make("wire_1p", seed=1)
-    plan = se.Plan(1, 1.0, spec["xi"], spec["M"], spec["P"], "pkb", dtype=torch.float32)
+    plan = se.Plan(1, 1.0, spec["xi"], spec["M"], spec["P"], "pkb", dtype=torch.float32, fft_sizes=fft_sizes)
     F, phi, _ = _run(plan, x, q)
-    idx = _sample(len(q), 200, 2)
+    idx = _stratified(plan, x, 200, 2)
+    info = plan.info()
+    assert len(idx) >= info["n_tiles"] // 4
+    if fft_sizes:
+        o = S.SEOracle(1, 1.0, spec["xi"], spec["M"], spec["P"], "pkb", lam=(info["Mt"] - spec["M"]) / spec["P"],
+                       s0=info["s0_mt"] / info["Mt"], s_mt=info["s_mt"], nl=info["n_l"])
+        assert o.Mt == info["Mt"] and o.g["s0Mt"] == info["s0_mt"]
+    else:
+        o = _oracle_for(plan)
+    pb, gb = o.potential(x, q, xt=x[idx], grad=True)
+    tp, tf = TOL[torch.float32]
+    assert _rel(phi[idx], pb) < tp
+    assert _rel(F[idx], -q[idx, None] * gb) < tf
+    _assert_elementwise(phi[idx], pb, 10 * tp)
+    _assert_elementwise(F[idx], -q[idx, None] * gb, 10 * tf)
+
+
+def test_fp32_tile_beyond_the_fixed_point_limit():
+    """FP32 gridding accumulates fixed-point integers in tiles of up to 65 536
+    particles and float atomics beyond: 70 000 particles packed into one tile
+    (3P, M = 32, tile edge 8: every lowest support point in cells 0..7) take the
+    float path, against oracle B."""
+    se = _se()
+    N = 70000
+    x = 3.0 / 32 + (8.0 / 32) * wl.uniform_positions(N, 1.0, 91) * (1 - 1e-7)
+    q = wl.uniform_charges(N, 91)
+    plan = se.Plan(3, 1.0, 6.0, 32, 8, "pkb", dtype=torch.float32, tile=8)
+    assert len(np.unique(_tile_ids(plan, x))) == 1
+    F, phi, _ = _run(plan, x, q)
+    idx = _sample(N, 300, 3)
     pb, gb = _oracle_for(plan).potential(x, q, xt=x[idx], grad=True)
-    assert _rel(phi[idx], pb) < TOL[torch.float32][0]
-    assert _rel(F[idx], -q[idx, None] * gb) < TOL[torch.float32][1]
+    assert _rel(phi[idx], pb) < 1e-5
+    assert _rel(F[idx], -q[idx, None] * gb) < 3e-5
 
 
 def test_wire_parameters_accuracy_against_direct_sum():
