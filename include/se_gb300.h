@@ -253,11 +253,16 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
  * nsys systems, system i with N[i] particles in a cubic box of side L[i],
  * periodic in its first D[i] directions, splitting parameter xi[i].  Each
  * system's grid M_i (Eq. KP_kinf) and support P_i (the approximation-error
- * estimate of Sec. 5.2 with the error-pollution rule, Sec. 6) are chosen for
- * the absolute tolerance eps_rel * B_i, B_i = sqrt(Q_i) f_c(xi_i L_i) / L_i
+ * estimate of Sec. 5.2 with the error-pollution rule, Sec. 6) start from the
+ * absolute tolerance eps_rel * B_i, B_i = sqrt(Q_i) f_c(xi_i L_i) / L_i
  * (Eq. fc-expression; Q = NULL takes Q_i = N_i / 3, the mean for charges
- * uniform in [-1, 1]); M_i is then rounded up to an FFT-friendly size.  The
- * window is w for all systems.  Every call replays one CUDA graph (captured on
+ * uniform in [-1, 1]), with P_i + 2 for the forces (Sec. 7.2) and M_i rounded
+ * up to an FFT-friendly size; the AFT of D = 1, 2 systems gets eps_rel / 4.
+ * With autotuning, the first call then measures, on its own inputs, the
+ * relative rms errors of phi and F of (M, P) candidates around that rule
+ * against an FP64 reference of each system and keeps the fastest candidate
+ * whose errors are both within eps_rel / 2 (se_batch_get_accuracy reports
+ * them).  The window is w for all systems.  Every call replays one CUDA graph (captured on
  * first use and whenever the pointers change) in one of two forms:
  *  - multi-system (SE_BATCH_FUSED): binning, gridding, block merge and
  *    gathering of all systems run as one kernel launch per stage and class of
@@ -289,6 +294,12 @@ se_status se_batch_force(se_batch_t batch, const void *x, const void *q, void *F
  * (no graph): the per-system baseline the batched form is measured against. */
 se_status se_batch_force_each(se_batch_t batch, const void *x, const void *q, void *F, void *phi,
                               double *energy);
+/* Relative rms errors of system i's phi and F that the autotuner measured for
+ * the chosen (M, P) against its FP64 reference on the first call's inputs
+ * (host outputs, either may be NULL; -1 when the batch was not autotuned or
+ * before the first call).  Batching has no counterpart in the paper.  Errors:
+ * SE_EINVAL for a bad batch or index. */
+se_status se_batch_get_accuracy(se_batch_t batch, int i, double *err_phi, double *err_F);
 /* Derived parameters of system i. */
 se_status se_batch_get_system(se_batch_t batch, int i, se_plan_info_t *info);
 /* Form of the captured graph (1 per-system, 2 multi-system) and the number of

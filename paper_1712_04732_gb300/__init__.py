@@ -269,6 +269,12 @@ class Batch:
         nat.check(self._lib.se_batch_get_system(self._h, i, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in nat.Info._fields_}
 
+    def accuracy(self, i):
+        """(phi, F) relative rms errors the autotuner measured for system i (-1: not measured)."""
+        ep, ef = ctypes.c_double(), ctypes.c_double()
+        nat.check(self._lib.se_batch_get_accuracy(self._h, i, ctypes.byref(ep), ctypes.byref(ef)))
+        return ep.value, ef.value
+
     def _sync_stream(self):
         s = torch.cuda.current_stream(self.device).cuda_stream
         if s != self._stream:

@@ -24,7 +24,7 @@ EXPORTS = ["se_opts_default", "se_plan_create", "se_plan_destroy", "se_plan_set_
            "se_plan_get_info", "se_plan_check", "se_potential", "se_force", "se_vjp",
            "se_plan_set_profiling", "se_plan_get_profile", "se_potential_noalloc",
            "se_batch_create", "se_batch_destroy", "se_batch_set_stream", "se_batch_force", "se_batch_force_each",
-           "se_batch_get_system", "se_batch_get_form", "se_real_space",
+           "se_batch_get_system", "se_batch_get_form", "se_batch_get_accuracy", "se_real_space",
            "se_params_from_tolerance", "se_measure_peak", "se_debug_fail_alloc", "se_status_str", "se_last_error"]
 SE_N_STAGES = 8
 STAGES = ["bin", "spread", "merge", "fft_fwd", "scale", "fft_inv", "gather", "energy"]
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "se_batch_force_each": (ci, [vp, vp, vp, vp, vp, vp]),
         "se_batch_get_system": (ci, [vp, ci, ctypes.POINTER(Info)]),
         "se_batch_get_form": (ci, [vp, ctypes.POINTER(ci), ctypes.POINTER(i64)]),
+        "se_batch_get_accuracy": (ci, [vp, ci, ctypes.POINTER(cd), ctypes.POINTER(cd)]),
         "se_plan_get_profile": (ci, [vp, ctypes.POINTER(cd), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "se_params_from_tolerance": (ci, [cd, cd, ctypes.c_int64, cd, ctypes.POINTER(cd), ci, ci,
                                           ctypes.POINTER(ci), ctypes.POINTER(ci)]),

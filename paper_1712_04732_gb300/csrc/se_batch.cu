@@ -61,6 +61,9 @@ struct se_batch_s {
     se_window window = SE_WIN_PKB;
     std::vector<double> L, xi;
     std::vector<int> D, M, P;
+    double eps_rel = 1e-5;            // requested relative rms tolerance
+    double aft_eps = 0.0;             // AFT tolerance of the plans (Eqs. estimate-s, estimate-nl)
+    std::vector<double> err_phi, err_F;   // errors measured by the parameter tuner (-1: not measured)
 };
 
 namespace {
@@ -74,6 +77,7 @@ se_status make_plan(se_batch_s *b, int i, const double L, int D, double xi, int 
     o.spread_mode = v.spread_mode;
     o.split = v.split;
     o.gather_mode = v.gather_mode;
+    o.aft_eps = b->aft_eps;
     const double box[3] = {L, L, L};
     se_status st = se_plan_create(out, box, D, xi, M, P, w, b->dtype, &o);
     if (st != SE_OK) return st;
@@ -185,6 +189,180 @@ se_status autotune(se_batch_s *b, const void *x, const void *q, void *F, void *p
     cudaEventDestroy(e1);
     b->tuned = true;
     return SE_OK;
+}
+
+// Relative rms difference |a - r| / |r| over n values.
+double rel_rms(const std::vector<double> &a, const std::vector<double> &r, size_t n)
+{
+    double d = 0.0, t = 0.0;
+    for (size_t k = 0; k < n; ++k) {
+        d += (a[k] - r[k]) * (a[k] - r[k]);
+        t += r[k] * r[k];
+    }
+    return t > 0.0 ? std::sqrt(d / t) : std::sqrt(d);
+}
+
+// Device scratch of the parameter tuner.
+struct TuneBuf {
+    double *x64 = nullptr;     // x [N][3] and q [N] in FP64 (the reference's input)
+    void *out = nullptr;       // F [N][3] and phi [N] of a run (batch precision or FP64)
+    ~TuneBuf()
+    {
+        if (x64) cudaFree(x64);
+        if (out) cudaFree(out);
+    }
+};
+
+// Stage 0 of the autotuner: the grid size M and support P of every system,
+// chosen on the call's own inputs.  The Sec. 6 rule gives (M0, P0); the
+// candidates are P in {P0 - 2, P0, P0 + 2, P0 + 4} and M in {M0, 1.25 M0,
+// 1.5 M0} (FFT-friendly, P <= min(M, 16)).  Each candidate's phi and F are
+// compared with an FP64 reference of the same system (support min(16,
+// P0 + 6), grid 1.5 M0 rounded up, AFT tolerance 1e-12, whose own error is far
+// below eps_rel); among the candidates whose relative rms errors of phi and F
+// are both within eps_rel / 2 (a margin for inputs that change between calls)
+// the fastest, by the median of three timed calls, is kept; if none is, the
+// most accurate.
+se_status tune_params(se_batch_s *b, const void *x, const void *q)
+{
+    const size_t e = elem(b);
+    int64_t nmax = 0;
+    for (int64_t n : b->N) nmax = std::max(nmax, n);
+    TuneBuf buf;
+    cudaError_t ce = cudaMalloc((void **)&buf.x64, sizeof(double) * 4 * nmax);
+    if (ce == cudaSuccess) ce = cudaMalloc(&buf.out, sizeof(double) * 4 * nmax);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return se::fail(SE_ENOMEM, "parameter tuner scratch");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return se::cuda_fail(ce, "tuner events");
+    }
+    std::vector<char> raw(e * 4 * nmax);
+    std::vector<double> h64(4 * nmax), rphi(nmax), rF(3 * nmax), cphi(nmax), cF(3 * nmax);
+    se_status st = SE_OK;
+    for (int i = 0; i < b->nsys && st == SE_OK; ++i) {
+        const int64_t n = b->N[i];
+        const char *xi_dev = static_cast<const char *>(x) + 3 * e * b->off[i];
+        const char *qi_dev = static_cast<const char *>(q) + e * b->off[i];
+        // the system's inputs in FP64 for the reference
+        ce = cudaMemcpy(raw.data(), xi_dev, 3 * e * n, cudaMemcpyDeviceToHost);
+        if (ce == cudaSuccess) ce = cudaMemcpy(raw.data() + 3 * e * n, qi_dev, e * n, cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) { st = se::cuda_fail(ce, "tuner inputs"); break; }
+        for (int64_t k = 0; k < 4 * n; ++k)
+            h64[k] = e == 4 ? double(reinterpret_cast<const float *>(raw.data())[k])
+                            : reinterpret_cast<const double *>(raw.data())[k];
+        if ((ce = cudaMemcpy(buf.x64, h64.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st = se::cuda_fail(ce, "tuner inputs");
+            break;
+        }
+        const int M0 = b->M[i], P0 = std::max(2, b->P[i] - 2);      // b->P holds the untuned rule's P0 + 2
+        const double box[3] = {b->L[i], b->L[i], b->L[i]};
+        // FP64 reference
+        {
+            se_opts o;
+            se_opts_default(&o);
+            o.aft_eps = 1e-12;
+            se_plan_t ref = nullptr;
+            const int Mr = fft_friendly(int(std::ceil(1.5 * M0))), Pr = std::min(16, P0 + 6);
+            st = se_plan_create(&ref, box, b->D[i], b->xi[i], Mr, std::min(Pr, Mr), b->window, SE_F64, &o);
+            double *dF = static_cast<double *>(buf.out), *dphi = dF + 3 * n;
+            if (st == SE_OK) st = se_plan_set_stream(ref, b->stream);
+            if (st == SE_OK) st = se_force(ref, n, buf.x64, buf.x64 + 3 * n, dF, dphi, nullptr, 0);
+            if (st == SE_OK && (ce = cudaStreamSynchronize(b->stream)) != cudaSuccess) st = se::cuda_fail(ce, "reference");
+            if (st == SE_OK && (ce = cudaMemcpy(rF.data(), dF, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                st = se::cuda_fail(ce, "reference results");
+            if (st == SE_OK && (ce = cudaMemcpy(rphi.data(), dphi, sizeof(double) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                st = se::cuda_fail(ce, "reference results");
+            se_plan_destroy(ref);
+            if (st != SE_OK) break;
+        }
+        // candidates around the rule
+        struct Cand { int M, P; };
+        std::vector<Cand> cands;
+        for (int dP : {-2, 0, 2, 4})
+            for (double f : {1.0, 1.25, 1.5}) {
+                const int Pc = P0 + dP;
+                const int Mc = fft_friendly(std::max(int(std::ceil(f * M0)), Pc));
+                if (Pc < 2 || Pc > 16) continue;
+                bool dup = false;
+                for (const Cand &c : cands) dup = dup || (c.M == Mc && c.P == Pc);
+                if (!dup) cands.push_back({Mc, Pc});
+            }
+        float best_t = 1e30f;
+        double best_err = 1e30;
+        int pick = -1, pick_acc = -1;
+        std::vector<double> errs(cands.size() * 2, -1.0);
+        for (size_t c = 0; c < cands.size() && st == SE_OK; ++c) {
+            se_plan_t p = nullptr;
+            se_status cs = make_plan(b, i, b->L[i], b->D[i], b->xi[i], cands[c].M, cands[c].P, b->window,
+                                     Variant{8, 0, 0, 0}, &p);
+            if (cs == SE_OK) cs = se_plan_set_stream(p, b->stream);
+            if (cs != SE_OK) {                               // not available for this grid: skip
+                se_plan_destroy(p);
+                if (cs == SE_ECUDA) st = cs;
+                continue;
+            }
+            char *dF = static_cast<char *>(buf.out), *dphi = dF + 3 * e * n;
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int r = 0; r < 4 && cs == SE_OK; ++r) {
+                ce = cudaEventRecord(e0, b->stream);
+                cs = se_force(p, n, xi_dev, qi_dev, dF, dphi, nullptr, 0);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                if (ce == cudaSuccess && r > 0) ce = cudaEventElapsedTime(&t[r - 1], e0, e1);
+                if (ce != cudaSuccess) cs = se::cuda_fail(ce, "timing a candidate");
+            }
+            if (cs == SE_OK && (ce = cudaMemcpy(raw.data(), dF, 4 * e * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+                cs = se::cuda_fail(ce, "candidate results");
+            se_plan_destroy(p);
+            if (cs != SE_OK) {
+                st = cs;
+                break;
+            }
+            for (int64_t k = 0; k < 3 * n; ++k)
+                cF[k] = e == 4 ? double(reinterpret_cast<const float *>(raw.data())[k])
+                               : reinterpret_cast<const double *>(raw.data())[k];
+            for (int64_t k = 0; k < n; ++k)
+                cphi[k] = e == 4 ? double(reinterpret_cast<const float *>(raw.data())[3 * n + k])
+                                 : reinterpret_cast<const double *>(raw.data())[3 * n + k];
+            const double ep = rel_rms(cphi, rphi, size_t(n)), ef = rel_rms(cF, rF, size_t(3 * n));
+            errs[2 * c] = ep;
+            errs[2 * c + 1] = ef;
+            std::sort(t, t + 3);
+            if (ep <= 0.5 * b->eps_rel && ef <= 0.5 * b->eps_rel && t[1] < best_t) {
+                best_t = t[1];
+                pick = int(c);
+            }
+            if (std::max(ep, ef) < best_err) {
+                best_err = std::max(ep, ef);
+                pick_acc = int(c);
+            }
+        }
+        if (st != SE_OK) break;
+        if (pick < 0) pick = pick_acc;
+        if (pick < 0) continue;                              // no candidate ran: keep the rule's plan
+        se_plan_t p = nullptr;
+        st = make_plan(b, i, b->L[i], b->D[i], b->xi[i], cands[pick].M, cands[pick].P, b->window,
+                       Variant{8, 0, 0, 0}, &p);
+        if (st != SE_OK) {
+            se_plan_destroy(p);
+            break;
+        }
+        se_plan_destroy(b->plans[i]);
+        b->plans[i] = p;
+        b->M[i] = cands[pick].M;
+        b->P[i] = cands[pick].P;
+        b->err_phi[i] = errs[2 * pick];
+        b->err_F[i] = errs[2 * pick + 1];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 // Order of the systems over the branches: longest first onto the least-loaded
@@ -304,7 +482,6 @@ se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *ph
     return b->form == kFormFused ? capture_fused(b, x, q, F, phi, energy) : capture_branches(b, x, q, F, phi, energy);
 }
 
-// Median time of a few replays of the captured graph.
 // Median of five timed replays of the captured graph (one untimed replay first).
 // Every CUDA call is checked: a candidate whose graph cannot run reports the
 // error instead of a time.
@@ -468,6 +645,10 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
     b->D.assign(D, D + nsys);
     b->M.assign(nsys, 0);
     b->P.assign(nsys, 0);
+    b->eps_rel = eps_rel;
+    b->aft_eps = eps_rel / 4.0;
+    b->err_phi.assign(nsys, -1.0);
+    b->err_F.assign(nsys, -1.0);
     se_status st = SE_OK;
     for (int i = 0; i < nsys && st == SE_OK; ++i) {
         // Sec. 6: M from Eq. (KP_kinf) and P from the approximation error for eps = eps_rel * B
@@ -476,7 +657,10 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
         int M = 0, P = 0;
         st = se_params_from_tolerance(eps_rel, xi[i], N[i], Qi, box, D[i], w, &M, &P);
         if (st != SE_OK) break;
-        P = std::min(std::max(P, 2), 16);
+        // forces need P + 2 for the potential's error (Sec. 7.2); the estimates of
+        // Sec. 5.2 then hold the potential and forces of every system to eps_rel,
+        // with a quarter of the budget given to the AFT
+        P = std::min(std::max(P + 2, 2), 16);
         M = fft_friendly(std::max(M, P));
         b->M[i] = M;
         b->P[i] = P;
@@ -536,6 +720,7 @@ se_status se_batch_force(se_batch_t b, const void *x, const void *q, void *F, vo
         release_fused(b);
         // tuning needs the real inputs; it runs each system eagerly a few times,
         // then times the execution forms as captured graphs
+        if ((st = tune_params(b, x, q)) != SE_OK) return st;
         if ((st = autotune(b, x, q, F, phi, energy, b->L, b->D, b->xi, b->M, b->P, b->window)) != SE_OK) return st;
         if ((st = tune_form(b, x, q, F, phi, energy)) != SE_OK) return st;
     }
@@ -565,6 +750,14 @@ se_status se_batch_get_form(se_batch_t b, int *form, int64_t *kernels_per_call)
     if (!b) return se::fail(SE_EINVAL, "batch is NULL");
     if (form) *form = b->form;
     if (kernels_per_call) *kernels_per_call = b->kernels_per_call;
+    return SE_OK;
+}
+
+se_status se_batch_get_accuracy(se_batch_t b, int i, double *err_phi, double *err_F)
+{
+    if (!b || i < 0 || i >= b->nsys) return se::fail(SE_EINVAL, "bad batch or index");
+    if (err_phi) *err_phi = b->err_phi[i];
+    if (err_F) *err_F = b->err_F[i];
     return SE_OK;
 }
 

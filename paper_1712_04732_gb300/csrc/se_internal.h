@@ -14,6 +14,37 @@ namespace se {
 constexpr int kMaxP = 16;       // largest window support compiled in
 constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
+constexpr int kGatherChunk = 256;  // particles per CTA of the tile-staged FP32 gathering (one round per warp)
+
+// Row pitch (elements) of a gridding block in shared memory: the smallest
+// pitch >= B0 for which the gridding kernels' access pattern -- a warp's lanes
+// on rows of P consecutive elements, stacked 32 / P deep -- touches the fewest
+// bank wavefronts (8-byte elements go out as two half-warps).  Used by the plan
+// and, at compile time, by the FP32 gridding kernel for tiles of edge 8.
+__host__ __device__ constexpr int gridding_pitch(int B0, int P, int elem)
+{
+    int best = B0, best_cost = 1 << 30;
+    for (int pitch = B0; pitch < B0 + 32; ++pitch) {
+        int cost = 0;
+        const int per_wave = elem == 8 ? 16 : 32;
+        for (int h = 0; h < 32 / per_wave; ++h) {
+            int banks[32] = {};
+            for (int l = h * per_wave; l < (h + 1) * per_wave; ++l) {
+                const int r = l / P, c = l % P;
+                const long word = (long(r) * pitch + c) * (elem / 4);
+                for (int w = 0; w < elem / 4; ++w) banks[(word + w) % 32]++;
+            }
+            int worst = 0;
+            for (int b = 0; b < 32; ++b) worst = banks[b] > worst ? banks[b] : worst;
+            cost += worst;
+        }
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = pitch;
+        }
+    }
+    return best;
+}
 constexpr int kLocalScanTiles = 4096;   // up to this many tiles each binning CTA scans the counts itself
 constexpr int kMergeJ = 6;      // most tiles per axis whose blocks overlap one grid point
 
@@ -143,7 +174,10 @@ struct se_plan_s {
     size_t tile_part_elems = 0;
     double *red = nullptr;               // small FP64 reduction outputs
     int *err = nullptr;                  // latched device-side input errors
-    int *counters = nullptr;             // completion counters of the last-CTA reductions (zero between calls)
+    int *counters = nullptr;             // completion counters of the last-CTA reductions (zero between calls);
+                                         // counters[2]: chunks in chunk_map
+    int2 *chunk_map = nullptr;           // work list of the tile-staged gathering: (tile, first particle)
+    size_t chunk_map_elems = 0;          // n_tiles + capacity / kGatherChunk + 1
     // particle workspace
     int64_t cap = 0;
     int2 *tile_rank = nullptr;           // (tile, rank) per input particle

@@ -73,6 +73,17 @@ static int split_for(const se_plan_s *p, int64_t N)
     return N < 192 * nt ? 2 : 4;
 }
 
+// The same for the FP32 gridding kernel of edge-8 tiles (measured on GB300:
+// one CTA per tile up to 149 particles per tile on average (slab, free space),
+// two at 208 with dense clouds (wire), four beyond 1024).
+static int split_fast(const se_plan_s *p, int64_t N)
+{
+    if (p->split > 0) return p->split;
+    const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
+    if (N < 192 * nt) return 1;
+    return N < 1024 * nt ? 2 : 4;
+}
+
 // Gridding (per-tile blocks into `scratch`) followed by the block merge into dst.
 template <typename T>
 static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, void *scratch)
@@ -91,17 +102,37 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
                                                               reinterpret_cast<T *>(scratch));
         });
     } else {
-        const int CL = mode == 1 ? 1 : split_for(p, N);
-        const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
         const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
+        // FP32 with edge-8 tiles: the kernel with the block geometry fixed at compile time
+        const bool fast = std::is_same<T, float>::value && p->P <= 10 && p->tg.T[0] == 8 && p->tg.T[1] == 8 &&
+                          p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4);
+        const int CL = mode == 1 ? 1 : fast ? split_fast(p, N) : split_for(p, N);
+        const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
         SE_DISPATCH_P(p->P, nu, {
-            auto kern = k_spread_cl<T, PP, NN>;
-            cudaError_t e = allow_smem(kern, sm);
-            if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
-            e = launch_pdl(kern, dim3(unsigned(nt * CL)), dim3(kThreads), sm, p->stream, unsigned(CL), p->tg,
-                           (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
-                           reinterpret_cast<T *>(scratch));
-            if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+            bool done = false;
+            if constexpr (std::is_same<T, float>::value && PP <= 10) {
+                if (fast) {
+                    auto kern = k_spread_cl_f32fast<PP, NN>;
+                    const size_t smf = std::max(sm, spread_fast_smem<PP>());
+                    cudaError_t e = allow_smem(kern, smf);
+                    if (e == cudaSuccess) e = prefer_shared(kern);
+                    if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+                    e = launch_pdl(kern, dim3(unsigned(nt * CL)), dim3(kThreads), smf, p->stream, unsigned(CL),
+                                   p->tg, (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
+                                   reinterpret_cast<float *>(scratch));
+                    if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+                    done = true;
+                }
+            }
+            if (!done) {
+                auto kern = k_spread_cl<T, PP, NN>;
+                cudaError_t e = allow_smem(kern, sm);
+                if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
+                e = launch_pdl(kern, dim3(unsigned(nt * CL)), dim3(kThreads), sm, p->stream, unsigned(CL), p->tg,
+                               (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
+                               reinterpret_cast<T *>(scratch));
+                if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+            }
         });
     }
     SE_LAUNCH_CHECK("spread");
@@ -425,11 +456,53 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
     double *part = energy ? p->tile_part : nullptr;
     const T *grid = reinterpret_cast<const T *>(p->grid_out);
     const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
-    // sparsely filled tiles: read the grid directly; otherwise stage each tile's block
-    const bool flat = p->gather_mode != 1;
-    const int split = flat ? 1 : split_for(p, N);
+    // FP32 with edge-8 tiles (default mode): the tile-staged kernel; mode 2 reads the
+    // grid directly, mode 1 is the generic staged kernel
+    // with P = 8 or 10 and at least 64 particles per tile on average, and mode 2 reads
+    // the grid directly (the default otherwise); mode 1 is the generic staged kernel
+    const bool fast = std::is_same<T, float>::value && p->gather_mode <= 0 && (p->P == 8 || p->P == 10) &&
+                      p->tg.T[0] == 8 && p->tg.T[1] == 8 && p->tg.T[2] == 8 &&
+                      p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) && N >= 64 * int64_t(nt);
+    const bool flat = !fast && p->gather_mode != 1;
+    const int split = flat || fast ? 1 : split_for(p, N);
     int nparts = nt * split;
-    if (flat) {
+    if (fast) {
+        // work list: chunks of at most kGatherChunk particles of one tile
+        const unsigned ncta = unsigned(nt + N / kGatherChunk + 1);
+        if (size_t(ncta) > p->chunk_map_elems) return fail(SE_EINVAL, "gathering work list exceeds the reserve");
+        const size_t msm = sizeof(int) * size_t(nt + 1);
+        const bool staged = msm <= 160 * 1024;
+        cudaError_t e = allow_smem(k_chunk_map, staged ? msm : 0);
+        if (e != cudaSuccess) return cuda_fail(e, "chunk map smem attribute");
+        e = launch_pdl(k_chunk_map, dim3(1), dim3(1024), staged ? msm : 0, p->stream, 1, nt, (const int *)p->tile_off,
+                       kGatherChunk, p->chunk_map, p->counters + 2, staged);
+        if (e != cudaSuccess) return cuda_fail(e, "chunk map launch");
+        SE_LAUNCH_CHECK("chunk_map");
+        SE_DISPATCH_P(p->P, nu, {
+            if constexpr (std::is_same<T, float>::value && PP <= 10) {
+                if (grad) {
+                    auto kern = k_gather_tile_f32fast<PP, NN, true>;
+                    const size_t sm = gather_fast_smem<PP, true>();
+                    if ((e = allow_smem(kern, sm)) == cudaSuccess) e = prefer_shared(kern);
+                    if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                    e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
+                                   (const int2 *)p->chunk_map, (const int *)(p->counters + 2), (const int *)p->tile_off,
+                                   fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, F, part, energy,
+                                   p->counters + 1, float(p->inv_h), self);
+                } else {
+                    auto kern = k_gather_tile_f32fast<PP, NN, false>;
+                    const size_t sm = gather_fast_smem<PP, false>();
+                    if ((e = allow_smem(kern, sm)) == cudaSuccess) e = prefer_shared(kern);
+                    if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                    e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
+                                   (const int2 *)p->chunk_map, (const int *)(p->counters + 2), (const int *)p->tile_off,
+                                   fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, (float *)nullptr, part,
+                                   energy, p->counters + 1, float(p->inv_h), self);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "gather launch");
+            }
+        });
+    } else if (flat) {
         SE_DISPATCH_P(p->P, nu, {
             constexpr int G = LaneMap<PP>::G;
             const int64_t per_cta = int64_t(kThreads / 32) * G;

@@ -644,6 +644,270 @@ k_spread_cl(TileGeom tg, const int *__restrict__ off, const typename Vec4<T>::ty
     spread_cl_tile<T, P, NU>(tg, tile, beg, end, fq, ia, g, wa, scratch + size_t(tile) * tg.blk);
 }
 
+// ---------------------------------------------------------------- FP32 gridding, edge-8 tiles
+// The per-tile work of k_spread_cl for FP32 plans whose gridding tiles have
+// edge 8 along every axis (the default): the block geometry is known at
+// compile time, B = 7 + P per axis with the row pitch of gridding_pitch, so
+// every shared-memory update addresses [base + constant].  Per particle a warp
+//  - reads its coordinate along the lane's axis, q s and the block offset from
+//    a per-warp staging row (written once per 32 particles),
+//  - evaluates W at the 3P stencil points (lane j < 3P: axis j / P, point
+//    j mod P) into one of two per-warp rows (double-buffered: one __syncwarp
+//    per particle orders writes and reads),
+//  - forms w_x w_y q s for its NE (x, y) points and adds w_x w_y w_z q s,
+//    rounded to an integer, at the P points along z.
+// The rounding is one fused multiply-add with the bias 1.5 * 2^23: for
+// |v| < 2^22 the sum's low mantissa bits hold round-to-nearest-even(v), and
+// subtracting the bias's bit pattern leaves that integer (no float-to-integer
+// conversion instruction, which issues at a quarter of the FMA rate; the
+// bias is exact for v in [-2^22, 2^23)).  The scale s = 2^e is therefore
+// bounded twice: s sum|q| <= kFixMax as before (no block value overflows), and
+// s max|q| <= 0.99999 2^22 (no single update leaves the exact range of the
+// bias; the window is at most 1 + 1e-6).
+template <int P>
+struct FastGeom {
+    static constexpr int B = 7 + P;                                   // extended block edge, tile edge 8
+    static constexpr int PITCH = gridding_pitch(B, P, 4);
+    static constexpr int PLANE = PITCH * B;
+    static constexpr int SBLK = PLANE * B;
+    static constexpr int NE = (P * P + 31) / 32;                      // (x, y) points per lane
+    static constexpr int WROW = 32;                                   // window row: one value per lane
+};
+
+__device__ __forceinline__ int fix_add_bits(float wxy, float wz)
+{
+    return __float_as_int(fmaf(wxy, wz, 12582912.0f)) - 0x4B400000;
+}
+
+// The particle loop of spread_tile_f32_fast for one window kind (PKB or
+// Gaussian, fixed at compile time): the warp's particles first, first + stride,
+// ... below end, 32 per round.  Each lane stages one record of the round in
+// shared memory (and loads its record of the next round meanwhile); then every
+// lane evaluates the window at stencil point (axis min(lane / P, 3), point
+// lane mod P) -- lanes past 3P compute values nobody reads, which keeps the
+// warp free of divergent branches -- into one of two rows of 32, and adds the
+// particle's P^3 integer updates.
+template <int P, int NU, bool PKB>
+__device__ __forceinline__ void spread_rounds_f32(int *blk, float *w2, float4 *ps, int *bs, int first, int end,
+                                                  int stride, const int o[3], const float4 *__restrict__ fq,
+                                                  const int4 *__restrict__ ia, const float *__restrict__ g,
+                                                  float alpha, const LaneCoef<float, NU> &cf, int lane, int ax,
+                                                  int kk, const int *poff, float scale)
+{
+    using G = FastGeom<P>;
+    int pdx[G::NE], pdy[G::NE];
+#pragma unroll
+    for (int e = 0; e < G::NE; ++e) {
+        const int pp = lane + 32 * e < P * P ? lane + 32 * e : 0;
+        pdx[e] = pp % P;
+        pdy[e] = pp / P;
+    }
+    constexpr bool kFull = (P * P) % 32 == 0;                          // every lane holds NE points
+    auto body = [&](int i, float *w) {
+        const float t = reinterpret_cast<const float *>(ps + i)[ax];
+        float v, dv;
+        win_eval<float, P, NU, false>(PKB ? SE_WIN_PKB : SE_WIN_GAUSSIAN, alpha, cf, t, kk, v, dv);
+        w[lane] = v;
+        __syncwarp();
+        const float qs = reinterpret_cast<const float *>(ps + i)[3];
+        int *base = blk + bs[i];
+        float wz[P];
+        if constexpr (P % 4 == 0) {
+#pragma unroll
+            for (int k = 0; k < P; k += 4) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(w + 2 * P + k);
+                wz[k] = t4.x; wz[k + 1] = t4.y; wz[k + 2] = t4.z; wz[k + 3] = t4.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < P; k += 2) {
+                const float2 t2 = *reinterpret_cast<const float2 *>(w + 2 * P + k);
+                wz[k] = t2.x; wz[k + 1] = t2.y;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < G::NE; ++e) {
+            if (kFull || lane + 32 * e < P * P) {
+                const float wxy = w[pdx[e]] * w[P + pdy[e]] * qs;
+                int *pe = base + poff[e];
+#pragma unroll
+                for (int dz = 0; dz < P; ++dz) atomicAdd(pe + dz * G::PLANE, fix_add_bits(wxy, wz[dz]));
+            }
+        }
+    };
+    int pl = first + lane * stride;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 a = make_int4(0, 0, 0, 0);
+    if (pl < end) {
+        r = fq[pl];
+        a = ia[pl];
+        if (g) r.w = g[a.x];
+    }
+    for (int p0 = first; p0 < end; p0 += 32 * stride) {
+        if (pl < end) {
+            ps[lane] = make_float4(r.x, r.y, r.z, r.w * scale);
+            bs[lane] = ((a.w - o[2]) * G::B + (a.z - o[1])) * G::PITCH + (a.y - o[0]);
+        }
+        pl += 32 * stride;                                   // the next round's record, loaded meanwhile
+        if (pl < end) {
+            r = fq[pl];
+            a = ia[pl];
+            if (g) r.w = g[a.x];
+        }
+        __syncwarp();
+        const int cnt = min(32, (end - p0 + stride - 1) / stride);
+        int i = 0;
+        for (; i + 1 < cnt; i += 2) {
+            body(i, w2);
+            body(i + 1, w2 + 32);
+        }
+        if (i < cnt) body(i, w2);
+        __syncwarp();                                        // the staging rows are rewritten next round
+    }
+}
+
+template <int P, int NU>
+__device__ __forceinline__ void spread_tile_f32_fast(int tile, const TileGeom &tg, int beg, int end,
+                                                     const float4 *__restrict__ fq, const int4 *__restrict__ ia,
+                                                     const float *__restrict__ g, const WindowArgs<float> &wa,
+                                                     float *__restrict__ dst)
+{
+    using G = FastGeom<P>;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = int(cluster.num_blocks()), rank = int(cluster.block_rank());
+    constexpr int NW = kThreads / 32;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int *blk = reinterpret_cast<int *>(smraw);
+    float *wrow = reinterpret_cast<float *>(blk + align_up_elems<int>(G::SBLK));   // [warp][2][WROW]
+    static_assert(3 * P <= 32, "the fast gridding kernel serves P <= 10");
+    float4 *pst = reinterpret_cast<float4 *>(wrow + NW * 2 * G::WROW);              // [warp][32] (t_x, t_y, t_z, q s)
+    int *bst = reinterpret_cast<int *>(pst + NW * 32);                               // [warp][32] block offsets
+    __shared__ float qsum[NW], qmax[NW];
+    __shared__ float sscale[2];
+    zero_smem(blk, G::SBLK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        float aq = 0.f, mq = 0.f;
+        for (int p = beg + threadIdx.x; p < end; p += blockDim.x) {
+            const float a = fabsf(g ? g[ia[p].x] : fq[p].w);
+            aq += a;
+            mq = fmaxf(mq, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            aq += __shfl_xor_sync(0xffffffffu, aq, o);
+            mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+        }
+        if (lane == 0) {
+            qsum[warp] = aq;
+            qmax[warp] = mq;
+        }
+    }
+    const int kk = lane % P;
+    LaneCoef<float, NU> cf;
+    if (wa.kind == SE_WIN_PKB) cf.load(wa, P, kk);
+    int o[3];
+    tile_origin(tg, tile, o);
+    int poff[G::NE];
+    bool pv[G::NE];
+#pragma unroll
+    for (int e = 0; e < G::NE; ++e) {
+        const int pp = lane + 32 * e;
+        pv[e] = pp < P * P;
+        poff[e] = pv[e] ? (pp / P) * G::PITCH + pp % P : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bound = 0.f, mx = 0.f;
+        for (int i = 0; i < NW; ++i) {
+            bound += qsum[i];
+            mx = fmaxf(mx, qmax[i]);
+        }
+        int e2 = bound > 0.f ? Fix<float>::scale_exp(bound) : 0;
+        if (mx > 0.f) {
+            int E;
+            const float m = frexpf(mx, &E);
+            // s max|q| <= 0.99999 2^22: the product of three window values (each at
+            // most 1 + 1e-6) and its float roundings stay below 2^22 in magnitude
+            e2 = min(e2, (m <= 0.99999f ? 22 : 21) - E);
+        }
+        e2 = max(-Fix<float>::kMaxExp, min(Fix<float>::kMaxExp, e2));
+        sscale[0] = ldexpf(1.0f, e2);
+        sscale[1] = ldexpf(1.0f, -e2);
+    }
+    __syncthreads();
+    const float scale = sscale[0], inv_scale = sscale[1];
+    float *w2 = wrow + warp * 2 * G::WROW;
+    float4 *ps = pst + warp * 32;
+    int *bs = bst + warp * 32;
+    const int stride = CL * NW, first = beg + rank * NW + warp;
+    const int axc = min(lane / P, 3);
+    if (wa.kind == SE_WIN_PKB)
+        spread_rounds_f32<P, NU, true>(blk, w2, ps, bs, first, end, stride, o, fq, ia, g, wa.alpha, cf, lane, axc,
+                                       kk, poff, scale);
+    else
+        spread_rounds_f32<P, NU, false>(blk, w2, ps, bs, first, end, stride, o, fq, ia, g, wa.alpha, cf, lane, axc,
+                                        kk, poff, scale);
+    cluster.sync();                                          // every copy complete and visible to the cluster
+    // the cluster's copies summed row by row (row r = z B + y at r PITCH in shared
+    // memory, r B in the compact block); CTA `rank` writes rows [rank R / CL, (rank + 1) R / CL)
+    const int *src[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
+    constexpr int R = G::B * G::B, RPW = 32 / G::B;
+    const int sub = lane / G::B, x = lane - sub * G::B;
+    const int r0 = rank * R / CL, r1 = (rank + 1) * R / CL;
+    if (sub < RPW)
+        for (int r = r0 + warp * RPW + sub; r < r1; r += NW * RPW) {
+            const int si = r * G::PITCH + x;
+            int v = src[0][si];
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (j < CL) v += src[j][si];
+            dst[r * G::B + x] = float(v) * inv_scale;
+        }
+    cluster.sync();                                          // no CTA leaves while its block is still read
+}
+
+// Dynamic shared memory of spread_tile_f32_fast.
+template <int P>
+__host__ __device__ constexpr size_t spread_fast_smem()
+{
+    using G = FastGeom<P>;
+    return (((size_t(G::SBLK) + 31) & ~size_t(31)) + size_t(kThreads / 32) * (2 * G::WROW + 32 * 4 + 32)) * 4;
+}
+
+// The same for a support P known at run time (P <= 10, even).
+static inline size_t spread_fast_smem_rt(int P)
+{
+    switch (P) {
+    case 2: return spread_fast_smem<2>();
+    case 4: return spread_fast_smem<4>();
+    case 6: return spread_fast_smem<6>();
+    case 8: return spread_fast_smem<8>();
+    default: return spread_fast_smem<10>();
+    }
+}
+
+// FP32 gridding for edge-8 tiles: spread_tile_f32_fast, or the generic tile
+// code (float atomics) for a tile of more than Fix<float>::kFixTile particles.
+template <int P, int NU>
+__global__ void __launch_bounds__(kThreads, P == 8 ? 5 : 4)
+k_spread_cl_f32fast(TileGeom tg, const int *__restrict__ off, const float4 *__restrict__ fq,
+                    const int4 *__restrict__ ia, const float *__restrict__ g, WindowArgs<float> wa,
+                    float *__restrict__ scratch)
+{
+    pdl_wait();
+    const int tile = blockIdx.x / int(cooperative_groups::this_cluster().num_blocks());
+    const int beg = off[tile], end = off[tile + 1];
+    if (beg == end) return;                               // the same for every CTA of the cluster
+    float *dst = scratch + size_t(tile) * tg.blk;
+    if (end - beg > Fix<float>::kFixTile)
+        spread_cl_tile<float, P, NU>(tg, tile, beg, end, fq, ia, g, wa, dst);
+    else
+        spread_tile_f32_fast<P, NU>(tile, tg, beg, end, fq, ia, g, wa, dst);
+}
+
 // Sum of the tile blocks covering each grid point, in a fixed order, written
 // to the forward-FFT input.  One CTA per tile writes that tile's T0 x T1 x T2
 // points (threads over x, y; loop over z); each point adds the blocks of the
@@ -1433,6 +1697,276 @@ k_gather_flat(int64_t N, TileGeom tg, const typename Vec4<T>::type *__restrict__
         cta_energy_partial(esum, part + blockIdx.x);
         finish_energy(part, gridDim.x, energy, done);
     }
+}
+
+// Sums of four values over the warp with six shuffles: the first two levels
+// exchange half of the values (a transposing butterfly), the last three sum
+// the one value left per lane.  Afterwards lanes 0-7 hold sum a, 8-15 sum b,
+// 16-23 sum c and 24-31 sum d.
+__device__ __forceinline__ float warp_sum4(float a, float b, float c, float d, int lane)
+{
+    const bool h16 = lane & 16, h8 = lane & 8;
+    float k0 = h16 ? c : a, k1 = h16 ? d : b;
+    k0 += __shfl_xor_sync(0xffffffffu, h16 ? a : c, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h16 ? b : d, 16);
+    float k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+// Work list of the tile-staged gathering: tile t is cut into chunks of at most
+// C consecutive sorted particles, and chunk k of the list covers particles
+// [map[k].y, min(map[k].y + C, off[t + 1])) of tile t = map[k].x; *total
+// receives the number of chunks (empty tiles have none).  One CTA: the tile
+// offsets are read once, coalesced, into shared memory when they fit
+// (staged = true: (nt + 1) ints of dynamic shared memory); each thread counts
+// the chunks of a contiguous run of tiles, the run counts are scanned with
+// warp shuffles, then each thread writes its run's chunks.
+static __global__ void __launch_bounds__(1024) k_chunk_map(int nt, const int *__restrict__ off, int C,
+                                                           int2 *__restrict__ map, int *__restrict__ total,
+                                                           bool staged)
+{
+    pdl_wait();
+    extern __shared__ int soff_raw[];
+    __shared__ int wsum[32];
+    const int *so = off;
+    if (staged) {
+        for (int i = threadIdx.x; i <= nt; i += blockDim.x) soff_raw[i] = off[i];
+        __syncthreads();
+        so = soff_raw;
+    }
+    const int E = (nt + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int loc = 0;
+    for (int i = 0; i < E && b + i < nt; ++i) loc += (so[b + i + 1] - so[b + i] + C - 1) / C;
+    int v = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int k = v - loc + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = 0; i < E && b + i < nt; ++i) {
+        const int t = b + i;
+        for (int p = so[t]; p < so[t + 1]; p += C) map[k++] = make_int2(t, p);
+    }
+    if (threadIdx.x == blockDim.x - 1) *total = k;
+}
+
+// The particle loop of k_gather_tile_f32fast for one window kind: the warp's
+// particles first, first + stride, ... below end, 32 per round (records staged
+// in shared memory, the next round's loaded meanwhile).  Every lane evaluates
+// W (and W') at stencil point (axis min(lane / P, 3), point lane mod P) into
+// a row of 32 (64) -- lanes past 3P compute values nobody reads, so the warp
+// never diverges.  Returns the lane's share of sum 1/2 q_m phi_m.
+template <int P, int NU, bool GRAD, bool PKB>
+__device__ __forceinline__ double gather_rounds_f32(const float *blk, float *w2, float4 *ps, int *bs, float4 *rs,
+                                                    int first, int end, int stride, const int o[3],
+                                                    const float4 *__restrict__ fq, const int4 *__restrict__ ia,
+                                                    float alpha, const LaneCoef<float, NU> &cf, int lane, int ax,
+                                                    int kk, const int *poff, float *__restrict__ phi,
+                                                    float *__restrict__ F, float inv_h, float self_coef)
+{
+    using G = FastGeom<P>;
+    constexpr int WR = GRAD ? 64 : 32;
+    constexpr int D = 32;                                   // offset of W' in a row
+    int pdx[G::NE], pdy[G::NE];
+#pragma unroll
+    for (int e = 0; e < G::NE; ++e) {
+        const int pp = lane + 32 * e < P * P ? lane + 32 * e : 0;
+        pdx[e] = pp % P;
+        pdy[e] = pp / P;
+    }
+    constexpr bool kFull = (P * P) % 32 == 0;
+    auto body = [&](int i, float *w) {
+        const float t = reinterpret_cast<const float *>(ps + i)[ax];
+        float val, dval = 0.f;
+        win_eval<float, P, NU, GRAD>(PKB ? SE_WIN_PKB : SE_WIN_GAUSSIAN, alpha, cf, t, kk, val, dval);
+        w[lane] = val;
+        if (GRAD) w[D + lane] = dval;
+        __syncwarp();
+        const float *base = blk + bs[i];
+        float wz[P], dwz[P];
+#pragma unroll
+        for (int k = 0; k < P; k += 2) {
+            const float2 t2 = *reinterpret_cast<const float2 *>(w + 2 * P + k);
+            wz[k] = t2.x;
+            wz[k + 1] = t2.y;
+            if (GRAD) {
+                const float2 d2 = *reinterpret_cast<const float2 *>(w + D + 2 * P + k);
+                dwz[k] = d2.x;
+                dwz[k + 1] = d2.y;
+            }
+        }
+        float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int e = 0; e < G::NE; ++e) {
+            if (kFull || lane + 32 * e < P * P) {
+                const float *pe = base + poff[e];
+                float tt = 0.f, tz = 0.f;
+#pragma unroll
+                for (int dz = 0; dz < P; ++dz) {
+                    const float h = pe[dz * G::PLANE];
+                    tt = fmaf(wz[dz], h, tt);
+                    if (GRAD) tz = fmaf(dwz[dz], h, tz);
+                }
+                const float wx = w[pdx[e]], wy = w[P + pdy[e]];
+                const float wxy = wx * wy;
+                sp = fmaf(wxy, tt, sp);
+                if (GRAD) {
+                    sz = fmaf(wxy, tz, sz);
+                    sx = fmaf(w[D + pdx[e]] * wy, tt, sx);
+                    sy = fmaf(wx * w[D + P + pdy[e]], tt, sy);
+                }
+            }
+        }
+        if (GRAD) {
+            const float k = warp_sum4(sp, sx, sy, sz, lane);
+            if ((lane & 7) == 0) reinterpret_cast<float *>(rs + i)[lane >> 3] = k;
+        } else {
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o2);
+            if (lane == 0) rs[i].x = sp;
+        }
+    };
+    double esum = 0.0;
+    int pl = first + lane * stride;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 a = make_int4(0, 0, 0, 0);
+    if (pl < end) {
+        r = fq[pl];
+        a = ia[pl];
+    }
+    for (int p0 = first; p0 < end; p0 += 32 * stride) {
+        const bool mine = pl < end;
+        const float qv = r.w;
+        const int m = a.x;
+        if (mine) {
+            ps[lane] = r;
+            bs[lane] = ((a.w - o[2]) * G::B + (a.z - o[1])) * G::PITCH + (a.y - o[0]);
+        }
+        pl += 32 * stride;                                   // the next round's record, loaded meanwhile
+        if (pl < end) {
+            r = fq[pl];
+            a = ia[pl];
+        }
+        __syncwarp();
+        const int cnt = min(32, (end - p0 + stride - 1) / stride);
+        int i = 0;
+        for (; i + 1 < cnt; i += 2) {
+            body(i, w2);
+            body(i + 1, w2 + WR);
+        }
+        if (i < cnt) body(i, w2);
+        __syncwarp();                                        // the round's results are in rs
+        if (mine) {
+            const float4 rr = rs[lane];
+            const float phv = rr.x + self_coef * qv;
+            if (phi) phi[m] = phv;
+            if (GRAD && F) {
+                const float sc = -qv * inv_h;
+                F[3 * int64_t(m)] = sc * rr.y;
+                F[3 * int64_t(m) + 1] = sc * rr.z;
+                F[3 * int64_t(m) + 2] = sc * rr.w;
+            }
+            esum += 0.5 * double(qv) * double(phv);
+        }
+    }
+    return esum;
+}
+
+// FP32 gathering for edge-8 tiles (Eq. complete_integral and, with GRAD,
+// Eq. force-method-1), the transpose of spread_tile_f32_fast: CTA (tile,
+// chunk) stages the tile's extended block in shared memory with the row pitch
+// of the gridding kernel and takes one chunk of at most kGatherChunk of the
+// tile's particles from the work list of k_chunk_map (dense tiles spread over
+// many CTAs, sparse ones take one).  Per particle a warp evaluates W (and W')
+// at the 3P stencil points into a double-buffered row; each lane reads its NE
+// (x, y) columns of the
+// block along z -- one bank wavefront per warp load -- and forms
+// sum_z W_z H and sum_z W'_z H, weights them with W_x W_y (and W'_x W_y,
+// W_x W'_y), and the warp sums phi and the three gradient factors.  Results of
+// 32 particles are written together to their original positions: phi_m
+// (+ self term), F_m = -q_m grad phi_m, and 1/2 q_m phi_m into the CTA's FP64
+// energy partial (the last CTA sums the partials).
+template <int P, int NU, bool GRAD>
+__global__ void __launch_bounds__(kThreads, P <= 8 ? 4 : 3)
+k_gather_tile_f32fast(TileGeom tg, const int2 *__restrict__ map, const int *__restrict__ nchunk,
+                      const int *__restrict__ off, const float4 *__restrict__ fq, const int4 *__restrict__ ia,
+                      WindowArgs<float> wa, const float *__restrict__ grid, GridView v, float *__restrict__ phi,
+                      float *__restrict__ F, double *__restrict__ part, double *energy, int *done, float inv_h,
+                      float self_coef)
+{
+    using G = FastGeom<P>;
+    constexpr int NW = kThreads / 32;
+    constexpr int WR = GRAD ? 64 : 32;
+    static_assert(3 * P <= 32, "the fast gathering kernel serves P <= 10");
+    pdl_wait();
+    double esum = 0.0;
+    if (int(blockIdx.x) < *nchunk) {                        // the launch covers the largest possible list
+        const int2 ck = map[blockIdx.x];
+        const int tile = ck.x, beg = ck.y, end = min(ck.y + kGatherChunk, off[tile + 1]);
+        extern __shared__ __align__(16) unsigned char smraw[];
+        float *blk = reinterpret_cast<float *>(smraw);
+        float *wrow = blk + align_up_elems<float>(G::SBLK);                        // [warp][2][WR]
+        float4 *pst = reinterpret_cast<float4 *>(wrow + NW * 2 * WR);              // [warp][32] (t_x, t_y, t_z, q)
+        int *bst = reinterpret_cast<int *>(pst + NW * 32);                         // [warp][32] block offsets
+        float4 *rst = reinterpret_cast<float4 *>(bst + NW * 32);                   // [warp][32] (phi, g_x, g_y, g_z)
+        int o[3];
+        tile_origin(tg, tile, o);
+        stage_block<float>(tg, o, grid, v, blk);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int kk = lane % P;
+        LaneCoef<float, NU> cf;
+        if (wa.kind == SE_WIN_PKB) cf.load(wa, P, kk);
+        int poff[G::NE];
+#pragma unroll
+        for (int e = 0; e < G::NE; ++e) {
+            const int pp = lane + 32 * e < P * P ? lane + 32 * e : 0;
+            poff[e] = (pp / P) * G::PITCH + pp % P;
+        }
+        float *w2 = wrow + warp * 2 * WR;
+        float4 *ps = pst + warp * 32;
+        int *bs = bst + warp * 32;
+        float4 *rs = rst + warp * 32;
+        cp_async_wait_all();
+        __syncthreads();
+        const int stride = NW, first = beg + warp;
+        const int axc = min(lane / P, 3);
+        if (wa.kind == SE_WIN_PKB)
+            esum = gather_rounds_f32<P, NU, GRAD, true>(blk, w2, ps, bs, rs, first, end, stride, o, fq, ia, wa.alpha,
+                                                        cf, lane, axc, kk, poff, phi, F, inv_h, self_coef);
+        else
+            esum = gather_rounds_f32<P, NU, GRAD, false>(blk, w2, ps, bs, rs, first, end, stride, o, fq, ia, wa.alpha,
+                                                         cf, lane, axc, kk, poff, phi, F, inv_h, self_coef);
+    }
+    if (part) {
+        cta_energy_partial(esum, part + blockIdx.x);
+        finish_energy(part, gridDim.x, energy, done);
+    }
+}
+
+// Dynamic shared memory of k_gather_tile_f32fast.
+template <int P, bool GRAD>
+__host__ __device__ constexpr size_t gather_fast_smem()
+{
+    using G = FastGeom<P>;
+    constexpr int WR = GRAD ? 64 : 32;
+    return (((size_t(G::SBLK) + 31) & ~size_t(31)) + size_t(kThreads / 32) * (2 * WR + 32 * 4 + 32 + 32 * 4)) * 4;
 }
 
 // Gathering for method 2 of Sec. 7.2: phi from H~ and the three components of

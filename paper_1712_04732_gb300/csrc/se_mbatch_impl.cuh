@@ -138,6 +138,9 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
             scr += int64_t(al32(size_t(nt) * p->tg.blk));
             J = std::max(J, overlap_tiles(p->tg));
             sm = std::max(sm, (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * c.P) * sizeof(T));
+            // FP32 systems with edge-8 tiles run the single-system kernel's tile code
+            if (sizeof(T) == 4 && c.P <= 10 && p->tg.T[0] == 8 && p->tg.T[1] == 8 && p->tg.T[2] == 8)
+                sm = std::max(sm, spread_fast_smem_rt(c.P));
             c.particles += s.n;
         }
         c.ntiles = tile - c.tile_begin;

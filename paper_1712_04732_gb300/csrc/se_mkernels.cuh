@@ -149,6 +149,15 @@ k_mspread_cl(const SysDesc<T> *__restrict__ sd, const int *__restrict__ tile_sys
         base = d.scr0 + int64_t(lt) * d.tg.blk;
     }
     __syncthreads();
+    if constexpr (std::is_same<T, float>::value && P <= 10) {
+        // the FP32 tile code of the single-system kernel for edge-8 tiles (the
+        // launch reserves its shared memory for such classes): the same blocks
+        if (tg.T[0] == 8 && tg.T[1] == 8 && tg.T[2] == 8 && tg.pitch == FastGeom<P>::PITCH &&
+            end - beg <= Fix<float>::kFixTile) {
+            spread_tile_f32_fast<P, NU>(lt, tg, beg, end, fq, ia, nullptr, wa, scratch + base);
+            return;
+        }
+    }
     spread_cl_tile<T, P, NU>(tg, lt, beg, end, fq, ia, nullptr, wa, scratch + base);
 }
 

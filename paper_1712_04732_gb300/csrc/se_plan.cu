@@ -666,31 +666,7 @@ se_status plan_set_fft_stream(se_plan_s *p)
 
 // ------------------------------------------------------------ build / reserve / release
 
-// Row pitch (elements) of a block in shared memory: the smallest pitch >= B0
-// for which the gridding kernel's access pattern -- rows of P consecutive lanes
-// stacked 32 / P deep -- touches the fewest bank wavefronts.
-static int choose_pitch(int B0, int P, int elem)
-{
-    int best = B0, best_cost = 1 << 30;
-    for (int pitch = B0; pitch < B0 + 32; ++pitch) {
-        int cost = 0;
-        // a warp instruction moves 32 elements; 8-byte elements go out as two half-warps
-        const int per_wave = elem == 8 ? 16 : 32;
-        for (int h = 0; h < 32 / per_wave; ++h) {
-            int banks[32] = {0};
-            for (int l = h * per_wave; l < (h + 1) * per_wave; ++l) {
-                const int r = l / P, c = l % P;
-                const long word = (long(r) * pitch + c) * (elem / 4);
-                for (int w = 0; w < elem / 4; ++w) banks[(word + w) % 32]++;
-            }
-            int worst = 0;
-            for (int b = 0; b < 32; ++b) worst = std::max(worst, banks[b]);
-            cost += worst;
-        }
-        if (cost < best_cost) { best_cost = cost; best = pitch; }
-    }
-    return best;
-}
+static int choose_pitch(int B0, int P, int elem) { return gridding_pitch(B0, P, elem); }
 
 static int choose_tile(int n, bool periodic, int pref)
 {
@@ -832,6 +808,15 @@ se_status plan_reserve(se_plan_s *p, int64_t n)
         if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * nparts)) != SE_OK) return st;
         p->tile_part_elems = nparts;
     }
+    // chunk list of the tile-staged gathering: at most one chunk per tile plus one
+    // per kGatherChunk particles
+    const size_t nchunk = size_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2] + size_t(cap / kGatherChunk) + 1;
+    if (nchunk > p->chunk_map_elems) {
+        dev_free(p, (void **)&p->chunk_map);
+        p->chunk_map_elems = 0;
+        if ((st = dev_alloc(p, (void **)&p->chunk_map, sizeof(int2) * nchunk)) != SE_OK) return st;
+        p->chunk_map_elems = nchunk;
+    }
     p->cap = cap;
     return SE_OK;
 }
@@ -871,7 +856,7 @@ void plan_release(se_plan_s *p)
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
                      (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
                      (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2, &p->spec_d, &p->U_d, &p->Z_d,
-                     &p->grid_d, &p->ztw};
+                     &p->grid_d, &p->ztw, (void **)&p->chunk_map};
     for (void **b : bufs) dev_free(p, b);
 }
 

@@ -44,7 +44,7 @@ def test_batch_matches_standalone_plans(autotune):
     for i, (xs, qs, D) in enumerate(sysl):
         n = len(qs)
         info = b.system_info(i)
-        plan = se.Plan(D, 1.0, specs[i][3], info["M"], info["P"], "pkb", dtype=torch.float32)
+        plan = se.Plan(D, 1.0, specs[i][3], info["M"], info["P"], "pkb", dtype=torch.float32, aft_eps=1e-5 / 4)
         Fp, pp, Ep = plan.force(xt[off:off + n], qt[off:off + n], energy=True)
         torch.cuda.synchronize()
         assert _rel(phi[off:off + n].cpu().numpy(), pp.cpu().numpy()) < 1e-5
@@ -57,9 +57,10 @@ def test_batch_matches_standalone_plans(autotune):
 
 
 def test_batch_parameters_meet_the_tolerance():
-    """M_i, P_i from Sec. 6 for eps_rms = 1e-5 B_i: the potential of each system
-    against the direct sums (3P k-sum, 2P closed forms), rms error within
-    1e-5 B_i and relative error within 1e-5."""
+    """Without autotuning, M_i and P_i + 2 from Sec. 6 for eps_rms = 1e-5 B_i (the
+    AFT at a quarter of it): the potential and forces of each system against
+    the direct sums (3P k-sum, 2P closed forms), rms error within 1e-5 B_i and
+    relative errors within 1e-5."""
     import paper_1712_04732_gb300 as se
     sysl, specs, x, q = _systems(6, seed=9)
     b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False)
@@ -71,11 +72,38 @@ def test_batch_parameters_meet_the_tolerance():
     for i, (xs, qs, D) in enumerate(sysl):
         n = len(qs)
         idx = np.arange(0, n, max(1, n // 200))
-        pa, _ = E.fourier(D, xs, qs, 1.0, specs[i][3], xt=xs[idx])
+        pa, ga = E.fourier(D, xs, qs, 1.0, specs[i][3], xt=xs[idx])
         ph = phi[off:off + n].cpu().numpy()[idx]
         assert _rel(ph, pa) < 1e-5
+        assert _rel(F[off:off + n].cpu().numpy()[idx], -qs[idx, None] * ga) < 1e-5
         B = prm.scale_B(prm.q_sum_sq(qs), specs[i][3], 1.0)
         assert float(np.sqrt(np.mean((ph - pa) ** 2))) <= 1e-5 * B
+        off += n
+    b.close()
+
+
+def test_autotuned_parameters_meet_the_tolerance_for_phi_and_F():
+    """The autotuner picks (M, P) per system from candidates around the Sec. 6
+    rule by errors measured against an FP64 reference on the first call's
+    inputs (each within eps_rel / 2): every system's phi and F then meet 1e-5
+    against the direct sums (3P k-sum, 2P closed forms), and the errors the
+    tuner reports agree with them."""
+    import paper_1712_04732_gb300 as se
+    sysl, specs, x, q = _systems(6, seed=9)
+    b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=True)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+    F, phi, _ = b.force(xt, qt)
+    torch.cuda.synchronize()
+    off = 0
+    for i, (xs, qs, D) in enumerate(sysl):
+        n = len(qs)
+        idx = np.arange(0, n, max(1, n // 200))
+        pa, ga = E.fourier(D, xs, qs, 1.0, specs[i][3], xt=xs[idx])
+        ep, ef = b.accuracy(i)
+        assert 0 <= ep <= 0.5e-5 and 0 <= ef <= 0.5e-5
+        assert _rel(phi[off:off + n].cpu().numpy()[idx], pa) < 1e-5
+        assert _rel(F[off:off + n].cpu().numpy()[idx], -qs[idx, None] * ga) < 1e-5
         off += n
     b.close()
 
@@ -97,11 +125,14 @@ def _mixed_systems(n_sys, seed, n_min=300, n_max=4000):
 def test_fused_form_matches_per_system_calls(dtype):
     """The multi-system form (one launch per stage over all systems) against one
     plain se_force per system on the same plans.  The gridding blocks are
-    fixed-point sums (exact in any order), the merge order and the per-particle
-    gathering are the same code, so potentials and forces are bitwise equal,
-    call after call; the energy sums per-CTA partials over the sorted records,
-    whose order inside a tile follows the atomic ranks of the binning, so it
-    agrees to rounding."""
+    fixed-point sums (exact in any order) and the merge order is fixed.  In
+    FP64 the gathering is the same code in both, so potentials and forces are
+    bitwise equal; an FP32 se_force of a system with 64 or more particles per
+    tile takes the tile-staged gathering, which sums the same products in
+    another order, so FP32 agrees to rounding.  Graph replays are bitwise
+    equal; the energy sums per-CTA partials over the sorted records, whose order
+    inside a tile follows the atomic ranks of the binning, so it agrees to
+    rounding."""
     import paper_1712_04732_gb300 as se
     sysl, specs, x, q = _mixed_systems(12, seed=5)
     b = se.Batch(specs, eps_rel=1e-5, dtype=dtype, autotune=False, form="fused")
@@ -115,7 +146,11 @@ def test_fused_form_matches_per_system_calls(dtype):
     torch.cuda.synchronize()
     assert b.form()[0] == "fused"
     assert torch.equal(phi, phi2) and torch.equal(F, F2)
-    assert torch.equal(phi, phie) and torch.equal(F, Fe)
+    if dtype == torch.float64:
+        assert torch.equal(phi, phie) and torch.equal(F, Fe)
+    else:
+        assert _rel(phi.cpu().numpy(), phie.cpu().numpy()) < 1e-6
+        assert _rel(F.cpu().numpy(), Fe.cpu().numpy()) < 1e-6
     rt = 1e-13 if dtype == torch.float64 else 1e-6
     np.testing.assert_allclose(En.cpu().numpy(), Ene.cpu().numpy(), rtol=rt)
     np.testing.assert_allclose(En2.cpu().numpy(), Ene.cpu().numpy(), rtol=rt)
