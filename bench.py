@@ -344,7 +344,7 @@ def rooflines(stage_ms, N, P, nu, peaks, traffic):
     cnt = algorithmic_counts(P, nu)
     fp32 = peaks["fp32_fma"]["value"]
     out = {}
-    for k, kern in (("spread", f"k_spread_cl<float,{P},{nu}>"), ("gather", f"k_gather_flat<float,{P},{nu},true>")):
+    for k, kern in (("spread", f"k_spread_cl_f32fast<{P},{nu}>"), ("gather", f"k_gather_tile_f32fast<{P},{nu},true>")):
         sec = stage_ms[k] * 1e-3
         flop = 2.0 * cnt[k] * N
         ach = flop / sec / 1e12

@@ -37,6 +37,19 @@ static size_t gather_smem(const se_plan_s *p, int nblocks)
     return (nblocks * al32(p->tg.sblk) + size_t(nw) * 32 * 6) * sizeof(T);
 }
 
+// The FP32 tile-staged gathering serves plans with edge-8 tiles, P = 8 or 10,
+// at least 64 particles per tile on average and at most 50000 tiles (its chunk
+// list is built from the tile offsets in shared memory), unless another
+// gathering mode is asked for.
+template <typename T>
+static bool use_tile_gather(const se_plan_s *p, int64_t N)
+{
+    const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
+    return std::is_same<T, float>::value && p->gather_mode <= 0 && (p->P == 8 || p->P == 10) && p->tg.T[0] == 8 &&
+           p->tg.T[1] == 8 && p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) && N >= 64 * nt &&
+           nt <= 50000;
+}
+
 template <typename T>
 se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
 {
@@ -46,14 +59,21 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     BinArgs<T> a = bin_args<T>(p);
     // few tiles: every scatter CTA scans the counts itself (no last-CTA scan)
     const bool local_scan = nt <= kLocalScanTiles;
-    k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
-                                                               p->tile_off, p->counters, !local_scan);
+    const bool staged = !local_scan && nt <= kStagedScanTiles;
+    const size_t csm = staged ? sizeof(int) * size_t(nt + 1) : 0;
+    // the gathering's chunk list, written by whichever CTA scans the counts in shared memory
+    int2 *cmap = use_tile_gather<T>(p, N) && nt <= kStagedScanTiles ? p->chunk_map : nullptr;
+    if ((e = allow_smem(k_bin_count<T>, csm)) != cudaSuccess) return cuda_fail(e, "bin_count smem attribute");
+    k_bin_count<T><<<blocks_for(N, 256), 256, csm, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
+                                                                 p->tile_off, p->counters, !local_scan, staged,
+                                                                 staged ? cmap : nullptr, p->counters + 2);
     SE_LAUNCH_CHECK("bin_count");
     {
         cudaError_t e = launch_pdl(k_bin_scatter<T>, dim3(blocks_for(N, 256)), dim3(256),
                                    local_scan ? sizeof(int) * (nt + 1) : 0, p->stream, 1, a, N, x, q, p->tile_off,
                                    (const int2 *)p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
-                                   p->prt.idx_anc, (const int *)(local_scan ? p->tile_cnt : nullptr), nt);
+                                   p->prt.idx_anc, (const int *)(local_scan ? p->tile_cnt : nullptr), nt,
+                                   local_scan ? cmap : nullptr, p->counters + 2);
         if (e != cudaSuccess) return cuda_fail(e, "bin_scatter launch");
     }
     SE_LAUNCH_CHECK("bin_scatter");
@@ -460,9 +480,7 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
     // grid directly, mode 1 is the generic staged kernel
     // with P = 8 or 10 and at least 64 particles per tile on average, and mode 2 reads
     // the grid directly (the default otherwise); mode 1 is the generic staged kernel
-    const bool fast = std::is_same<T, float>::value && p->gather_mode <= 0 && (p->P == 8 || p->P == 10) &&
-                      p->tg.T[0] == 8 && p->tg.T[1] == 8 && p->tg.T[2] == 8 &&
-                      p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) && N >= 64 * int64_t(nt);
+    const bool fast = use_tile_gather<T>(p, N);
     const bool flat = !fast && p->gather_mode != 1;
     const int split = flat || fast ? 1 : split_for(p, N);
     int nparts = nt * split;
@@ -470,14 +488,15 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
         // work list: chunks of at most kGatherChunk particles of one tile
         const unsigned ncta = unsigned(nt + N / kGatherChunk + 1);
         if (size_t(ncta) > p->chunk_map_elems) return fail(SE_EINVAL, "gathering work list exceeds the reserve");
-        const size_t msm = sizeof(int) * size_t(nt + 1);
-        const bool staged = msm <= 160 * 1024;
-        cudaError_t e = allow_smem(k_chunk_map, staged ? msm : 0);
-        if (e != cudaSuccess) return cuda_fail(e, "chunk map smem attribute");
-        e = launch_pdl(k_chunk_map, dim3(1), dim3(1024), staged ? msm : 0, p->stream, 1, nt, (const int *)p->tile_off,
-                       kGatherChunk, p->chunk_map, p->counters + 2, staged);
-        if (e != cudaSuccess) return cuda_fail(e, "chunk map launch");
-        SE_LAUNCH_CHECK("chunk_map");
+        cudaError_t e = cudaSuccess;
+        if (nt > kStagedScanTiles) {                      // the binning did not write the chunk list
+            const size_t msm = sizeof(int) * size_t(nt + 1);
+            if ((e = allow_smem(k_chunk_map, msm)) != cudaSuccess) return cuda_fail(e, "chunk map smem attribute");
+            e = launch_pdl(k_chunk_map, dim3(1), dim3(1024), msm, p->stream, 1, nt, (const int *)p->tile_off,
+                           kGatherChunk, p->chunk_map, p->counters + 2);
+            if (e != cudaSuccess) return cuda_fail(e, "chunk map launch");
+            SE_LAUNCH_CHECK("chunk_map");
+        }
         SE_DISPATCH_P(p->P, nu, {
             if constexpr (std::is_same<T, float>::value && PP <= 10) {
                 if (grad) {

@@ -144,28 +144,92 @@ __device__ __forceinline__ void block_scan_smem(int n, const int *__restrict__ c
     __syncthreads();
 }
 
+// Work list of the tile-staged gathering, written by one CTA from the tile
+// offsets so[0..nt] (in shared memory): tile t is cut into chunks of at most C
+// consecutive sorted particles, and chunk k of the list covers particles
+// [map[k].y, min(map[k].y + C, so[t + 1])) of tile t = map[k].x; *total receives
+// the number of chunks (empty tiles have none).  Each thread counts the chunks
+// of a contiguous run of tiles, the run counts are scanned with warp shuffles,
+// then each thread writes its run's chunks.  Every thread of the CTA calls it.
+__device__ __forceinline__ void chunk_map_cta(int nt, const int *so, int C, int2 *__restrict__ map,
+                                              int *__restrict__ total)
+{
+    __shared__ int wsum[32];
+    const int E = (nt + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int loc = 0;
+    for (int i = 0; i < E && b + i < nt; ++i) loc += (so[b + i + 1] - so[b + i] + C - 1) / C;
+    int v = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int k = v - loc + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = 0; i < E && b + i < nt; ++i) {
+        const int t = b + i;
+        for (int p = so[t]; p < so[t + 1]; p += C) map[k++] = make_int2(t, p);
+    }
+    if (threadIdx.x == blockDim.x - 1) *total = k;
+    __syncthreads();
+}
+
+// The same as a kernel of one CTA over tile offsets in global memory (read
+// once, coalesced, into (nt + 1) ints of dynamic shared memory).
+static __global__ void __launch_bounds__(1024) k_chunk_map(int nt, const int *__restrict__ off, int C,
+                                                           int2 *__restrict__ map, int *__restrict__ total)
+{
+    pdl_wait();
+    extern __shared__ int soff_raw[];
+    for (int i = threadIdx.x; i <= nt; i += blockDim.x) soff_raw[i] = off[i];
+    __syncthreads();
+    chunk_map_cta(nt, soff_raw, C, map, total);
+}
+
 // Tile of every particle (counting pass of the counting sort) and, when
 // scan_last is set, the exclusive scan of the tile counts into tile offsets by
-// the CTA that finishes last (otherwise k_bin_scatter scans the counts itself).
+// the CTA that finishes last (otherwise k_bin_scatter scans the counts itself);
+// with staged_scan that CTA scans in (ntiles + 1) ints of dynamic shared memory
+// and, when cmap is given, also writes the gathering's chunk list.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q, int *__restrict__ cnt,
-            int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done, bool scan_last)
+            int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done, bool scan_last,
+            bool staged_scan, int2 *__restrict__ cmap, int *__restrict__ ncmap)
 {
     __shared__ int part[256];
     __shared__ int carry;
     __shared__ bool last;
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    int tile = -1;
     if (i < N) {
         T xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
         T qv = q[i];
         int anc[3];
         T frac[3];
         locate(a, xp, qv, anc, frac, err);
-        const int tile = ((anc[2] / a.T[2]) * a.nt[1] + anc[1] / a.T[1]) * a.nt[0] + anc[0] / a.T[0];
-        const int r = atomicAdd(&cnt[tile], 1);
-        tile_rank[i] = make_int2(tile, r);
+        tile = ((anc[2] / a.T[2]) * a.nt[1] + anc[1] / a.T[1]) * a.nt[0] + anc[0] / a.T[0];
     }
+    // one atomic per distinct tile of the warp (particles of a dense cloud share
+    // tiles); ranks follow the lane order within the warp
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader && tile >= 0) base = atomicAdd(&cnt[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (i < N) tile_rank[i] = make_int2(tile, base + __popc(peers & ((1u << lane) - 1u)));
     if (!scan_last) return;
     __threadfence();
     __syncthreads();
@@ -173,18 +237,30 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
     __syncthreads();
     if (!last) return;
     __threadfence();
-    block_scan(ntiles, cnt, off, part, &carry);
+    if (staged_scan) {
+        // the counts scanned in shared memory (dynamic, ntiles + 1 ints), then published
+        extern __shared__ int scnt[];
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x) scnt[t] = __ldcg(cnt + t);
+        __syncthreads();
+        block_scan_smem(ntiles, scnt, scnt);                // in place: each entry is read before it is written
+        for (int t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = scnt[t];
+        if (cmap) chunk_map_cta(ntiles, scnt, kGatherChunk, cmap, ncmap);
+    } else {
+        block_scan(ntiles, cnt, off, part, &carry);
+    }
     if (threadIdx.x == 0) *done = 0;
 }
 
 // Sorted records: particle i goes to position off[tile] + rank.  With cnt !=
 // nullptr every CTA first scans the ntiles counts into shared memory (few
-// tiles), and CTA 0 publishes the offsets to off[].
+// tiles), and CTA 0 publishes the offsets to off[] (and, when cmap is given,
+// the gathering's chunk list).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
               int *__restrict__ off, const int2 *__restrict__ tile_rank,
-              typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia, const int *__restrict__ cnt, int ntiles)
+              typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia, const int *__restrict__ cnt, int ntiles,
+              int2 *__restrict__ cmap, int *__restrict__ ncmap)
 {
     pdl_wait();
 
@@ -192,8 +268,10 @@ k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restr
     const int *o = off;
     if (cnt) {
         block_scan_smem(ntiles, cnt, soff);
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (int t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = soff[t];
+            if (cmap) chunk_map_cta(ntiles, soff, kGatherChunk, cmap, ncmap);
+        }
         o = soff;
     }
     int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -1715,56 +1793,6 @@ __device__ __forceinline__ float warp_sum4(float a, float b, float c, float d, i
     k += __shfl_xor_sync(0xffffffffu, k, 2);
     k += __shfl_xor_sync(0xffffffffu, k, 1);
     return k;
-}
-
-// Work list of the tile-staged gathering: tile t is cut into chunks of at most
-// C consecutive sorted particles, and chunk k of the list covers particles
-// [map[k].y, min(map[k].y + C, off[t + 1])) of tile t = map[k].x; *total
-// receives the number of chunks (empty tiles have none).  One CTA: the tile
-// offsets are read once, coalesced, into shared memory when they fit
-// (staged = true: (nt + 1) ints of dynamic shared memory); each thread counts
-// the chunks of a contiguous run of tiles, the run counts are scanned with
-// warp shuffles, then each thread writes its run's chunks.
-static __global__ void __launch_bounds__(1024) k_chunk_map(int nt, const int *__restrict__ off, int C,
-                                                           int2 *__restrict__ map, int *__restrict__ total,
-                                                           bool staged)
-{
-    pdl_wait();
-    extern __shared__ int soff_raw[];
-    __shared__ int wsum[32];
-    const int *so = off;
-    if (staged) {
-        for (int i = threadIdx.x; i <= nt; i += blockDim.x) soff_raw[i] = off[i];
-        __syncthreads();
-        so = soff_raw;
-    }
-    const int E = (nt + blockDim.x - 1) / blockDim.x;
-    const int b = threadIdx.x * E;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    int loc = 0;
-    for (int i = 0; i < E && b + i < nt; ++i) loc += (so[b + i + 1] - so[b + i] + C - 1) / C;
-    int v = loc;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    if (lane == 31) wsum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < nw ? wsum[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
-        }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    int k = v - loc + (warp > 0 ? wsum[warp - 1] : 0);
-    for (int i = 0; i < E && b + i < nt; ++i) {
-        const int t = b + i;
-        for (int p = so[t]; p < so[t + 1]; p += C) map[k++] = make_int2(t, p);
-    }
-    if (threadIdx.x == blockDim.x - 1) *total = k;
 }
 
 // The particle loop of k_gather_tile_f32fast for one window kind: the warp's
