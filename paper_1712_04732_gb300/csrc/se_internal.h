@@ -1,6 +1,7 @@
 // Internal declarations of the Spectral Ewald library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <cstdint>
@@ -177,6 +178,8 @@ struct se_plan_s {
     int *err = nullptr;                  // latched device-side input errors
     int *counters = nullptr;             // completion counters of the last-CTA reductions (zero between calls);
                                          // counters[2]: chunks in chunk_map
+    CUtensorMap gout_map{};              // TMA descriptor of grid_out for the tile-staged FP32 gathering
+    bool gout_map_ok = false;            // gout_map encoded (else the gathering stages with cp.async)
     int2 *chunk_map = nullptr;           // work list of the tile-staged gathering: (tile, first particle)
     size_t chunk_map_elems = 0;          // n_tiles + capacity / kGatherChunk + 1
     // particle workspace

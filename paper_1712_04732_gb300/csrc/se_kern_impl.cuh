@@ -45,7 +45,7 @@ template <typename T>
 static bool use_tile_gather(const se_plan_s *p, int64_t N)
 {
     const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
-    return std::is_same<T, float>::value && p->gather_mode <= 0 && (p->P == 8 || p->P == 10) && p->tg.T[0] == 8 &&
+    return std::is_same<T, float>::value && (p->gather_mode <= 0 || p->gather_mode == 3) && (p->P == 8 || p->P == 10) &&
            p->tg.T[1] == 8 && p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) && N >= 64 * nt &&
            nt <= 50000;
 }
@@ -499,7 +499,29 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
         }
         SE_DISPATCH_P(p->P, nu, {
             if constexpr (std::is_same<T, float>::value && PP <= 10) {
-                if (grad) {
+                if (p->gather_mode == 3) {
+                    // four particles per warp (the direct-read kernel's lane layout) on the staged block
+                    const size_t sm = gather_tile4_smem<PP>();
+                    if (grad) {
+                        auto kern = k_gather_tile4_f32<PP, NN, true>;
+                        if ((e = allow_smem(kern, sm)) == cudaSuccess) e = prefer_shared(kern);
+                        if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                        e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
+                                       (const int2 *)p->chunk_map, (const int *)(p->counters + 2),
+                                       (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout,
+                                       phi, F, part, energy, p->counters + 1, float(p->inv_h), self, p->gout_map,
+                                       p->gout_map_ok && grid == p->grid_out, p->err);
+                    } else {
+                        auto kern = k_gather_tile4_f32<PP, NN, false>;
+                        if ((e = allow_smem(kern, sm)) == cudaSuccess) e = prefer_shared(kern);
+                        if (e != cudaSuccess) return cuda_fail(e, "gather smem attribute");
+                        e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
+                                       (const int2 *)p->chunk_map, (const int *)(p->counters + 2),
+                                       (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout,
+                                       phi, (float *)nullptr, part, energy, p->counters + 1, float(p->inv_h), self, p->gout_map,
+                                       p->gout_map_ok && grid == p->grid_out, p->err);
+                    }
+                } else if (grad) {
                     auto kern = k_gather_tile_f32fast<PP, NN, true>;
                     const size_t sm = gather_fast_smem<PP, true>();
                     if ((e = allow_smem(kern, sm)) == cudaSuccess) e = prefer_shared(kern);
@@ -507,7 +529,8 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
                     e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
                                    (const int2 *)p->chunk_map, (const int *)(p->counters + 2), (const int *)p->tile_off,
                                    fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, F, part, energy,
-                                   p->counters + 1, float(p->inv_h), self);
+                                   p->counters + 1, float(p->inv_h), self, p->gout_map,
+                                   p->gout_map_ok && grid == p->grid_out, p->err);
                 } else {
                     auto kern = k_gather_tile_f32fast<PP, NN, false>;
                     const size_t sm = gather_fast_smem<PP, false>();
@@ -516,7 +539,8 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
                     e = launch_pdl(kern, dim3(ncta), dim3(kThreads), sm, p->stream, 1, p->tg,
                                    (const int2 *)p->chunk_map, (const int *)(p->counters + 2), (const int *)p->tile_off,
                                    fq, (const int4 *)p->prt.idx_anc, wa, grid, p->gout, phi, (float *)nullptr, part,
-                                   energy, p->counters + 1, float(p->inv_h), self);
+                                   energy, p->counters + 1, float(p->inv_h), self, p->gout_map,
+                                   p->gout_map_ok && grid == p->grid_out, p->err);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "gather launch");
             }

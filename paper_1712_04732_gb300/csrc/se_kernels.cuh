@@ -31,6 +31,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Bits latched in the plan's error word.
 constexpr int kErrOutOfBox = 1;
 constexpr int kErrNotFinite = 2;
+constexpr int kErrTimeout = 4;      // a bounded device-side wait gave up (reported as SE_ETIMEOUT)
 
 // Geometry of the particle -> grid map passed to the binning kernels.
 template <typename R>
@@ -770,7 +771,7 @@ __device__ __forceinline__ void spread_rounds_f32(int *blk, float *w2, float4 *p
                                                   int stride, const int o[3], const float4 *__restrict__ fq,
                                                   const int4 *__restrict__ ia, const float *__restrict__ g,
                                                   float alpha, const LaneCoef<float, NU> &cf, int lane, int ax,
-                                                  int kk, const int *poff, float scale)
+                                                  int kk, const int *poff, float scale, float4 r, int4 a)
 {
     using G = FastGeom<P>;
     int pdx[G::NE], pdy[G::NE];
@@ -813,14 +814,7 @@ __device__ __forceinline__ void spread_rounds_f32(int *blk, float *w2, float4 *p
             }
         }
     };
-    int pl = first + lane * stride;
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    int4 a = make_int4(0, 0, 0, 0);
-    if (pl < end) {
-        r = fq[pl];
-        a = ia[pl];
-        if (g) r.w = g[a.x];
-    }
+    int pl = first + lane * stride;                        // (r, a): this lane's first record, loaded by the caller
     for (int p0 = first; p0 < end; p0 += 32 * stride) {
         if (pl < end) {
             ps[lane] = make_float4(r.x, r.y, r.z, r.w * scale);
@@ -863,8 +857,17 @@ __device__ __forceinline__ void spread_tile_f32_fast(int tile, const TileGeom &t
     int *bst = reinterpret_cast<int *>(pst + NW * 32);                               // [warp][32] block offsets
     __shared__ float qsum[NW], qmax[NW];
     __shared__ float sscale[2];
-    zero_smem(blk, G::SBLK);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this lane's first record, loaded before the |q| pass so that the two latencies overlap
+    const int first = beg + rank * NW + warp, stride = CL * NW;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 a0 = make_int4(0, 0, 0, 0);
+    if (first + lane * stride < end) {
+        r0 = fq[first + lane * stride];
+        a0 = ia[first + lane * stride];
+        if (g) r0.w = g[a0.x];
+    }
+    zero_smem(blk, G::SBLK);
     {
         float aq = 0.f, mq = 0.f;
         for (int p = beg + threadIdx.x; p < end; p += blockDim.x) {
@@ -918,14 +921,13 @@ __device__ __forceinline__ void spread_tile_f32_fast(int tile, const TileGeom &t
     float *w2 = wrow + warp * 2 * G::WROW;
     float4 *ps = pst + warp * 32;
     int *bs = bst + warp * 32;
-    const int stride = CL * NW, first = beg + rank * NW + warp;
     const int axc = min(lane / P, 3);
     if (wa.kind == SE_WIN_PKB)
         spread_rounds_f32<P, NU, true>(blk, w2, ps, bs, first, end, stride, o, fq, ia, g, wa.alpha, cf, lane, axc,
-                                       kk, poff, scale);
+                                       kk, poff, scale, r0, a0);
     else
         spread_rounds_f32<P, NU, false>(blk, w2, ps, bs, first, end, stride, o, fq, ia, g, wa.alpha, cf, lane, axc,
-                                        kk, poff, scale);
+                                        kk, poff, scale, r0, a0);
     cluster.sync();                                          // every copy complete and visible to the cluster
     // the cluster's copies summed row by row (row r = z B + y at r PITCH in shared
     // memory, r B in the compact block); CTA `rank` writes rows [rank R / CL, (rank + 1) R / CL)
@@ -934,9 +936,9 @@ __device__ __forceinline__ void spread_tile_f32_fast(int tile, const TileGeom &t
     for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
     constexpr int R = G::B * G::B, RPW = 32 / G::B;
     const int sub = lane / G::B, x = lane - sub * G::B;
-    const int r0 = rank * R / CL, r1 = (rank + 1) * R / CL;
+    const int row0 = rank * R / CL, row1 = (rank + 1) * R / CL;
     if (sub < RPW)
-        for (int r = r0 + warp * RPW + sub; r < r1; r += NW * RPW) {
+        for (int r = row0 + warp * RPW + sub; r < row1; r += NW * RPW) {
             const int si = r * G::PITCH + x;
             int v = src[0][si];
 #pragma unroll
@@ -1487,6 +1489,46 @@ __device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- TMA (cp.async.bulk.tensor) with an mbarrier, for the staged gathering
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// 3D tiled load of the box at coordinates (x, y, z) (x * 4 bytes a multiple of
+// 16) into shared memory dst (128-byte aligned); completion counted on mbar.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+        : "memory");
+}
+// Wait for phase `parity` of the mbarrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, int limit)
+{
+    for (int i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr int kWaitPolls = 1 << 20;   // about a second at the longest
+
 // Stage the extended block of a tile (tile origin o) from the real grid into
 // shared memory (row pitch tg.pitch) with asynchronous copies: warps take rows
 // (y, z), lanes run along x.  Periodic axes wrap; points past a free axis' end
@@ -1516,6 +1558,63 @@ __device__ __forceinline__ void stage_block(const TileGeom &tg, const int o[3], 
         b1 += nw;
         while (b1 >= B1) { b1 -= B1; ++b2; }
     }
+}
+
+// Staging of an edge-8 tile's extended block for the FP32 gathering kernels,
+// in two halves so that other set-up overlaps the copy.  With a TMA descriptor
+// of the grid (use_tma), thread 0 loads the block as one box of PITCH x B x B
+// floats -- exactly the staged layout -- counted on the mbarrier; points past a
+// free side come back as zeros (never used).  Otherwise the block is staged with
+// cp.async (stage_block).  stage_tile_finish waits (bounded: SE_ETIMEOUT is
+// latched in err when the copy does not arrive), loads the points of a block
+// that runs past a periodic side from the other end of the grid, and
+// synchronises the CTA.  blk is 128-byte aligned.
+template <int P>
+__device__ __forceinline__ void stage_tile_start(const TileGeom &tg, const int o[3], const float *__restrict__ grid,
+                                                 GridView v, float *blk, const CUtensorMap *tmap, bool use_tma,
+                                                 uint64_t *mbar)
+{
+    if (use_tma) {
+        if (threadIdx.x == 0) {
+            mbar_init(mbar, 1);
+            mbar_expect_tx(mbar, unsigned(FastGeom<P>::SBLK) * 4u);
+            tma_load_3d(blk, tmap, o[0], o[1], o[2], mbar);
+        }
+    } else {
+        stage_block<float>(tg, o, grid, v, blk);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void stage_tile_finish(const TileGeom &tg, const int o[3], const float *__restrict__ grid,
+                                                  GridView v, float *blk, bool use_tma, uint64_t *mbar, int *err)
+{
+    using G = FastGeom<P>;
+    if (use_tma) {
+        __syncthreads();                                 // the mbarrier is initialised
+        if (!mbar_wait(mbar, 0, kWaitPolls)) {
+            if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+            mbar_wait(mbar, 0, kWaitPolls);              // the copy in flight, once more, bounded
+        }
+        const bool wx = tg.periodic[0] && o[0] + G::B > tg.n[0];
+        const bool wy = tg.periodic[1] && o[1] + G::B > tg.n[1];
+        const bool wz = tg.periodic[2] && o[2] + G::B > tg.n[2];
+        if (wx || wy || wz)
+            for (int e = threadIdx.x; e < G::B * G::B * G::B; e += blockDim.x) {
+                const int c = e % G::B, y = (e / G::B) % G::B, z = e / (G::B * G::B);
+                int gx = o[0] + c, gy = o[1] + y, gz = o[2] + z;
+                const bool ox = gx >= tg.n[0], oy = gy >= tg.n[1], oz = gz >= tg.n[2];
+                if (!(ox || oy || oz)) continue;
+                if ((ox && !tg.periodic[0]) || (oy && !tg.periodic[1]) || (oz && !tg.periodic[2])) continue;
+                if (ox) gx -= tg.n[0];
+                if (oy) gy -= tg.n[1];
+                if (oz) gz -= tg.n[2];
+                blk[z * G::PLANE + y * G::PITCH + c] = grid[gx + gy * v.s1 + gz * v.s2];
+            }
+    } else {
+        cp_async_wait_all();
+    }
+    __syncthreads();
 }
 
 // Weights of one particle group at this lane's offset dx along the three axes,
@@ -1807,7 +1906,8 @@ __device__ __forceinline__ double gather_rounds_f32(const float *blk, float *w2,
                                                     const float4 *__restrict__ fq, const int4 *__restrict__ ia,
                                                     float alpha, const LaneCoef<float, NU> &cf, int lane, int ax,
                                                     int kk, const int *poff, float *__restrict__ phi,
-                                                    float *__restrict__ F, float inv_h, float self_coef)
+                                                    float *__restrict__ F, float inv_h, float self_coef, float4 r,
+                                                    int4 a)
 {
     using G = FastGeom<P>;
     constexpr int WR = GRAD ? 64 : 32;
@@ -1872,13 +1972,7 @@ __device__ __forceinline__ double gather_rounds_f32(const float *blk, float *w2,
         }
     };
     double esum = 0.0;
-    int pl = first + lane * stride;
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    int4 a = make_int4(0, 0, 0, 0);
-    if (pl < end) {
-        r = fq[pl];
-        a = ia[pl];
-    }
+    int pl = first + lane * stride;                        // (r, a): this lane's first record, loaded by the caller
     for (int p0 = first; p0 < end; p0 += 32 * stride) {
         const bool mine = pl < end;
         const float qv = r.w;
@@ -1937,7 +2031,7 @@ k_gather_tile_f32fast(TileGeom tg, const int2 *__restrict__ map, const int *__re
                       const int *__restrict__ off, const float4 *__restrict__ fq, const int4 *__restrict__ ia,
                       WindowArgs<float> wa, const float *__restrict__ grid, GridView v, float *__restrict__ phi,
                       float *__restrict__ F, double *__restrict__ part, double *energy, int *done, float inv_h,
-                      float self_coef)
+                      float self_coef, const __grid_constant__ CUtensorMap tmap, bool use_tma, int *err)
 {
     using G = FastGeom<P>;
     constexpr int NW = kThreads / 32;
@@ -1948,16 +2042,24 @@ k_gather_tile_f32fast(TileGeom tg, const int2 *__restrict__ map, const int *__re
     if (int(blockIdx.x) < *nchunk) {                        // the launch covers the largest possible list
         const int2 ck = map[blockIdx.x];
         const int tile = ck.x, beg = ck.y, end = min(ck.y + kGatherChunk, off[tile + 1]);
-        extern __shared__ __align__(16) unsigned char smraw[];
-        float *blk = reinterpret_cast<float *>(smraw);
+        extern __shared__ __align__(128) unsigned char smraw[];
+        __shared__ __align__(8) uint64_t mbar;
+        float *blk = reinterpret_cast<float *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));   // 128-byte aligned
         float *wrow = blk + align_up_elems<float>(G::SBLK);                        // [warp][2][WR]
         float4 *pst = reinterpret_cast<float4 *>(wrow + NW * 2 * WR);              // [warp][32] (t_x, t_y, t_z, q)
         int *bst = reinterpret_cast<int *>(pst + NW * 32);                         // [warp][32] block offsets
         float4 *rst = reinterpret_cast<float4 *>(bst + NW * 32);                   // [warp][32] (phi, g_x, g_y, g_z)
         int o[3];
         tile_origin(tg, tile, o);
-        stage_block<float>(tg, o, grid, v, blk);
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        // this lane's first record, loaded before the staging so that the two latencies overlap
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 a0 = make_int4(0, 0, 0, 0);
+        if (beg + warp + lane * NW < end) {
+            r0 = fq[beg + warp + lane * NW];
+            a0 = ia[beg + warp + lane * NW];
+        }
+        stage_tile_start<P>(tg, o, grid, v, blk, &tmap, use_tma, &mbar);
         const int kk = lane % P;
         LaneCoef<float, NU> cf;
         if (wa.kind == SE_WIN_PKB) cf.load(wa, P, kk);
@@ -1971,21 +2073,114 @@ k_gather_tile_f32fast(TileGeom tg, const int2 *__restrict__ map, const int *__re
         float4 *ps = pst + warp * 32;
         int *bs = bst + warp * 32;
         float4 *rs = rst + warp * 32;
-        cp_async_wait_all();
-        __syncthreads();
+        stage_tile_finish<P>(tg, o, grid, v, blk, use_tma, &mbar, err);
         const int stride = NW, first = beg + warp;
         const int axc = min(lane / P, 3);
         if (wa.kind == SE_WIN_PKB)
             esum = gather_rounds_f32<P, NU, GRAD, true>(blk, w2, ps, bs, rs, first, end, stride, o, fq, ia, wa.alpha,
-                                                        cf, lane, axc, kk, poff, phi, F, inv_h, self_coef);
+                                                        cf, lane, axc, kk, poff, phi, F, inv_h, self_coef, r0, a0);
         else
             esum = gather_rounds_f32<P, NU, GRAD, false>(blk, w2, ps, bs, rs, first, end, stride, o, fq, ia, wa.alpha,
-                                                         cf, lane, axc, kk, poff, phi, F, inv_h, self_coef);
+                                                         cf, lane, axc, kk, poff, phi, F, inv_h, self_coef, r0, a0);
     }
     if (part) {
         cta_energy_partial(esum, part + blockIdx.x);
         finish_energy(part, gridDim.x, energy, done);
     }
+}
+
+// The tile-staged FP32 gathering with the lane layout of the direct-read
+// kernel: a warp serves G = 32 / P particles at a time, lane (group, dx) holds
+// stencil offset dx of one particle and walks the P^2 rows (dy, dz) of its
+// stencil in the staged block, and the P lanes of a particle are summed by
+// shuffles.  Same chunk work list, staging and outputs as
+// k_gather_tile_f32fast; the window values of a group go through a per-warp
+// shared row of 6 P values per group.
+template <int P, int NU, bool GRAD>
+__global__ void __launch_bounds__(kThreads, 4)
+k_gather_tile4_f32(TileGeom tg, const int2 *__restrict__ map, const int *__restrict__ nchunk,
+                   const int *__restrict__ off, const float4 *__restrict__ fq, const int4 *__restrict__ ia,
+                   WindowArgs<float> wa, const float *__restrict__ grid, GridView v, float *__restrict__ phi,
+                   float *__restrict__ F, double *__restrict__ part, double *energy, int *done, float inv_h,
+                   float self_coef, const __grid_constant__ CUtensorMap tmap, bool use_tma, int *err)
+{
+    using FG = FastGeom<P>;
+    constexpr int NW = kThreads / 32;
+    constexpr int G = LaneMap<P>::G;
+    pdl_wait();
+    double esum = 0.0;
+    if (int(blockIdx.x) < *nchunk) {
+        const int2 ck = map[blockIdx.x];
+        const int tile = ck.x, beg = ck.y, end = min(ck.y + kGatherChunk, off[tile + 1]);
+        extern __shared__ __align__(128) unsigned char smraw[];
+        __shared__ __align__(8) uint64_t mbar;
+        float *blk = reinterpret_cast<float *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+        float *wb = blk + align_up_elems<float>(FG::SBLK);                 // [warp][G][6P]
+        int o[3];
+        tile_origin(tg, tile, o);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int grp = lane / P, dx = lane - grp * P;
+        const bool lane_on = grp < G;
+        // the group's records are loaded one iteration ahead (the first before the staging)
+        float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 an = make_int4(0, 0, 0, 0);
+        if (lane_on && beg + warp * G + grp < end) {
+            rn = fq[beg + warp * G + grp];
+            an = ia[beg + warp * G + grp];
+        }
+        stage_tile_start<P>(tg, o, grid, v, blk, &tmap, use_tma, &mbar);
+        LaneCoef<float, NU> cf;
+        if (wa.kind == SE_WIN_PKB) cf.load(wa, P, dx);
+        float *w = wb + (warp * G + (lane_on ? grp : 0)) * 6 * P;
+        stage_tile_finish<P>(tg, o, grid, v, blk, use_tma, &mbar, err);
+        for (int p0 = beg + warp * G; p0 < end; p0 += NW * G) {
+            const int p = p0 + grp;
+            const bool has = lane_on && p < end;
+            const float4 r = rn;
+            const int4 a = an;
+            if (lane_on && p + NW * G < end) {
+                rn = fq[p + NW * G];
+                an = ia[p + NW * G];
+            }
+            if (has) group_weights<float, P, NU, GRAD>(wa, cf, r, dx, w);
+            __syncwarp();
+            float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            if (has) {
+                const float *col = blk + ((a.w - o[2]) * FG::B + (a.z - o[1])) * FG::PITCH + (a.y - o[0]) + dx;
+                group_contract<float, P, GRAD>(w, dx, [&](int dy, int dz) { return col[dz * FG::PLANE + dy * FG::PITCH]; },
+                                               ph, gx, gy, gz);
+            }
+            ph = group_sum<float, P>(ph, dx);
+            if (GRAD) {
+                gx = group_sum<float, P>(gx, dx);
+                gy = group_sum<float, P>(gy, dx);
+                gz = group_sum<float, P>(gz, dx);
+            }
+            if (has && dx == 0) {
+                const float phv = ph + self_coef * r.w;
+                const int64_t m = a.x;
+                if (phi) phi[m] = phv;
+                if (GRAD && F) {
+                    const float sc = -r.w * inv_h;
+                    F[3 * m] = sc * gx;
+                    F[3 * m + 1] = sc * gy;
+                    F[3 * m + 2] = sc * gz;
+                }
+                esum += 0.5 * double(r.w) * double(phv);
+            }
+            __syncwarp();
+        }
+    }
+    if (part) {
+        cta_energy_partial(esum, part + blockIdx.x);
+        finish_energy(part, gridDim.x, energy, done);
+    }
+}
+
+template <int P>
+__host__ __device__ constexpr size_t gather_tile4_smem()
+{
+    return (((size_t(FastGeom<P>::SBLK) + 31) & ~size_t(31)) + size_t(kThreads / 32) * LaneMap<P>::G * 6 * P) * 4 + 128;
 }
 
 // Dynamic shared memory of k_gather_tile_f32fast.
@@ -1994,7 +2189,8 @@ __host__ __device__ constexpr size_t gather_fast_smem()
 {
     using G = FastGeom<P>;
     constexpr int WR = GRAD ? 64 : 32;
-    return (((size_t(G::SBLK) + 31) & ~size_t(31)) + size_t(kThreads / 32) * (2 * WR + 32 * 4 + 32 + 32 * 4)) * 4;
+    return (((size_t(G::SBLK) + 31) & ~size_t(31)) + size_t(kThreads / 32) * (2 * WR + 32 * 4 + 32 + 32 * 4)) * 4 +
+           128;                                          // room to align the block to 128 bytes
 }
 
 // Gathering for method 2 of Sec. 7.2: phi from H~ and the three components of

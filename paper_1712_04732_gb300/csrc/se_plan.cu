@@ -8,6 +8,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "se_internal.h"
 
 namespace se {
@@ -683,6 +685,42 @@ static int choose_tile(int n, bool periodic, int pref)
     return 1;
 }
 
+// TMA descriptor of the inverse-transform output grid for the tile-staged FP32
+// gathering (tiles of edge 8, P <= 10): a 3D box of gridding_pitch x B x B
+// floats (B = 7 + P), which lands in shared memory with exactly the row pitch
+// and plane size of the staged block; coordinates past a free side read zeros.
+// Left unset (the kernel then stages with cp.async) when the driver's encoder
+// is not available or the grid's strides are not multiples of 16 bytes.
+static void encode_gout_map(se_plan_s *p)
+{
+    p->gout_map_ok = false;
+    if (p->dtype != SE_F32 || p->P > 10 || p->tg.T[0] != 8 || p->tg.T[1] != 8 || p->tg.T[2] != 8) return;
+    const int B = 7 + p->P, pitch = gridding_pitch(B, p->P, 4);
+    if (p->tg.pitch != pitch) return;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    }
+    if (!encode) return;
+    const cuuint64_t dims[3] = {cuuint64_t(p->tg.n[0]), cuuint64_t(p->tg.n[1]), cuuint64_t(p->tg.n[2])};
+    const cuuint64_t strides[2] = {cuuint64_t(p->gout.s1) * 4, cuuint64_t(p->gout.s2) * 4};
+    if (strides[0] % 16 || strides[1] % 16 || reinterpret_cast<uintptr_t>(p->grid_out) % 16) return;
+    const cuuint32_t box[3] = {cuuint32_t(pitch), cuuint32_t(B), cuuint32_t(B)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(&p->gout_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->grid_out, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    p->gout_map_ok = r == CUDA_SUCCESS;
+}
+
 se_status plan_build(se_plan_s *p)
 {
     cudaError_t ce = cudaGetDevice(&p->dev);
@@ -784,6 +822,7 @@ se_status plan_build(se_plan_s *p)
     if ((st = build_tables(p)) != SE_OK) return st;
     if ((st = make_plans(p)) != SE_OK) return st;
     if ((st = plan_set_fft_stream(p)) != SE_OK) return st;
+    encode_gout_map(p);
     return SE_OK;
 }
 

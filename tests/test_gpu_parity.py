@@ -63,12 +63,14 @@ def test_force_and_potential_match_discrete_oracle(D, window, dtype):
 
 
 @pytest.mark.parametrize("spread_mode,gather_mode,split", [
-    (1, 1, 1), (2, 1, 2), (2, 1, 4), (2, 2, 8), (3, 1, 1), (3, 2, 1), (1, 2, 3)])
+    (1, 1, 1), (2, 1, 2), (2, 1, 4), (2, 2, 8), (3, 1, 1), (3, 2, 1), (1, 2, 3), (2, 3, 2), (2, 0, 1)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_every_kernel_variant(spread_mode, gather_mode, split, dtype):
     """Gridding variants (shared atomics, cluster-split atomics, per-warp private
-    blocks) and gathering variants (staged with split CTAs, direct reads) give the
-    same potential and forces."""
+    blocks) and gathering variants (staged with split CTAs, direct reads, the
+    staged block over chunks with four particles or one particle per warp --
+    the FP32 defaults at 111 particles per tile) give the same potential and
+    forces."""
     se = _se()
     N, M = 3000, 24
     x = wl.uniform_positions(N, 1.0, 41)
