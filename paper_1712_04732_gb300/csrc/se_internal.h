@@ -16,6 +16,7 @@ constexpr int kMaxP = 16;       // largest window support compiled in
 constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
 constexpr int kGatherChunk = 256;  // particles per CTA of the tile-staged FP32 gathering (one round per warp)
+constexpr int kHeavyTile = 1536;   // FP32 gridding: tiles with more particles get a cluster of 8 CTAs
 
 // Row pitch (elements) of a gridding block in shared memory: the smallest
 // pitch >= B0 for which the gridding kernels' access pattern -- a warp's lanes
@@ -177,10 +178,11 @@ struct se_plan_s {
     double *red = nullptr;               // small FP64 reduction outputs
     int *err = nullptr;                  // latched device-side input errors
     int *counters = nullptr;             // completion counters of the last-CTA reductions (zero between calls);
-                                         // counters[2]: chunks in chunk_map
+                                         // counters[2]: chunks in chunk_map, [3]: heavy tiles
     CUtensorMap gout_map{};              // TMA descriptor of grid_out for the tile-staged FP32 gathering
     bool gout_map_ok = false;            // gout_map encoded (else the gathering stages with cp.async)
     int2 *chunk_map = nullptr;           // work list of the tile-staged gathering: (tile, first particle)
+    int *heavy_tiles = nullptr;          // FP32 gridding: tiles of more than kHeavyTile particles (counters[3])
     size_t chunk_map_elems = 0;          // n_tiles + capacity / kGatherChunk + 1
     // particle workspace
     int64_t cap = 0;

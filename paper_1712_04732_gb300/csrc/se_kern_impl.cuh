@@ -50,6 +50,24 @@ static bool use_tile_gather(const se_plan_s *p, int64_t N)
            nt <= 50000;
 }
 
+// The FP32 gridding kernel with compile-time block geometry: tiles of edge 8,
+// P <= 10, the plan's pitch; by default (spread_mode 0) dense tiles take a
+// second launch from the heavy-tile list.
+template <typename T>
+static bool use_fast_spread(const se_plan_s *p)
+{
+    return std::is_same<T, float>::value && p->P <= 10 && p->tg.T[0] == 8 && p->tg.T[1] == 8 && p->tg.T[2] == 8 &&
+           p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4);
+}
+
+// Whether this call builds the work lists of the FP32 tile kernels.
+template <typename T>
+static bool want_lists(const se_plan_s *p, int64_t N)
+{
+    const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
+    return (use_tile_gather<T>(p, N) || (use_fast_spread<T>(p) && p->spread_mode <= 0)) && nt <= 50000;
+}
+
 template <typename T>
 se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
 {
@@ -61,22 +79,33 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     const bool local_scan = nt <= kLocalScanTiles;
     const bool staged = !local_scan && nt <= kStagedScanTiles;
     const size_t csm = staged ? sizeof(int) * size_t(nt + 1) : 0;
-    // the gathering's chunk list, written by whichever CTA scans the counts in shared memory
-    int2 *cmap = use_tile_gather<T>(p, N) && nt <= kStagedScanTiles ? p->chunk_map : nullptr;
+    // the work lists of the FP32 tile kernels, written by whichever CTA scans the counts in
+    // shared memory (more tiles: a kernel of their own after the binning)
+    const bool lists = want_lists<T>(p, N);
+    int2 *cmap = lists && nt <= kStagedScanTiles ? p->chunk_map : nullptr;
     if ((e = allow_smem(k_bin_count<T>, csm)) != cudaSuccess) return cuda_fail(e, "bin_count smem attribute");
     k_bin_count<T><<<blocks_for(N, 256), 256, csm, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
                                                                  p->tile_off, p->counters, !local_scan, staged,
-                                                                 staged ? cmap : nullptr, p->counters + 2);
+                                                                 staged ? cmap : nullptr, p->counters + 2,
+                                                                 p->heavy_tiles, p->counters + 3);
     SE_LAUNCH_CHECK("bin_count");
     {
         cudaError_t e = launch_pdl(k_bin_scatter<T>, dim3(blocks_for(N, 256)), dim3(256),
                                    local_scan ? sizeof(int) * (nt + 1) : 0, p->stream, 1, a, N, x, q, p->tile_off,
                                    (const int2 *)p->tile_rank, reinterpret_cast<typename Vec4<T>::type *>(p->prt.frac_q),
                                    p->prt.idx_anc, (const int *)(local_scan ? p->tile_cnt : nullptr), nt,
-                                   local_scan ? cmap : nullptr, p->counters + 2);
+                                   local_scan ? cmap : nullptr, p->counters + 2, p->heavy_tiles, p->counters + 3);
         if (e != cudaSuccess) return cuda_fail(e, "bin_scatter launch");
     }
     SE_LAUNCH_CHECK("bin_scatter");
+    if (lists && nt > kStagedScanTiles) {
+        const size_t msm = sizeof(int) * size_t(nt + 1);
+        if ((e = allow_smem(k_work_lists, msm)) != cudaSuccess) return cuda_fail(e, "work lists smem attribute");
+        e = launch_pdl(k_work_lists, dim3(1), dim3(1024), msm, p->stream, 1, nt, (const int *)p->tile_off,
+                       kGatherChunk, p->chunk_map, p->counters + 2, p->heavy_tiles, p->counters + 3, kHeavyTile);
+        if (e != cudaSuccess) return cuda_fail(e, "work lists launch");
+        SE_LAUNCH_CHECK("work_lists");
+    }
     prof_mark(p, 1);
     return SE_OK;
 }
@@ -124,9 +153,14 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
     } else {
         const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
         // FP32 with edge-8 tiles: the kernel with the block geometry fixed at compile time
-        const bool fast = std::is_same<T, float>::value && p->P <= 10 && p->tg.T[0] == 8 && p->tg.T[1] == 8 &&
-                          p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4);
+        const bool fast = use_fast_spread<T>(p);
         const int CL = mode == 1 ? 1 : fast ? split_fast(p, N) : split_for(p, N);
+        // dense tiles in a launch of their own (the work lists hold them), for systems of 128
+        // particles per tile or more on average (sparser ones rarely have dense tiles, and
+        // the second launch costs about a microsecond even when its list is empty)
+        const bool split_heavy = fast && p->spread_mode <= 0 && want_lists<T>(p, N) && N > kHeavyTile &&
+                                 N >= 128 * int64_t(nt);
+        const int hmax = split_heavy ? int(std::min<int64_t>(nt, N / (kHeavyTile + 1))) : 0;
         const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
         SE_DISPATCH_P(p->P, nu, {
             bool done = false;
@@ -139,8 +173,17 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
                     if (e != cudaSuccess) return cuda_fail(e, "spread smem attribute");
                     e = launch_pdl(kern, dim3(unsigned(nt * CL)), dim3(kThreads), smf, p->stream, unsigned(CL),
                                    p->tg, (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
-                                   reinterpret_cast<float *>(scratch));
+                                   reinterpret_cast<float *>(scratch), (const int *)nullptr, (const int *)nullptr,
+                                   split_heavy ? kHeavyTile : 0);
                     if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+                    if (hmax > 0) {
+                        SE_LAUNCH_CHECK("spread");
+                        e = launch_pdl(kern, dim3(unsigned(hmax * 8)), dim3(kThreads), smf, p->stream, 8u, p->tg,
+                                       (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
+                                       reinterpret_cast<float *>(scratch), (const int *)p->heavy_tiles,
+                                       (const int *)(p->counters + 3), 0);
+                        if (e != cudaSuccess) return cuda_fail(e, "heavy-tile spread launch");
+                    }
                     done = true;
                 }
             }
@@ -488,15 +531,7 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
         // work list: chunks of at most kGatherChunk particles of one tile
         const unsigned ncta = unsigned(nt + N / kGatherChunk + 1);
         if (size_t(ncta) > p->chunk_map_elems) return fail(SE_EINVAL, "gathering work list exceeds the reserve");
-        cudaError_t e = cudaSuccess;
-        if (nt > kStagedScanTiles) {                      // the binning did not write the chunk list
-            const size_t msm = sizeof(int) * size_t(nt + 1);
-            if ((e = allow_smem(k_chunk_map, msm)) != cudaSuccess) return cuda_fail(e, "chunk map smem attribute");
-            e = launch_pdl(k_chunk_map, dim3(1), dim3(1024), msm, p->stream, 1, nt, (const int *)p->tile_off,
-                           kGatherChunk, p->chunk_map, p->counters + 2);
-            if (e != cudaSuccess) return cuda_fail(e, "chunk map launch");
-            SE_LAUNCH_CHECK("chunk_map");
-        }
+        cudaError_t e = cudaSuccess;                      // the chunk list comes from the binning
         SE_DISPATCH_P(p->P, nu, {
             if constexpr (std::is_same<T, float>::value && PP <= 10) {
                 if (p->gather_mode == 3) {

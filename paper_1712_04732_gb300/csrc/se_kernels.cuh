@@ -145,17 +145,24 @@ __device__ __forceinline__ void block_scan_smem(int n, const int *__restrict__ c
     __syncthreads();
 }
 
-// Work list of the tile-staged gathering, written by one CTA from the tile
-// offsets so[0..nt] (in shared memory): tile t is cut into chunks of at most C
-// consecutive sorted particles, and chunk k of the list covers particles
-// [map[k].y, min(map[k].y + C, so[t + 1])) of tile t = map[k].x; *total receives
-// the number of chunks (empty tiles have none).  Each thread counts the chunks
-// of a contiguous run of tiles, the run counts are scanned with warp shuffles,
-// then each thread writes its run's chunks.  Every thread of the CTA calls it.
-__device__ __forceinline__ void chunk_map_cta(int nt, const int *so, int C, int2 *__restrict__ map,
-                                              int *__restrict__ total)
+// Work lists of the FP32 tile kernels, written by one CTA from the tile
+// offsets so[0..nt] (in shared memory):
+//  - the gathering's chunks: tile t is cut into chunks of at most C consecutive
+//    sorted particles, and chunk k covers particles [map[k].y, min(map[k].y + C,
+//    so[t + 1])) of tile t = map[k].x; *nmap receives the number of chunks
+//    (empty tiles have none).  Each thread counts the chunks of a contiguous run
+//    of tiles, the run counts are scanned with warp shuffles, then each thread
+//    writes its run's chunks;
+//  - the gridding's heavy tiles (more than heavy_thr particles), in any order,
+//    *nheavy of them (heavy may be nullptr).
+// Every thread of the CTA calls it.
+__device__ __forceinline__ void work_lists_cta(int nt, const int *so, int C, int2 *__restrict__ map,
+                                               int *__restrict__ nmap, int *__restrict__ heavy,
+                                               int *__restrict__ nheavy, int heavy_thr)
 {
     __shared__ int wsum[32];
+    __shared__ int hcount;
+    if (threadIdx.x == 0) hcount = 0;
     const int E = (nt + blockDim.x - 1) / blockDim.x;
     const int b = threadIdx.x * E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -181,33 +188,39 @@ __device__ __forceinline__ void chunk_map_cta(int nt, const int *so, int C, int2
     for (int i = 0; i < E && b + i < nt; ++i) {
         const int t = b + i;
         for (int p = so[t]; p < so[t + 1]; p += C) map[k++] = make_int2(t, p);
+        if (heavy && so[t + 1] - so[t] > heavy_thr) heavy[atomicAdd(&hcount, 1)] = t;
     }
-    if (threadIdx.x == blockDim.x - 1) *total = k;
+    if (threadIdx.x == blockDim.x - 1) *nmap = k;
+    __syncthreads();
+    if (threadIdx.x == 0 && heavy) *nheavy = hcount;
     __syncthreads();
 }
 
 // The same as a kernel of one CTA over tile offsets in global memory (read
 // once, coalesced, into (nt + 1) ints of dynamic shared memory).
-static __global__ void __launch_bounds__(1024) k_chunk_map(int nt, const int *__restrict__ off, int C,
-                                                           int2 *__restrict__ map, int *__restrict__ total)
+static __global__ void __launch_bounds__(1024) k_work_lists(int nt, const int *__restrict__ off, int C,
+                                                            int2 *__restrict__ map, int *__restrict__ nmap,
+                                                            int *__restrict__ heavy, int *__restrict__ nheavy,
+                                                            int heavy_thr)
 {
     pdl_wait();
     extern __shared__ int soff_raw[];
     for (int i = threadIdx.x; i <= nt; i += blockDim.x) soff_raw[i] = off[i];
     __syncthreads();
-    chunk_map_cta(nt, soff_raw, C, map, total);
+    work_lists_cta(nt, soff_raw, C, map, nmap, heavy, nheavy, heavy_thr);
 }
 
 // Tile of every particle (counting pass of the counting sort) and, when
 // scan_last is set, the exclusive scan of the tile counts into tile offsets by
 // the CTA that finishes last (otherwise k_bin_scatter scans the counts itself);
 // with staged_scan that CTA scans in (ntiles + 1) ints of dynamic shared memory
-// and, when cmap is given, also writes the gathering's chunk list.
+// and, when cmap is given, also writes the work lists of the FP32 tile kernels.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q, int *__restrict__ cnt,
             int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done, bool scan_last,
-            bool staged_scan, int2 *__restrict__ cmap, int *__restrict__ ncmap)
+            bool staged_scan, int2 *__restrict__ cmap, int *__restrict__ ncmap, int *__restrict__ heavy,
+            int *__restrict__ nheavy)
 {
     __shared__ int part[256];
     __shared__ int carry;
@@ -245,7 +258,7 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
         __syncthreads();
         block_scan_smem(ntiles, scnt, scnt);                // in place: each entry is read before it is written
         for (int t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = scnt[t];
-        if (cmap) chunk_map_cta(ntiles, scnt, kGatherChunk, cmap, ncmap);
+        if (cmap) work_lists_cta(ntiles, scnt, kGatherChunk, cmap, ncmap, heavy, nheavy, kHeavyTile);
     } else {
         block_scan(ntiles, cnt, off, part, &carry);
     }
@@ -255,13 +268,13 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
 // Sorted records: particle i goes to position off[tile] + rank.  With cnt !=
 // nullptr every CTA first scans the ntiles counts into shared memory (few
 // tiles), and CTA 0 publishes the offsets to off[] (and, when cmap is given,
-// the gathering's chunk list).
+// the work lists of the FP32 tile kernels).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q,
               int *__restrict__ off, const int2 *__restrict__ tile_rank,
               typename Vec4<T>::type *__restrict__ fq, int4 *__restrict__ ia, const int *__restrict__ cnt, int ntiles,
-              int2 *__restrict__ cmap, int *__restrict__ ncmap)
+              int2 *__restrict__ cmap, int *__restrict__ ncmap, int *__restrict__ heavy, int *__restrict__ nheavy)
 {
     pdl_wait();
 
@@ -271,7 +284,7 @@ k_bin_scatter(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restr
         block_scan_smem(ntiles, cnt, soff);
         if (blockIdx.x == 0) {
             for (int t = threadIdx.x; t <= ntiles; t += blockDim.x) off[t] = soff[t];
-            if (cmap) chunk_map_cta(ntiles, soff, kGatherChunk, cmap, ncmap);
+            if (cmap) work_lists_cta(ntiles, soff, kGatherChunk, cmap, ncmap, heavy, nheavy, kHeavyTile);
         }
         o = soff;
     }
@@ -971,16 +984,27 @@ static inline size_t spread_fast_smem_rt(int P)
 
 // FP32 gridding for edge-8 tiles: spread_tile_f32_fast, or the generic tile
 // code (float atomics) for a tile of more than Fix<float>::kFixTile particles.
+// Launched twice when heavy_thr > 0: over every tile, skipping those of more
+// than heavy_thr particles, then (heavy != nullptr) over the list of those
+// tiles with larger clusters, so that dense tiles do not hold up the launch.
 template <int P, int NU>
 __global__ void __launch_bounds__(kThreads, P == 8 ? 5 : 4)
 k_spread_cl_f32fast(TileGeom tg, const int *__restrict__ off, const float4 *__restrict__ fq,
                     const int4 *__restrict__ ia, const float *__restrict__ g, WindowArgs<float> wa,
-                    float *__restrict__ scratch)
+                    float *__restrict__ scratch, const int *__restrict__ heavy, const int *__restrict__ nheavy,
+                    int heavy_thr)
 {
     pdl_wait();
-    const int tile = blockIdx.x / int(cooperative_groups::this_cluster().num_blocks());
+    // every CTA of a cluster takes the same branches below
+    const int c = blockIdx.x / int(cooperative_groups::this_cluster().num_blocks());
+    int tile = c;
+    if (heavy) {                                          // the launch over the list of heavy tiles
+        if (c >= *nheavy) return;
+        tile = heavy[c];
+    }
     const int beg = off[tile], end = off[tile + 1];
-    if (beg == end) return;                               // the same for every CTA of the cluster
+    if (beg == end) return;
+    if (!heavy && heavy_thr > 0 && end - beg > heavy_thr) return;   // left to the heavy-tile launch
     float *dst = scratch + size_t(tile) * tg.blk;
     if (end - beg > Fix<float>::kFixTile)
         spread_cl_tile<float, P, NU>(tg, tile, beg, end, fq, ia, g, wa, dst);

@@ -763,6 +763,7 @@ se_status plan_build(se_plan_s *p)
     se_status st;
     if ((st = dev_alloc(p, (void **)&p->tile_cnt, sizeof(int) * (nt + 1))) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->tile_off, sizeof(int) * (nt + 1))) != SE_OK) return st;
+    if ((st = dev_alloc(p, (void **)&p->heavy_tiles, sizeof(int) * nt)) != SE_OK) return st;
     p->tile_part_elems = size_t(std::max(8 * nt, 256));
     if ((st = dev_alloc(p, (void **)&p->tile_part, sizeof(double) * p->tile_part_elems)) != SE_OK) return st;
     if ((st = dev_alloc(p, (void **)&p->red, sizeof(double) * 8)) != SE_OK) return st;
@@ -895,7 +896,7 @@ void plan_release(se_plan_s *p)
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
                      (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
                      (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2, &p->spec_d, &p->U_d, &p->Z_d,
-                     &p->grid_d, &p->ztw, (void **)&p->chunk_map};
+                     &p->grid_d, &p->ztw, (void **)&p->chunk_map, (void **)&p->heavy_tiles};
     for (void **b : bufs) dev_free(p, b);
 }
 
