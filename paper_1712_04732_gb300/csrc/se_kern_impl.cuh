@@ -154,12 +154,14 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
         const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
         // FP32 with edge-8 tiles: the kernel with the block geometry fixed at compile time
         const bool fast = use_fast_spread<T>(p);
-        const int CL = mode == 1 ? 1 : fast ? split_fast(p, N) : split_for(p, N);
         // dense tiles in a launch of their own (the work lists hold them), for systems of 128
         // particles per tile or more on average (sparser ones rarely have dense tiles, and
-        // the second launch costs about a microsecond even when its list is empty)
+        // the second launch costs about a microsecond even when its list is empty); the other
+        // tiles then take one CTA each (measured best on the wire workload: 208 against 217 us
+        // with two)
         const bool split_heavy = fast && p->spread_mode <= 0 && want_lists<T>(p, N) && N > kHeavyTile &&
                                  N >= 128 * int64_t(nt);
+        const int CL = mode == 1 ? 1 : !fast ? split_for(p, N) : (split_heavy && p->split <= 0) ? 1 : split_fast(p, N);
         const int hmax = split_heavy ? int(std::min<int64_t>(nt, N / (kHeavyTile + 1))) : 0;
         const size_t sm = (al32(p->tg.sblk) + size_t(kThreads / 32) * 3 * p->P) * sizeof(T);
         SE_DISPATCH_P(p->P, nu, {
@@ -358,7 +360,8 @@ static se_status forward(se_plan_s *p, void *gin)
     }
     SE_LAUNCH_CHECK("pad");
     // Alg. 1 steps 2-4: free-direction transforms of every class
-    if ((r = fft_c2c(p->free_main, spec, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "free fwd");
+    if ((r = fft_c2c(p->free_main, spec + (p->D == 1 ? p->nI + 1 : 0), CUFFT_FORWARD)) != CUFFT_SUCCESS)
+        return cufft_fail(r, "free fwd");
     if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "I fwd");
     if ((r = fft_c2c(p->free_Z, Z, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "zero fwd");
     return SE_OK;
@@ -422,7 +425,8 @@ static se_status inverse(se_plan_s *p, typename Cplx<T>::type *spec, typename Cp
     if (p->D != 3) {
         const int row = p->Mv[0] / 2 + 1;
         // Alg. 2 steps 1-3
-        if ((r = fft_c2c(p->free_main, spec, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "free inv");
+        if ((r = fft_c2c(p->free_main, spec + (p->D == 1 ? p->nI + 1 : 0), CUFFT_INVERSE)) != CUFFT_SUCCESS)
+            return cufft_fail(r, "free inv");
         if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "I inv");
         if ((r = fft_c2c(p->free_Z, Z, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "zero inv");
         // Alg. 2 steps 2-4: truncate to M~ and merge back

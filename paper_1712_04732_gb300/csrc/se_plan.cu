@@ -640,9 +640,11 @@ static se_status make_plans(se_plan_s *p)
         int n[1] = {Mv[0]};
         SE_PLAN(cufftPlanMany(&p->fwd, 1, n, nullptr, 1, 0, nullptr, 1, 0, R2C, Mt[1] * Mt[2]), p->have_fwd, "plan fwd");
         SE_PLAN(cufftPlanMany(&p->inv, 1, n, nullptr, 1, 0, nullptr, 1, 0, C2R, Mt[1] * Mt[2]), p->have_inv, "plan inv");
-        // (z, y) planes of each x' (element stride M_0/2 + 1)
+        // (z, y) planes of each x' (element stride M_0/2 + 1) of the class J: x' = nI + 1 ...
+        // M_0/2 (the zero plane and the planes of the set I are transformed padded)
         int nz[2] = {Mt[2], Mt[1]};
-        SE_PLAN(cufftPlanMany(&p->free_main, 2, nz, nz, row, 1, nz, row, 1, C2C, row), p->have_free_main, "plan free");
+        SE_PLAN(cufftPlanMany(&p->free_main, 2, nz, nz, row, 1, nz, row, 1, C2C, row - 1 - p->nI), p->have_free_main,
+                "plan free");
         if (p->nI > 0) {
             int ns[2] = {p->sv[2], p->sv[1]};
             SE_PLAN(cufftPlanMany(&p->free_I, 2, ns, nullptr, 1, 0, nullptr, 1, 0, C2C, p->nI), p->have_free_I, "plan I");
