@@ -48,7 +48,8 @@ __host__ __device__ constexpr int gridding_pitch(int B0, int P, int elem)
     return best;
 }
 constexpr int kLocalScanTiles = 4096;   // up to this many tiles each binning CTA scans the counts itself
-constexpr int kStagedScanTiles = 8192;  // up to this many the last counting CTA scans in shared memory
+constexpr int kStagedScanTiles = 8192;  // up to this many the last counting CTA may scan in shared memory
+constexpr int kScanListTiles = 50000;   // up to this many a one-CTA kernel scans the counts in shared memory
 constexpr int kMergeJ = 6;      // most tiles per axis whose blocks overlap one grid point
 
 // Window description passed by value to the tile kernels.  For the PKB the

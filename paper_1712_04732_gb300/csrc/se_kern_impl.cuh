@@ -75,20 +75,29 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     cudaError_t e = cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * (nt + 1), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
     BinArgs<T> a = bin_args<T>(p);
-    // few tiles: every scatter CTA scans the counts itself (no last-CTA scan)
+    // few tiles: every scatter CTA scans the counts itself; up to kScanListTiles a one-CTA
+    // kernel of 1024 threads scans them in shared memory between the two passes; beyond, the
+    // counting CTA that finishes last scans them in global memory
     const bool local_scan = nt <= kLocalScanTiles;
-    const bool staged = !local_scan && nt <= kStagedScanTiles;
-    const size_t csm = staged ? sizeof(int) * size_t(nt + 1) : 0;
+    const bool scan_kernel = !local_scan && nt <= kScanListTiles;
     // the work lists of the FP32 tile kernels, written by whichever CTA scans the counts in
-    // shared memory (more tiles: a kernel of their own after the binning)
+    // shared memory (with more tiles: a kernel of their own after the binning)
     const bool lists = want_lists<T>(p, N);
-    int2 *cmap = lists && nt <= kStagedScanTiles ? p->chunk_map : nullptr;
-    if ((e = allow_smem(k_bin_count<T>, csm)) != cudaSuccess) return cuda_fail(e, "bin_count smem attribute");
-    k_bin_count<T><<<blocks_for(N, 256), 256, csm, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
-                                                                 p->tile_off, p->counters, !local_scan, staged,
-                                                                 staged ? cmap : nullptr, p->counters + 2,
-                                                                 p->heavy_tiles, p->counters + 3);
+    int2 *cmap = lists ? p->chunk_map : nullptr;
+    if ((e = allow_smem(k_bin_count<T>, 0)) != cudaSuccess) return cuda_fail(e, "bin_count smem attribute");
+    k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
+                                                               p->tile_off, p->counters, !local_scan && !scan_kernel,
+                                                               false, nullptr, p->counters + 2, p->heavy_tiles,
+                                                               p->counters + 3);
     SE_LAUNCH_CHECK("bin_count");
+    if (scan_kernel) {
+        const size_t ssm = sizeof(int) * size_t(nt + 1);
+        if ((e = allow_smem(k_scan_lists, ssm)) != cudaSuccess) return cuda_fail(e, "scan smem attribute");
+        e = launch_pdl(k_scan_lists, dim3(1), dim3(1024), ssm, p->stream, 1, nt, (const int *)p->tile_cnt,
+                       p->tile_off, cmap, p->counters + 2, p->heavy_tiles, p->counters + 3);
+        if (e != cudaSuccess) return cuda_fail(e, "scan launch");
+        SE_LAUNCH_CHECK("scan_lists");
+    }
     {
         cudaError_t e = launch_pdl(k_bin_scatter<T>, dim3(blocks_for(N, 256)), dim3(256),
                                    local_scan ? sizeof(int) * (nt + 1) : 0, p->stream, 1, a, N, x, q, p->tile_off,
@@ -98,7 +107,7 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
         if (e != cudaSuccess) return cuda_fail(e, "bin_scatter launch");
     }
     SE_LAUNCH_CHECK("bin_scatter");
-    if (lists && nt > kStagedScanTiles) {
+    if (lists && !local_scan && !scan_kernel) {
         const size_t msm = sizeof(int) * size_t(nt + 1);
         if ((e = allow_smem(k_work_lists, msm)) != cudaSuccess) return cuda_fail(e, "work lists smem attribute");
         e = launch_pdl(k_work_lists, dim3(1), dim3(1024), msm, p->stream, 1, nt, (const int *)p->tile_off,
@@ -131,6 +140,38 @@ static int split_fast(const se_plan_s *p, int64_t N)
     const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
     if (N < 192 * nt) return 1;
     return N < 1024 * nt ? 2 : 4;
+}
+
+// Cluster size of the heavy-tile gridding launch: 16 CTAs where the device runs
+// clusters of that (non-portable) size with this kernel's resources, else 8;
+// decided once per kernel.
+template <typename K>
+static unsigned heavy_cluster(K kern, size_t smem)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, unsigned> known;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = known.find(reinterpret_cast<const void *>(kern));
+    if (it != known.end()) return it->second;
+    unsigned hc = 8;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 16;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) hc = 16;
+    }
+    cudaGetLastError();
+    known[reinterpret_cast<const void *>(kern)] = hc;
+    return hc;
 }
 
 // Gridding (per-tile blocks into `scratch`) followed by the block merge into dst.
@@ -180,7 +221,8 @@ static se_status spread_impl(se_plan_s *p, int64_t N, const T *g, void *dst, voi
                     if (e != cudaSuccess) return cuda_fail(e, "spread launch");
                     if (hmax > 0) {
                         SE_LAUNCH_CHECK("spread");
-                        e = launch_pdl(kern, dim3(unsigned(hmax * 8)), dim3(kThreads), smf, p->stream, 8u, p->tg,
+                        const unsigned hc = heavy_cluster(kern, smf);
+                        e = launch_pdl(kern, dim3(unsigned(hmax) * hc), dim3(kThreads), smf, p->stream, hc, p->tg,
                                        (const int *)p->tile_off, fq, (const int4 *)p->prt.idx_anc, g, wa,
                                        reinterpret_cast<float *>(scratch), (const int *)p->heavy_tiles,
                                        (const int *)(p->counters + 3), 0);

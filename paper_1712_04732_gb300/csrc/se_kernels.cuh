@@ -196,6 +196,24 @@ __device__ __forceinline__ void work_lists_cta(int nt, const int *so, int C, int
     __syncthreads();
 }
 
+// Exclusive scan of the ntiles tile counts into the tile offsets off[0..ntiles]
+// by one CTA of 1024 threads in (ntiles + 1) ints of dynamic shared memory,
+// and, when map is given, the work lists of the FP32 tile kernels
+// (work_lists_cta).  Used between the counting and scatter passes when there
+// are too many tiles for every scatter CTA to scan them itself.
+static __global__ void __launch_bounds__(1024) k_scan_lists(int nt, const int *__restrict__ cnt, int *__restrict__ off,
+                                                            int2 *__restrict__ map, int *__restrict__ nmap,
+                                                            int *__restrict__ heavy, int *__restrict__ nheavy)
+{
+    pdl_wait();
+    extern __shared__ int scnt_raw[];
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) scnt_raw[t] = cnt[t];
+    __syncthreads();
+    block_scan_smem(nt, scnt_raw, scnt_raw);               // in place: each entry is read before it is written
+    for (int t = threadIdx.x; t <= nt; t += blockDim.x) off[t] = scnt_raw[t];
+    if (map) work_lists_cta(nt, scnt_raw, kGatherChunk, map, nmap, heavy, nheavy, kHeavyTile);
+}
+
 // The same as a kernel of one CTA over tile offsets in global memory (read
 // once, coalesced, into (nt + 1) ints of dynamic shared memory).
 static __global__ void __launch_bounds__(1024) k_work_lists(int nt, const int *__restrict__ off, int C,
@@ -698,9 +716,7 @@ __device__ __forceinline__ void spread_cl_tile(const TileGeom &tg, int tile, int
     // The cluster's copies are summed row by row (row r = z B1 + y sits at r pitch
     // in shared memory and at r B0 in the compact block); CTA `rank` writes rows
     // [rank R / CL, (rank + 1) R / CL), 32 / B0 rows per warp instruction.
-    const A *src[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
+
     const int B0 = tg.B[0], R = tg.B[1] * tg.B[2];
     const int rpw = 32 / B0, sub = lane / B0, x = lane - sub * B0;
     const int r0 = rank * R / CL, r1 = (rank + 1) * R / CL;
@@ -708,16 +724,13 @@ __device__ __forceinline__ void spread_cl_tile(const TileGeom &tg, int tile, int
         for (int r = r0 + warp * rpw + sub; r < r1; r += nw * rpw) {
             const int si = r * pitch + x;
             if (fix) {
-                A v = src[0][si];
-#pragma unroll
-                for (int j = 1; j < 8; ++j)
-                    if (j < CL) v += src[j][si];
+                A v = blk[si];
+                for (int j = 1; j < CL; ++j) v += *cluster.map_shared_rank(blk + si, (rank + j) % CL);
                 dst[r * B0 + x] = T(v) * inv_scale;
             } else {
-                T v = reinterpret_cast<const T *>(src[0])[si];
-#pragma unroll
-                for (int j = 1; j < 8; ++j)
-                    if (j < CL) v += reinterpret_cast<const T *>(src[j])[si];
+                T v = reinterpret_cast<const T *>(blk)[si];
+                for (int j = 1; j < CL; ++j)
+                    v += *reinterpret_cast<const T *>(cluster.map_shared_rank(blk + si, (rank + j) % CL));
                 dst[r * B0 + x] = v;
             }
         }
@@ -944,19 +957,14 @@ __device__ __forceinline__ void spread_tile_f32_fast(int tile, const TileGeom &t
     cluster.sync();                                          // every copy complete and visible to the cluster
     // the cluster's copies summed row by row (row r = z B + y at r PITCH in shared
     // memory, r B in the compact block); CTA `rank` writes rows [rank R / CL, (rank + 1) R / CL)
-    const int *src[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) src[j] = cluster.map_shared_rank(blk, j < CL ? j : 0);
     constexpr int R = G::B * G::B, RPW = 32 / G::B;
     const int sub = lane / G::B, x = lane - sub * G::B;
     const int row0 = rank * R / CL, row1 = (rank + 1) * R / CL;
     if (sub < RPW)
         for (int r = row0 + warp * RPW + sub; r < row1; r += NW * RPW) {
             const int si = r * G::PITCH + x;
-            int v = src[0][si];
-#pragma unroll
-            for (int j = 1; j < 8; ++j)
-                if (j < CL) v += src[j][si];
+            int v = blk[si];
+            for (int j = 1; j < CL; ++j) v += *cluster.map_shared_rank(blk + si, (rank + j) % CL);
             dst[r * G::B + x] = float(v) * inv_scale;
         }
     cluster.sync();                                          // no CTA leaves while its block is still read
