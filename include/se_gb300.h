@@ -95,9 +95,10 @@ typedef struct {
     int    gather_mode; /* [<= 0] gathering kernel: 1 tile block staged in shared memory,
                            `split` CTAs per tile; 2 direct reads of the grid; 3 (FP32, tiles of
                            edge 8, P = 8 or 10) the staged block with four particles per warp
-                           over chunks of at most 256 particles; by default FP32 plans of that
-                           kind with 64 or more particles per tile take the staged block with
-                           one particle per warp over the same chunks, the others mode 2 */
+                           over chunks of at most 256 particles; 4 (FP32, same conditions) the
+                           staged block with one particle per warp over the same chunks, which
+                           by default FP32 plans of that kind with 64 or more particles per tile
+                           take (the others mode 2) */
     int    split;       /* [<= 0] CTAs per tile for spread_mode 2 / gather_mode 1 (1..8) */
     int    force_method; /* [<= 0 -> 1] how se_force differentiates (Sec. 7.2): 1 gathers with
                            the window's derivative, Eq. (force-method-1); 2 multiplies the

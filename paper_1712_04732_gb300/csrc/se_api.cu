@@ -312,9 +312,9 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     p->spread_mode = o.spread_mode;
     p->gather_mode = o.gather_mode;
     p->split = o.split;
-    if (o.spread_mode > 3 || o.gather_mode > 3 || o.split > 8) {
+    if (o.spread_mode > 3 || o.gather_mode > 4 || o.split > 8) {
         delete p;
-        return fail(SE_EINVAL, "spread_mode must be 0..3, gather_mode 0..3, split 0..8");
+        return fail(SE_EINVAL, "spread_mode must be 0..3, gather_mode 0..4, split 0..8");
     }
     if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
     if (o.force_method > 2) { delete p; return fail(SE_EINVAL, "force_method must be 1 or 2 (Sec. 7.2)"); }

@@ -17,6 +17,7 @@ constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
 constexpr int kGatherChunk = 256;  // particles per CTA of the tile-staged FP32 gathering (one round per warp)
 constexpr int kHeavyTile = 1536;   // FP32 gridding: tiles with more particles get a cluster of 8 CTAs
+constexpr int kTileGatherMean = 64;  // FP32 gathering: staged tiles from this many particles per tile on average
 
 // Row pitch (elements) of a gridding block in shared memory: the smallest
 // pitch >= B0 for which the gridding kernels' access pattern -- a warp's lanes
@@ -148,6 +149,10 @@ struct se_plan_s {
     int spread_mode = 0, gather_mode = 0, split = 0;   // kernel variants (0: chosen per call)
     int force_method = 1;                // Sec. 7.2: 1 derivative of the window, 2 i k in the scaling
     cudaStream_t stream = nullptr;
+    // D = 1, 2: the AFT classes I and zero mode run on these two streams, forked from
+    // and joined back into `stream` by events around each transform stage
+    cudaStream_t aux[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {};
 
     // ---- device memory ----
     size_t elem = 4;                     // sizeof(T)

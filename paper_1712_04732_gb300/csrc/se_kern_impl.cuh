@@ -38,16 +38,17 @@ static size_t gather_smem(const se_plan_s *p, int nblocks)
 }
 
 // The FP32 tile-staged gathering serves plans with edge-8 tiles, P = 8 or 10,
-// at least 64 particles per tile on average and at most 50000 tiles (its chunk
-// list is built from the tile offsets in shared memory), unless another
-// gathering mode is asked for.
+// at least kTileGatherMean particles per tile on average (any number with
+// gather_mode 4) and at most 50000 tiles (its chunk list is built from the tile
+// offsets in shared memory), unless another gathering mode is asked for.
 template <typename T>
 static bool use_tile_gather(const se_plan_s *p, int64_t N)
 {
     const int64_t nt = int64_t(p->tg.nt[0]) * p->tg.nt[1] * p->tg.nt[2];
-    return std::is_same<T, float>::value && (p->gather_mode <= 0 || p->gather_mode == 3) && (p->P == 8 || p->P == 10) &&
-           p->tg.T[1] == 8 && p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) && N >= 64 * nt &&
-           nt <= 50000;
+    const int gm = p->gather_mode;
+    return std::is_same<T, float>::value && (gm <= 0 || gm == 3 || gm == 4) && (p->P == 8 || p->P == 10) &&
+           p->tg.T[0] == 8 && p->tg.T[1] == 8 && p->tg.T[2] == 8 && p->tg.pitch == gridding_pitch(7 + p->P, p->P, 4) &&
+           (gm == 4 || N >= kTileGatherMean * nt) && nt <= 50000;
 }
 
 // The FP32 gridding kernel with compile-time block geometry: tiles of edge 8,
@@ -372,6 +373,27 @@ static se_status convolve_zcol(se_plan_s *p, void *gin, void *gout, bool ik)
 
 // Alg. 4 step 2: forward FFT (D = 3, 0) or AFT (Alg. 1, D = 1, 2) of gin into
 // spec (and U, Z).
+// Fork the AFT classes I and zero mode off the plan's stream onto its two
+// auxiliary streams, and join them back (D = 1, 2; no-ops otherwise).
+static se_status aft_fork(se_plan_s *p)
+{
+    if (!p->aux[0]) return SE_OK;
+    cudaError_t e = cudaEventRecord(p->ev_fork, p->stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->aux[k], p->ev_fork, 0);
+    return e == cudaSuccess ? SE_OK : cuda_fail(e, "AFT fork");
+}
+
+static se_status aft_join(se_plan_s *p)
+{
+    if (!p->aux[0]) return SE_OK;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(p->ev_join[k], p->aux[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev_join[k], 0);
+    }
+    return e == cudaSuccess ? SE_OK : cuda_fail(e, "AFT join");
+}
+
 template <typename T>
 static se_status forward(se_plan_s *p, void *gin)
 {
@@ -401,12 +423,15 @@ static se_status forward(se_plan_s *p, void *gin)
                                                                p->s0v[1], p->s0v[2], row, spec, U, Z);
     }
     SE_LAUNCH_CHECK("pad");
-    // Alg. 1 steps 2-4: free-direction transforms of every class
+    // Alg. 1 steps 2-4: free-direction transforms of every class, the classes I and
+    // zero mode on the auxiliary streams (their cuFFT plans are bound to them)
+    se_status st;
+    if ((st = aft_fork(p)) != SE_OK) return st;
     if ((r = fft_c2c(p->free_main, spec + (p->D == 1 ? p->nI + 1 : 0), CUFFT_FORWARD)) != CUFFT_SUCCESS)
         return cufft_fail(r, "free fwd");
     if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "I fwd");
     if ((r = fft_c2c(p->free_Z, Z, CUFFT_FORWARD)) != CUFFT_SUCCESS) return cufft_fail(r, "zero fwd");
-    return SE_OK;
+    return aft_join(p);
 }
 
 // Alg. 4 step 3, Eq. (scale), in place on spec (and U, Z).  With ik, also the
@@ -426,29 +451,32 @@ static se_status scale(se_plan_s *p, bool ik)
         SE_LAUNCH_CHECK("scale");
         return SE_OK;
     }
+    se_status st;
+    if ((st = aft_fork(p)) != SE_OK) return st;
     const ScaleBox<T> &sb = sb_spec<T>(p);
     const unsigned nb = blocks_for(int64_t(sb.n0) * sb.n1 * sb.n2, 256);
     if (ik) k_scale_box_ik<T><<<nb, 256, 0, p->stream>>>(sb, ib_spec<T>(p), spec, reinterpret_cast<C *>(p->spec_d));
     else k_scale_box<T><<<nb, 256, 0, p->stream>>>(sb, spec);
     SE_LAUNCH_CHECK("scale");
     if (p->D == 3) return SE_OK;
-    // the classes I and zero mode of the AFT (D = 1, 2)
+    // the classes I and zero mode of the AFT (D = 1, 2), on the auxiliary streams
     C *U = reinterpret_cast<C *>(p->U);
     C *Z = reinterpret_cast<C *>(p->Z);
+    cudaStream_t sI = p->aux[0] ? p->aux[0] : p->stream, sZ = p->aux[1] ? p->aux[1] : p->stream;
     if (p->have_free_I) {
         const ScaleBox<T> &su = sb_U<T>(p);
         const unsigned nu = blocks_for(int64_t(su.n0) * su.n1 * su.n2, 256);
-        if (ik) k_scale_box_ik<T><<<nu, 256, 0, p->stream>>>(su, ib_U<T>(p), U, reinterpret_cast<C *>(p->U_d));
-        else k_scale_box<T><<<nu, 256, 0, p->stream>>>(su, U);
+        if (ik) k_scale_box_ik<T><<<nu, 256, 0, sI>>>(su, ib_U<T>(p), U, reinterpret_cast<C *>(p->U_d));
+        else k_scale_box<T><<<nu, 256, 0, sI>>>(su, U);
         SE_LAUNCH_CHECK("scale I");
     }
     if (ik)
-        k_scale_tab_ik<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(tab, ib_Z<T>(p), Z,
-                                                                             reinterpret_cast<C *>(p->Z_d));
+        k_scale_tab_ik<T><<<blocks_for(p->Z_elems, 256), 256, 0, sZ>>>(tab, ib_Z<T>(p), Z,
+                                                                      reinterpret_cast<C *>(p->Z_d));
     else
-        k_scale_tab<T><<<blocks_for(p->Z_elems, 256), 256, 0, p->stream>>>(int64_t(p->Z_elems), tab, Z);
+        k_scale_tab<T><<<blocks_for(p->Z_elems, 256), 256, 0, sZ>>>(int64_t(p->Z_elems), tab, Z);
     SE_LAUNCH_CHECK("scale 0");
-    return SE_OK;
+    return aft_join(p);
 }
 
 // Alg. 4 step 4: inverse FFT (D = 3, 0) or AIFT (Alg. 2, D = 1, 2) of the
@@ -466,11 +494,14 @@ static se_status inverse(se_plan_s *p, typename Cplx<T>::type *spec, typename Cp
     }
     if (p->D != 3) {
         const int row = p->Mv[0] / 2 + 1;
-        // Alg. 2 steps 1-3
+        // Alg. 2 steps 1-3 (the classes I and zero mode on the auxiliary streams)
+        se_status st;
+        if ((st = aft_fork(p)) != SE_OK) return st;
         if ((r = fft_c2c(p->free_main, spec + (p->D == 1 ? p->nI + 1 : 0), CUFFT_INVERSE)) != CUFFT_SUCCESS)
             return cufft_fail(r, "free inv");
         if (p->have_free_I && (r = fft_c2c(p->free_I, U, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "I inv");
         if ((r = fft_c2c(p->free_Z, Z, CUFFT_INVERSE)) != CUFFT_SUCCESS) return cufft_fail(r, "zero inv");
+        if ((st = aft_join(p)) != SE_OK) return st;
         // Alg. 2 steps 2-4: truncate to M~ and merge back
         if (p->D == 2) {
             const int64_t n = int64_t(p->nI) * p->Mtv[2] + p->Mtv[2];

@@ -660,9 +660,13 @@ se_status plan_set_fft_stream(se_plan_s *p)
 {
     cufftHandle hs[5] = {p->fwd, p->inv, p->free_main, p->free_I, p->free_Z};
     bool have[5] = {p->have_fwd, p->have_inv, p->have_free_main, p->have_free_I, p->have_free_Z};
+    // the classes I and zero mode of the AFT on their own streams (D = 1, 2)
+    cudaStream_t st[5] = {p->stream, p->stream, p->stream, p->aux[0] ? p->aux[0] : p->stream,
+                          p->aux[1] ? p->aux[1] : p->stream};
+    if (p->D == 0) st[3] = st[4] = p->stream;
     for (int i = 0; i < 5; ++i)
         if (have[i]) {
-            cufftResult r = cufftSetStream(hs[i], p->stream);
+            cufftResult r = cufftSetStream(hs[i], st[i]);
             if (r != CUFFT_SUCCESS) return cufft_fail(r, "cufftSetStream");
         }
     return SE_OK;
@@ -824,6 +828,14 @@ se_status plan_build(se_plan_s *p)
     }
     if ((st = build_tables(p)) != SE_OK) return st;
     if ((st = make_plans(p)) != SE_OK) return st;
+    if (p->D == 1 || p->D == 2) {
+        cudaError_t e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "AFT class streams");
+    }
     if ((st = plan_set_fft_stream(p)) != SE_OK) return st;
     encode_gout_map(p);
     return SE_OK;
@@ -888,6 +900,14 @@ se_status plan_second_grid(se_plan_s *p)
 void plan_release(se_plan_s *p)
 {
     real_release(p);
+    for (int k = 0; k < 2; ++k) {
+        if (p->aux[k]) cudaStreamDestroy(p->aux[k]);
+        if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+        p->aux[k] = nullptr;
+        p->ev_join[k] = nullptr;
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    p->ev_fork = nullptr;
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
     if (p->have_free_main) cufftDestroy(p->free_main);

@@ -63,7 +63,7 @@ def test_force_and_potential_match_discrete_oracle(D, window, dtype):
 
 
 @pytest.mark.parametrize("spread_mode,gather_mode,split", [
-    (1, 1, 1), (2, 1, 2), (2, 1, 4), (2, 2, 8), (3, 1, 1), (3, 2, 1), (1, 2, 3), (2, 3, 2), (2, 0, 1)])
+    (1, 1, 1), (2, 1, 2), (2, 1, 4), (2, 2, 8), (3, 1, 1), (3, 2, 1), (1, 2, 3), (2, 3, 2), (2, 0, 1), (2, 4, 1)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_every_kernel_variant(spread_mode, gather_mode, split, dtype):
     """Gridding variants (shared atomics, cluster-split atomics, per-warp private
