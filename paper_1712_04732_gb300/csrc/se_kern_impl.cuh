@@ -377,7 +377,7 @@ static se_status convolve_zcol(se_plan_s *p, void *gin, void *gout, bool ik)
 // auxiliary streams, and join them back (D = 1, 2; no-ops otherwise).
 static se_status aft_fork(se_plan_s *p)
 {
-    if (!p->aux[0]) return SE_OK;
+    if (!p->aux[0] || (p->D != 1 && p->D != 2)) return SE_OK;
     cudaError_t e = cudaEventRecord(p->ev_fork, p->stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->aux[k], p->ev_fork, 0);
     return e == cudaSuccess ? SE_OK : cuda_fail(e, "AFT fork");
@@ -385,7 +385,7 @@ static se_status aft_fork(se_plan_s *p)
 
 static se_status aft_join(se_plan_s *p)
 {
-    if (!p->aux[0]) return SE_OK;
+    if (!p->aux[0] || (p->D != 1 && p->D != 2)) return SE_OK;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaEventRecord(p->ev_join[k], p->aux[k]);
@@ -462,7 +462,8 @@ static se_status scale(se_plan_s *p, bool ik)
     // the classes I and zero mode of the AFT (D = 1, 2), on the auxiliary streams
     C *U = reinterpret_cast<C *>(p->U);
     C *Z = reinterpret_cast<C *>(p->Z);
-    cudaStream_t sI = p->aux[0] ? p->aux[0] : p->stream, sZ = p->aux[1] ? p->aux[1] : p->stream;
+    const bool par = p->aux[0] && (p->D == 1 || p->D == 2);
+    cudaStream_t sI = par ? p->aux[0] : p->stream, sZ = par ? p->aux[1] : p->stream;
     if (p->have_free_I) {
         const ScaleBox<T> &su = sb_U<T>(p);
         const unsigned nu = blocks_for(int64_t(su.n0) * su.n1 * su.n2, 256);

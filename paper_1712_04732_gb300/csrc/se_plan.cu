@@ -663,7 +663,7 @@ se_status plan_set_fft_stream(se_plan_s *p)
     // the classes I and zero mode of the AFT on their own streams (D = 1, 2)
     cudaStream_t st[5] = {p->stream, p->stream, p->stream, p->aux[0] ? p->aux[0] : p->stream,
                           p->aux[1] ? p->aux[1] : p->stream};
-    if (p->D == 0) st[3] = st[4] = p->stream;
+    if (p->D == 0 || p->D == 3) st[3] = st[4] = p->stream;
     for (int i = 0; i < 5; ++i)
         if (have[i]) {
             cufftResult r = cufftSetStream(hs[i], st[i]);
@@ -828,7 +828,7 @@ se_status plan_build(se_plan_s *p)
     }
     if ((st = build_tables(p)) != SE_OK) return st;
     if ((st = make_plans(p)) != SE_OK) return st;
-    if (p->D == 1 || p->D == 2) {
+    if (p->D == 1 || p->D == 2) {   // auxiliary streams of the AFT classes
         cudaError_t e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking);
