@@ -38,10 +38,11 @@ sys.path.insert(0, ROOT)
 METRIC = "particles/s (phi+F) at rms rel err <=1e-5, FP32 vs FP64 form; spread/gather GB/s"
 WORKLOAD = "wire_1p"
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the tile kernels on
-# the headline workload, from one ncu capture of this benchmark's FP32 step
-# (profiles/); None until taken for the kernels as they are now
-NCU_TRAFFIC = {"spread": None, "gather": None}
+# dram__bytes_read.sum + dram__bytes_write.sum of the tile kernels on the
+# headline workload, from one ncu capture of this benchmark's FP32 step
+# (profiles/wire_1p_tile_kernels.md); the gridding stage is two launches (light
+# tiles 39.00 MB, heavy tiles 4.81 MB).  Set to None when a kernel changes.
+NCU_TRAFFIC = {"spread": 43.818e6, "gather": 61.208e6}
 # targets of the oracle's sample on the headline workload (about 20 s of the
 # host's cores through the xi route of oracle A)
 CPU_TARGETS = 128
@@ -350,6 +351,8 @@ def rooflines(stage_ms, N, P, nu, peaks, traffic):
         ach = flop / sec / 1e12
         e = {"kernel": kern, "bound": "alu", "achieved": ach, "peak": fp32, "unit": "TFLOP/s", "frac": ach / fp32,
              "traffic": traffic.get(k), "launch_ms": stage_ms[k],
+             "traffic_what": "bytes per stage, dram read + write, one cold-cache ncu capture"
+                             + (" (two launches: light and heavy tiles)" if k == "spread" else ""),
              "per_launch": f"{flop:.4e} flop ({cnt[k]} FMA/particle x {N})",
              "peak_source": "measured: se_measure_peak FP32 FMA chains on this GPU (of measured)"}
         if k == "spread":
