@@ -56,6 +56,8 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-form", choices=["auto", "lines", "fused", "branches"], default="auto",
+                    help="execution form of the batched systems (auto: the autotuner's choice)")
     ap.add_argument("--only", choices=["batch", "slab_2p", "wire_1p"], default=None,
                     help="time only the batched form or one workload's FP32 step (profiling aid; "
                          "prints its own JSON line)")
@@ -428,7 +430,7 @@ def run_slab(se, wl, dev, flush, steps, warmup, world):
             "transform_lengths": {"Mt": list(inf["Mt_v"]), "s0Mt": list(inf["s0_mt_v"]), "sMt": list(inf["s_mt_v"])}}
 
 
-def run_batch(se, wl, dev, flush, steps):
+def run_batch(se, wl, dev, flush, steps, form="auto"):
     """64 independent systems, N log-uniform in [1e3, 1e5], D alternating 3, 2,
     xi = 8 (N/1e4)^(1/3), PKB, per-system M and P from the Sec. 6 rules at
     relative tolerance 1e-5, FP32, phi + F: the autotuned batched graph against
@@ -442,7 +444,7 @@ def run_batch(se, wl, dev, flush, steps):
     q = torch.tensor(np.concatenate([s[1] for s in sysl]), dtype=torch.float32, device=dev)
     ntot = x.shape[0]
     t0 = time.perf_counter()
-    b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, device=dev)
+    b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, device=dev, form=form)
     out = (torch.empty((ntot, 3), device=dev), torch.empty(ntot, device=dev),
            torch.empty(len(specs), dtype=torch.float64, device=dev))
     b.force(x, q, out=out)                          # autotune + capture
@@ -492,7 +494,7 @@ def run_ours(a):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     if a.only is not None:
         if a.only == "batch":
-            res = {"batch_form": run_batch(se, wl, dev, flush, a.steps)}
+            res = {"batch_form": run_batch(se, wl, dev, flush, a.steps, a.batch_form)}
         elif a.only == "slab_2p":
             res = {"slab_2p": run_slab(se, wl, dev, flush, a.steps, a.warmup, world)}
         else:
@@ -581,7 +583,7 @@ def run_ours(a):
         line["free_0p"] = run_free_space(se, wl, dev, flush, min(a.steps, 200), min(a.warmup, 10), world, rank,
                                          with_cpu)
         line["slab_2p"] = run_slab(se, wl, dev, flush, min(a.steps, 50), min(a.warmup, 5), world)
-        line["batch_form"] = run_batch(se, wl, dev, flush, min(a.steps, 50))
+        line["batch_form"] = run_batch(se, wl, dev, flush, min(a.steps, 50), a.batch_form)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

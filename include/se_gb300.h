@@ -268,19 +268,23 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
  * against an FP64 reference of each system and keeps the fastest candidate
  * whose errors are both within eps_rel / 2 (se_batch_get_accuracy reports
  * them).  The window is w for all systems.  Every call replays one CUDA graph (captured on
- * first use and whenever the pointers change) in one of two forms:
- *  - multi-system (SE_BATCH_FUSED): binning, gridding, block merge and
- *    gathering of all systems run as one kernel launch per stage and class of
- *    systems with equal support P_i (Alg. 4 steps 1 and 5), each system's
- *    transforms and scaling (steps 2-4) in parallel graph branches;
+ * first use and whenever the pointers change) in one of three forms:
+ *  - single pipeline (SE_BATCH_LINES; every system D = 3 or 2, force method 1):
+ *    binning, gridding, block merge and gathering of all systems as one kernel
+ *    launch per stage and class of systems with equal support P_i (Alg. 4
+ *    steps 1 and 5), and the transforms and scaling of all systems (steps 2-4,
+ *    with the adaptive transform of Alg. 1 / Alg. 2 for D = 2) in five
+ *    launches, each a list of line transforms of every system; no cuFFT call;
+ *  - multi-system (SE_BATCH_FUSED): the same stages, each system's transforms
+ *    and scaling (cuFFT) in parallel graph branches;
  *  - per-system (SE_BATCH_BRANCHES): each system's whole pipeline in parallel
  *    graph branches.
  * Unless SE_BATCH_NO_AUTOTUNE is given, the first se_batch_force call times the
  * gridding tile (4, 8, 16) and kernel variants per system on the real inputs,
- * then the forms as captured graphs (the multi-system one with 1, 2, 4 or 8
- * CTAs per gridding tile, also with tiles of edge 4 for systems of more than
+ * then the forms as captured graphs (the two multi-system ones with 1, 2, 4 or
+ * 8 CTAs per gridding tile, also with tiles of edge 4 for systems of more than
  * 512 particles per tile), and keeps the fastest; without autotuning the
- * form is the multi-system one unless SE_BATCH_BRANCHES is given.
+ * form is the multi-system one unless a form flag is given.
  * Arrays x [sum N][3], q [sum N], F [sum N][3], phi [sum N] (may be NULL) are
  * concatenated in system order (device pointers); energy [nsys] (device, may be
  * NULL) receives E_i = 1/2 sum q phi per system.  The first call synchronises
@@ -288,6 +292,7 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
 #define SE_BATCH_NO_AUTOTUNE 1u
 #define SE_BATCH_BRANCHES    2u   /* use the per-system form only */
 #define SE_BATCH_FUSED       4u   /* use the multi-system form only */
+#define SE_BATCH_LINES       8u   /* use the single-pipeline form only */
 typedef struct se_batch_s *se_batch_t;
 se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int *D, const double *L,
                           const double *xi, const double *Q, double eps_rel, se_window w, se_dtype dt,
@@ -307,9 +312,10 @@ se_status se_batch_force_each(se_batch_t batch, const void *x, const void *q, vo
 se_status se_batch_get_accuracy(se_batch_t batch, int i, double *err_phi, double *err_F);
 /* Derived parameters of system i. */
 se_status se_batch_get_system(se_batch_t batch, int i, se_plan_info_t *info);
-/* Form of the captured graph (1 per-system, 2 multi-system) and the number of
- * library kernels one call launches (cuFFT's own kernels excluded; valid after
- * the first se_batch_force).  Batching has no counterpart in the paper.  Either
+/* Form of the captured graph (1 per-system, 2 multi-system, 3 single
+ * pipeline) and the number of library kernels one call launches (cuFFT's own
+ * kernels excluded; the single pipeline launches none; valid after the first
+ * se_batch_force).  Batching has no counterpart in the paper.  Either
  * pointer (host memory, written by the call) may be NULL.  Errors: SE_EINVAL
  * for a NULL batch. */
 se_status se_batch_get_form(se_batch_t batch, int *form, int64_t *kernels_per_call);

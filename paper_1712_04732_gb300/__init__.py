@@ -220,11 +220,15 @@ class Batch:
     M and P from the rules of Sec. 6 for relative tolerance ``eps_rel``, autotuned
     kernel variants and one CUDA graph per call.  ``systems`` is a list of
     (N, D, L, xi) tuples; ``Q`` optional per-system sums of q^2.  ``form``:
-    "auto" (the tuner chooses), "fused" (binning, gridding, merge and gathering
-    of all systems in one launch per stage and support class) or "branches"
-    (every system's own pipeline in parallel graph branches)."""
+    "auto" (the tuner chooses), "lines" (binning, gridding, merge and gathering
+    of all systems in one launch per stage and support class, and the
+    transforms of all systems in five launches; D = 3 and 2 only), "fused"
+    (the same stages, each system's transforms in parallel graph branches) or
+    "branches" (every system's own pipeline in parallel graph branches)."""
 
-    _FORMS = {"auto": 0, "branches": nat.SE_BATCH_BRANCHES, "fused": nat.SE_BATCH_FUSED}
+    _FORMS = {"auto": 0, "branches": nat.SE_BATCH_BRANCHES, "fused": nat.SE_BATCH_FUSED,
+              "lines": nat.SE_BATCH_LINES}
+    _FORM_NAMES = {1: "branches", 2: "fused", 3: "lines"}
 
     def __init__(self, systems, eps_rel=1e-5, window="pkb", dtype=torch.float32, device=None, Q=None,
                  autotune=True, form="auto"):
@@ -258,11 +262,11 @@ class Batch:
             pass
 
     def form(self):
-        """("fused" | "branches", library kernels per call) of the captured graph."""
+        """("lines" | "fused" | "branches", library kernels per call) of the captured graph."""
         f = ctypes.c_int()
         k = ctypes.c_int64()
         nat.check(self._lib.se_batch_get_form(self._h, ctypes.byref(f), ctypes.byref(k)))
-        return ("fused" if f.value == 2 else "branches"), int(k.value)
+        return self._FORM_NAMES[f.value], int(k.value)
 
     def system_info(self, i):
         inf = nat.Info()

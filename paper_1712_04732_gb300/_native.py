@@ -13,7 +13,7 @@ from . import build as _build
 SE_WIN_GAUSSIAN, SE_WIN_PKB = 0, 1
 SE_F32, SE_F64 = 0, 1
 SE_ADD_SELF, SE_CHECK_NEUTRAL, SE_SYNC_CHECK, SE_HOST_IO = 1, 2, 4, 8
-SE_BATCH_NO_AUTOTUNE, SE_BATCH_BRANCHES, SE_BATCH_FUSED = 1, 2, 4
+SE_BATCH_NO_AUTOTUNE, SE_BATCH_BRANCHES, SE_BATCH_FUSED, SE_BATCH_LINES = 1, 2, 4, 8
 SE_ACCUMULATE = 16
 
 STATUS = {0: "SE_OK", 1: "SE_EINVAL", 2: "SE_ENONNEUTRAL", 3: "SE_EOUTOFBOX", 4: "SE_ENOMEM",

@@ -1,10 +1,11 @@
 // Batched evaluation of many independent systems (se_batch_*): per-system
 // parameters from the rules of Sec. 6, a timing autotuner over the gridding
-// tile, kernel variants and execution form, and one CUDA graph per call.  Two
-// forms: the multi-system pipeline (binning, gridding, merge and gathering of
-// all systems in one launch per stage and window-support class, the transforms
-// of each system in parallel graph branches), or every system's whole pipeline
-// in parallel graph branches.
+// tile, kernel variants and execution form, and one CUDA graph per call.  Three
+// forms: the single pipeline (binning, gridding, merge and gathering of all
+// systems in one launch per stage and window-support class, and the transforms
+// of all systems in five launches), the multi-system pipeline with each
+// system's transforms in parallel graph branches instead, or every system's
+// whole pipeline in parallel graph branches.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,7 +33,7 @@ struct Variant {
     int tile, spread_mode, split, gather_mode;
 };
 
-enum Form { kFormBranches = 1, kFormFused = 2 };
+enum Form { kFormBranches = 1, kFormFused = 2, kFormLines = 3 };
 
 }  // namespace
 
@@ -51,10 +52,10 @@ struct se_batch_s {
     cudaGraphExec_t exec = nullptr;
     const void *key[5] = {};          // pointers the graph was captured with
     bool tuned = false, autotune = true;
-    int form = kFormFused;            // kFormFused or kFormBranches
+    int form = kFormFused;            // kFormFused, kFormLines or kFormBranches
     int force_form = 0;               // form fixed by the caller (0: chosen by the tuner)
     int fused_cl = 0;                 // CTAs per gridding tile of the multi-system form (0: rule)
-    se::MBatch mb;                    // multi-system workspace (form kFormFused)
+    se::MBatch mb;                    // multi-system workspace (forms kFormFused, kFormLines)
     bool mb_built = false;
     int64_t kernels_per_call = 0;     // library kernels one call launches (cuFFT excluded)
     int64_t graph_launches = 0;
@@ -123,6 +124,9 @@ se_status build_fused(se_batch_s *b)
     se_status st = b->dtype == SE_F32 ? se::MOps<float>::build(&b->mb, b->plans, b->off, b->fused_cl)
                                       : se::MOps<double>::build(&b->mb, b->plans, b->off, b->fused_cl);
     if (st == SE_OK) b->mb_built = true;
+    if (st == SE_OK && b->form == kFormLines)
+        st = b->dtype == SE_F32 ? se::MOps<float>::build_lines(&b->mb, b->plans)
+                                : se::MOps<double>::build_lines(&b->mb, b->plans);
     return st;
 }
 
@@ -383,11 +387,12 @@ std::vector<int> assign_branches(const se_batch_s *b)
     return br;
 }
 
-// Capture of the multi-system form: gridding of every system, the transforms
-// of the systems in parallel branches, gathering of every system.
+// Capture of the multi-system forms: gridding of every system, the transforms
+// of the systems (in parallel branches, or the five multi-system launches of
+// the single-pipeline form), gathering of every system.
 se_status capture_fused(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
 {
-    if (!b->mb_built) {
+    if (!b->mb_built || (b->form == kFormLines && !b->mb.lines_built)) {
         se_status st = build_fused(b);
         if (st != SE_OK) return st;
     }
@@ -401,7 +406,9 @@ se_status capture_fused(se_batch_s *b, const void *x, const void *q, void *F, vo
                        ? se::MOps<float>::grid(&b->mb, static_cast<const float *>(x), static_cast<const float *>(q), b->cap)
                        : se::MOps<double>::grid(&b->mb, static_cast<const double *>(x), static_cast<const double *>(q),
                                                 b->cap);
-    if (st == SE_OK) {
+    if (st == SE_OK && b->form == kFormLines) {
+        st = b->dtype == SE_F32 ? se::MOps<float>::lines(&b->mb, b->cap) : se::MOps<double>::lines(&b->mb, b->cap);
+    } else if (st == SE_OK) {
         cudaEventRecord(b->fork, b->cap);
         for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(b->branch[k], b->fork, 0);
         const std::vector<int> br = assign_branches(b);
@@ -479,7 +486,7 @@ se_status capture_branches(se_batch_s *b, const void *x, const void *q, void *F,
 
 se_status capture(se_batch_s *b, const void *x, const void *q, void *F, void *phi, double *energy)
 {
-    return b->form == kFormFused ? capture_fused(b, x, q, F, phi, energy) : capture_branches(b, x, q, F, phi, energy);
+    return b->form == kFormBranches ? capture_branches(b, x, q, F, phi, energy) : capture_fused(b, x, q, F, phi, energy);
 }
 
 // Median of five timed replays of the captured graph (one untimed replay first).
@@ -532,10 +539,11 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
             if (alt[i]) std::swap(alt[i], b->plans[i]);
     };
     std::vector<Cand> cands;
-    if (b->force_form != kFormBranches)
-        for (int d = 0; d < (have_alt ? 2 : 1); ++d)
-            for (int cl : {0, 1, 2, 4, 8}) cands.push_back({kFormFused, cl, d == 1});
-    if (b->force_form != kFormFused) cands.push_back({kFormBranches, 0, false});
+    for (int form : {kFormLines, kFormFused})
+        if (b->force_form == 0 || b->force_form == form)
+            for (int d = 0; d < (have_alt ? 2 : 1); ++d)
+                for (int cl : {0, 1, 2, 4, 8}) cands.push_back({form, cl, d == 1});
+    if (b->force_form == 0 || b->force_form == kFormBranches) cands.push_back({kFormBranches, 0, false});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     {
         cudaError_t e = cudaEventCreate(&e0);
@@ -561,7 +569,7 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
         // a candidate that cannot be built or captured (workspace, capture errors)
         // is skipped; the call fails only if none can
         se_status cs = SE_OK;
-        if (c.form == kFormFused) {
+        if (c.form != kFormBranches) {
             b->fused_cl = c.cl;
             cs = build_fused(b);
         }
@@ -605,7 +613,7 @@ se_status tune_form(se_batch_s *b, const void *x, const void *q, void *F, void *
     if (pick.dense4)
         for (int i = 0; i < b->nsys; ++i)
             if (b->plans[i]->tg.T[0] == 4) b->chosen[i].tile = 4;
-    return pick.form == kFormFused ? build_fused(b) : SE_OK;
+    return pick.form != kFormBranches ? build_fused(b) : SE_OK;
 }
 
 }  // namespace
@@ -624,11 +632,16 @@ se_status se_batch_create(se_batch_t *out, int nsys, const int64_t *N, const int
     b->nsys = nsys;
     b->dtype = dt;
     b->autotune = !(flags & SE_BATCH_NO_AUTOTUNE);
-    if ((flags & SE_BATCH_FUSED) && (flags & SE_BATCH_BRANCHES)) {
+    const int nforms = ((flags & SE_BATCH_FUSED) ? 1 : 0) + ((flags & SE_BATCH_BRANCHES) ? 1 : 0) +
+                       ((flags & SE_BATCH_LINES) ? 1 : 0);
+    if (nforms > 1) {
         delete b;
-        return se::fail(SE_EINVAL, "SE_BATCH_FUSED and SE_BATCH_BRANCHES exclude each other");
+        return se::fail(SE_EINVAL, "SE_BATCH_FUSED, SE_BATCH_BRANCHES and SE_BATCH_LINES exclude each other");
     }
-    b->force_form = (flags & SE_BATCH_FUSED) ? kFormFused : (flags & SE_BATCH_BRANCHES) ? kFormBranches : 0;
+    b->force_form = (flags & SE_BATCH_FUSED)      ? kFormFused
+                    : (flags & SE_BATCH_BRANCHES) ? kFormBranches
+                    : (flags & SE_BATCH_LINES)    ? kFormLines
+                                                  : 0;
     b->form = b->force_form ? b->force_form : kFormFused;
     b->N.assign(N, N + nsys);
     b->off.resize(nsys + 1, 0);

@@ -311,7 +311,8 @@ struct Ops {
 struct MClass {
     int P = 0, nu = 0;
     int tile_begin = 0, ntiles = 0;      // global tiles of the class
-    int cta_begin = 0, ncta = 0;         // gathering CTAs of the class
+    int cta_begin = 0, ncta = 0;         // gathering CTAs of the class (flat gathering)
+    int fast_begin = 0, nfast = 0;       // tile-staged gathering: the class's entries of MBatch::ftiles
     int64_t particles = 0;
     int CL = 1;                          // CTAs per tile of the gridding cluster
     int J = 2;                           // tiles per axis whose blocks overlap a grid point
@@ -322,8 +323,9 @@ struct MClass {
 struct MBatch {
     int nsys = 0;
     int64_t ntot = 0;
-    int ntiles = 0, ncta = 0;
+    int ntiles = 0, ncta = 0, nfast = 0;
     std::vector<MClass> classes;
+    int *ftiles = nullptr;               // [nfast] global tiles gathered by the tile-staged kernel
     void *desc = nullptr;                // SysDesc<T>[nsys]
     int64_t *p0 = nullptr;               // [nsys + 1] first particle of each system (caller's order)
     int *tile_sys = nullptr;             // [ntiles] system of each global tile
@@ -337,6 +339,14 @@ struct MBatch {
     int *err = nullptr;                  // latched input errors
     int64_t bytes = 0;
     int64_t launches = 0;                // kernels launched by the multi-system stages
+    // multi-system transforms (se_mlines.cuh): per-system descriptors, the line
+    // groups of the five passes (items [loff[k], loff[k] + lcount[k]) of pass k)
+    // and the table of roots of unity
+    void *lsys = nullptr;
+    void *litems = nullptr;
+    void *ltw = nullptr;
+    int lcount[5] = {0, 0, 0, 0, 0}, loff[5] = {0, 0, 0, 0, 0};
+    bool lines_built = false;
 };
 
 template <typename T>
@@ -349,6 +359,12 @@ struct MOps {
     static se_status grid(MBatch *m, const T *x, const T *q, cudaStream_t s);
     // Gathering of phi and F from every plan's grid_out, energies E[nsys].
     static se_status gather(MBatch *m, T *phi, T *F, double *energy, cudaStream_t s);
+    // Multi-system transforms and scaling (Alg. 4 steps 2-4) from every plan's
+    // grid_in to its grid_out: descriptors built once (SE_EINVAL when a system
+    // is not D = 3 or 2, or a transform is longer than the line buffers), then
+    // five launches per call.
+    static se_status build_lines(MBatch *m, const std::vector<se_plan_t> &plans);
+    static se_status lines(MBatch *m, cudaStream_t s);
     static void release(MBatch *m);
 };
 

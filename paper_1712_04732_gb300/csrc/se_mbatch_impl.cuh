@@ -9,6 +9,7 @@
 
 #include "se_launch.cuh"
 #include "se_mkernels.cuh"
+#include "se_mlines.cuh"
 
 namespace se {
 
@@ -56,13 +57,19 @@ template <typename T>
 void MOps<T>::release(MBatch *m)
 {
     void *bufs[] = {m->desc, m->p0, m->tile_sys, m->cta_sys, m->tile_cnt, m->tile_off, m->tile_rank,
-                    m->prt.frac_q, m->prt.idx_anc, m->scratch, m->part, m->done, m->err};
+                    m->prt.frac_q, m->prt.idx_anc, m->scratch, m->part, m->done, m->err,
+                    m->lsys, m->litems, m->ltw, m->ftiles};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    m->lsys = m->litems = m->ltw = nullptr;
+    for (int k = 0; k < 5; ++k) m->lcount[k] = m->loff[k] = 0;
+    m->lines_built = false;
     m->desc = nullptr;
     m->p0 = nullptr;
     m->tile_sys = m->cta_sys = m->tile_cnt = m->tile_off = nullptr;
     m->tile_rank = nullptr;
+    m->ftiles = nullptr;
+    m->nfast = 0;
     m->prt = Particles{};
     m->scratch = nullptr;
     m->part = nullptr;
@@ -96,7 +103,7 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
         by_win[std::make_tuple(p->P, p->nu, p->window, p->shape, -resident)].push_back(i);
     }
     std::vector<SysDesc<T>> d(nsys);
-    std::vector<int> tile_sys, cta_sys;
+    std::vector<int> tile_sys, cta_sys, ftiles;
     int64_t scr = 0, sp = 0;
     int tile = 0, cta = 0;
     for (const auto &kv : by_win) {
@@ -106,6 +113,7 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
         c.nu = c.plan->window == SE_WIN_PKB ? c.plan->nu : nu_default(c.P);
         c.tile_begin = tile;
         c.cta_begin = cta;
+        c.fast_begin = int(ftiles.size());
         const int G = 32 / c.P;
         const int per_cta = (kThreads / 32) * G;
         int J = 1;
@@ -124,14 +132,22 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
             s.sp0 = sp;
             s.n = int(off[i + 1] - off[i]);
             const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
+            // FP32 systems with edge-8 tiles and P <= 10: tile-staged gathering,
+            // one CTA per tile; the others: the flat gathering
+            const bool fast = sizeof(T) == 4 && c.P <= 10 && p->tg.T[0] == 8 && p->tg.T[1] == 8 &&
+                              p->tg.T[2] == 8 && p->tg.B[0] == 7 + c.P && p->tg.B[1] == 7 + c.P &&
+                              p->tg.B[2] == 7 + c.P;
             s.tile0 = tile;
             s.scr0 = scr;
             s.cta0 = cta;
-            s.ncta = (s.n + per_cta - 1) / per_cta;
+            s.ncta = fast ? 0 : (s.n + per_cta - 1) / per_cta;
+            s.fpos0 = fast ? int(ftiles.size()) - c.fast_begin : -1;
             s.inv_h = T(p->inv_h);
             s.self_coef = T(0);
             tile_sys.insert(tile_sys.end(), nt, i);
             cta_sys.insert(cta_sys.end(), s.ncta, i);
+            if (fast)
+                for (int t = 0; t < nt; ++t) ftiles.push_back(tile + t);
             tile += nt;
             cta += s.ncta;
             sp += s.n;
@@ -145,6 +161,7 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
         }
         c.ntiles = tile - c.tile_begin;
         c.ncta = cta - c.cta_begin;
+        c.nfast = int(ftiles.size()) - c.fast_begin;
         c.J = J <= 2 ? 2 : J <= 3 ? 3 : J <= 4 ? 4 : kMergeJ;
         if (J > kMergeJ) return fail(SE_EINVAL, "batch: gridding blocks overlap too many tiles");
         c.spread_smem = sm;
@@ -155,6 +172,7 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
     }
     m->ntiles = tile;
     m->ncta = cta;
+    m->nfast = int(ftiles.size());
     std::vector<int64_t> p0(off.begin(), off.end());
     se_status st = SE_OK;
     const int64_t N = m->ntot;
@@ -168,7 +186,8 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
         (st = m_alloc<T>(m, &m->prt.frac_q, 4 * sizeof(T) * N)) != SE_OK ||
         (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->prt.idx_anc), sizeof(int4) * N)) != SE_OK ||
         (st = m_alloc<T>(m, &m->scratch, sizeof(T) * size_t(scr))) != SE_OK ||
-        (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->part), sizeof(double) * cta)) != SE_OK ||
+        (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->part), sizeof(double) * (cta + m->nfast))) != SE_OK ||
+        (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->ftiles), sizeof(int) * m->nfast)) != SE_OK ||
         (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->done), sizeof(int) * nsys)) != SE_OK ||
         (st = m_alloc<T>(m, reinterpret_cast<void **>(&m->err), sizeof(int))) != SE_OK) {
         release(m);
@@ -178,6 +197,8 @@ se_status MOps<T>::build(MBatch *m, const std::vector<se_plan_t> &plans, const s
     if (e == cudaSuccess) e = cudaMemcpy(m->p0, p0.data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->tile_sys, tile_sys.data(), sizeof(int) * tile, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->cta_sys, cta_sys.data(), sizeof(int) * cta, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m->nfast)
+        e = cudaMemcpy(m->ftiles, ftiles.data(), sizeof(int) * m->nfast, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->done, 0, sizeof(int) * nsys);
     if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -244,13 +265,204 @@ se_status MOps<T>::gather(MBatch *m, T *phi, T *F, double *energy, cudaStream_t 
     double *part = energy ? m->part : nullptr;
     for (const MClass &c : m->classes) {
         const WindowArgs<T> wa = window_args<T>(c.plan);
-        SE_M_DISPATCH_P(c.P, c.nu, {
-            k_mgather_flat<T, PP, NN, true><<<unsigned(c.ncta), kThreads, 0, s>>>(
-                sd, m->cta_sys, c.cta_begin, fq, m->prt.idx_anc, wa, phi, F, part, energy, m->done);
-        });
-        SE_M_CHECK("batch gather");
+        if (c.ncta > 0) {
+            SE_M_DISPATCH_P(c.P, c.nu, {
+                k_mgather_flat<T, PP, NN, true><<<unsigned(c.ncta), kThreads, 0, s>>>(
+                    sd, m->cta_sys, c.cta_begin, fq, m->prt.idx_anc, wa, phi, F, part, energy, m->done);
+            });
+            SE_M_CHECK("batch gather");
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (c.nfast > 0) {
+                cudaError_t e = cudaSuccess;
+                double *fpart = part ? part + m->ncta + c.fast_begin : nullptr;
+                SE_M_DISPATCH_P(c.P, c.nu, {
+                    if constexpr (PP <= 10) {
+                        auto kern = k_mgather_tile_f32<PP, NN>;
+                        constexpr size_t sm = gather_fast_smem<PP, true>();
+                        if ((e = allow_smem(kern, sm)) == cudaSuccess)
+                            e = launch_pdl(kern, dim3(unsigned(c.nfast)), dim3(kThreads), sm, s, 1,
+                                           static_cast<const SysDesc<float> *>(m->desc), (const int *)m->tile_sys,
+                                           (const int *)(m->ftiles + c.fast_begin), (const int *)m->tile_off,
+                                           (const float4 *)fq, (const int4 *)m->prt.idx_anc, wa, phi, F, fpart,
+                                           energy, m->done);
+                    }
+                });
+                if (e != cudaSuccess) return cuda_fail(e, "batch tile gather launch");
+                SE_M_CHECK("batch tile gather");
+            }
+        }
     }
     return SE_OK;
+}
+
+// Radices of a line transform of length n (4, 2, 3, 5, 7, then any other
+// prime factor); false when n is longer than the line buffers.
+static bool line_factors(int n, FftLen &L)
+{
+    L.n = n;
+    L.nf = 0;
+    if (n < 1 || n > kLineElems) return false;
+    int r = n;
+    auto take = [&](int f) {
+        while (r % f == 0 && L.nf < kFftMaxFactors) {
+            L.r[L.nf++] = f;
+            r /= f;
+        }
+    };
+    take(4);
+    take(2);
+    for (int f = 3; f <= r && L.nf < kFftMaxFactors; f += 2) take(f);
+    return r == 1;
+}
+
+template <typename T>
+se_status MOps<T>::build_lines(MBatch *m, const std::vector<se_plan_t> &plans)
+{
+    using C = typename Cplx<T>::type;
+    if (m->lsys) cudaFree(m->lsys);
+    if (m->litems) cudaFree(m->litems);
+    if (m->ltw) cudaFree(m->ltw);
+    m->lsys = m->litems = m->ltw = nullptr;
+    m->lines_built = false;
+    const int nsys = int(plans.size());
+    std::vector<LineSys<T>> ls(nsys);
+    std::vector<LineItem> items[5];
+    std::map<int, int> tw_off;                         // length -> offset of its roots
+    std::vector<double> tw;                            // (re, im) pairs
+    auto len = [&](int n, FftLen &L) -> bool {
+        if (!line_factors(n, L)) return false;
+        auto it = tw_off.find(n);
+        if (it == tw_off.end()) {
+            it = tw_off.emplace(n, int(tw.size() / 2)).first;
+            for (int k = 0; k < n; ++k) {
+                const double a = -2.0 * M_PI * double(k) / double(n);
+                tw.push_back(std::cos(a));
+                tw.push_back(std::sin(a));
+            }
+        }
+        L.tw = it->second;
+        return true;
+    };
+    auto split = [](int total, int cap) {             // even chunks of at most cap
+        const int chunks = (total + cap - 1) / cap;
+        return (total + chunks - 1) / chunks;
+    };
+    for (int i = 0; i < nsys; ++i) {
+        const se_plan_s *p = plans[i];
+        if (p->D != 3 && p->D != 2) return fail(SE_EINVAL, "multi-system transforms serve D = 3 and 2");
+        if (p->force_method != 1) return fail(SE_EINVAL, "multi-system transforms serve force method 1");
+        LineSys<T> &d = ls[i];
+        std::memset(&d, 0, sizeof(d));
+        d.D = p->D;
+        d.n0 = p->tg.n[0];
+        d.n1 = p->tg.n[1];
+        d.n2 = p->tg.n[2];
+        d.row = d.n0 / 2 + 1;
+        d.gin = static_cast<const T *>(p->grid_in);
+        d.gout = static_cast<T *>(p->grid_out);
+        d.spec = static_cast<C *>(p->spec);
+        if constexpr (sizeof(T) == 4) {
+            d.sbJ = p->sb_spec_f;
+            d.sbU = p->sb_U_f;
+        } else {
+            d.sbJ = p->sb_spec_d;
+            d.sbU = p->sb_U_d;
+        }
+        bool ok = len(d.n0, d.lx) && len(d.n1, d.ly) && len(d.n2, d.lz);
+        if (p->D == 2) {
+            d.nI = p->nI;
+            d.nl0 = p->nIv[0];
+            d.nl1 = p->nIv[1];
+            d.tab0 = static_cast<const T *>(p->sigma_tab);
+            d.lines = p->I_lines;
+            ok = ok && len(p->s0v[2], d.l0) && (p->nI == 0 || len(p->sv[2], d.lI));
+        }
+        if (!ok) return fail(SE_EINVAL, "multi-system transforms: a transform longer than " +
+                                            std::to_string(kLineElems) + " points");
+        // line groups of every pass (each of at most kLineElems values)
+        const int rows = std::max(2, 2 * (kLineElems / d.n0));
+        const int rx = split(d.n1, std::min(d.n1 + (d.n1 & 1), rows));
+        const int ry = split(d.row, std::max(1, kLineElems / d.n1));
+        for (int z = 0; z < d.n2; ++z) {
+            for (int y0 = 0; y0 < d.n1; y0 += rx + (rx & 1)) {
+                const LineItem it{i, 0, z, y0, std::min(rx + (rx & 1), d.n1 - y0)};
+                items[kPassXF].push_back(it);
+                items[kPassXI].push_back(it);
+            }
+            for (int k0 = 0; k0 < d.row; k0 += ry) {
+                const LineItem it{i, 0, z, k0, std::min(ry, d.row - k0)};
+                items[kPassYF].push_back(it);
+                items[kPassYI].push_back(it);
+            }
+        }
+        const int rz = split(d.row, std::max(1, kLineElems / d.lz.n));
+        for (int ky = 0; ky < d.n1; ++ky)
+            for (int k0 = 0; k0 < d.row; k0 += rz) {
+                // D = 2: a group made only of lines of the set I or the zero mode is left out
+                bool any = d.D == 3;
+                for (int kx = k0; kx < std::min(d.row, k0 + rz) && !any; ++kx)
+                    any = !(kx <= d.nl0 && (ky <= d.nl1 || ky >= d.n1 - d.nl1));
+                if (any) items[kPassZ].push_back(LineItem{i, kLineJ, ky, k0, std::min(rz, d.row - k0)});
+            }
+        if (p->D == 2) {
+            if (d.nI > 0) {
+                const int ri = split(d.nI, std::max(1, kLineElems / d.lI.n));
+                for (int l0 = 0; l0 < d.nI; l0 += ri)
+                    items[kPassZ].push_back(LineItem{i, kLineI, l0, 0, std::min(ri, d.nI - l0)});
+            }
+            items[kPassZ].push_back(LineItem{i, kLineZero, 0, 0, 1});
+        }
+    }
+    std::vector<LineItem> all;
+    for (int k = 0; k < 5; ++k) {
+        m->loff[k] = int(all.size());
+        m->lcount[k] = int(items[k].size());
+        all.insert(all.end(), items[k].begin(), items[k].end());
+    }
+    std::vector<C> twc(tw.size() / 2);
+    for (size_t k = 0; k < twc.size(); ++k) {
+        twc[k].x = T(tw[2 * k]);
+        twc[k].y = T(tw[2 * k + 1]);
+    }
+    se_status st;
+    if ((st = m_alloc<T>(m, &m->lsys, sizeof(LineSys<T>) * nsys)) != SE_OK ||
+        (st = m_alloc<T>(m, &m->litems, sizeof(LineItem) * all.size())) != SE_OK ||
+        (st = m_alloc<T>(m, &m->ltw, sizeof(C) * twc.size())) != SE_OK)
+        return st;
+    cudaError_t e = cudaMemcpy(m->lsys, ls.data(), sizeof(LineSys<T>) * nsys, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->litems, all.data(), sizeof(LineItem) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->ltw, twc.data(), sizeof(C) * twc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch transform tables");
+    m->lines_built = true;
+    return SE_OK;
+}
+
+template <typename T>
+se_status MOps<T>::lines(MBatch *m, cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    if (!m->lines_built) return fail(SE_EINVAL, "multi-system transforms not built");
+    const auto *ls = static_cast<const LineSys<T> *>(m->lsys);
+    const auto *items = static_cast<const LineItem *>(m->litems);
+    const auto *tw = static_cast<const C *>(m->ltw);
+    constexpr size_t sm = mlines_smem<T>();
+    auto run = [&](auto kern, int pass) -> se_status {
+        if (m->lcount[pass] == 0) return SE_OK;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e == cudaSuccess)
+            e = launch_pdl(kern, dim3(unsigned(m->lcount[pass])), dim3(kLineThreads), sm, s, 1, ls,
+                           items + m->loff[pass], tw);
+        if (e != cudaSuccess) return cuda_fail(e, "batch transform launch");
+        SE_M_CHECK("batch transform");
+        return SE_OK;
+    };
+    se_status st;
+    if ((st = run(k_mlines<T, kPassXF>, kPassXF)) != SE_OK) return st;
+    if ((st = run(k_mlines<T, kPassYF>, kPassYF)) != SE_OK) return st;
+    if ((st = run(k_mlines<T, kPassZ>, kPassZ)) != SE_OK) return st;
+    if ((st = run(k_mlines<T, kPassYI>, kPassYI)) != SE_OK) return st;
+    return run(k_mlines<T, kPassXI>, kPassXI);
 }
 
 template struct MOps<T_INST>;

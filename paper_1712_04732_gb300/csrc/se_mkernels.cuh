@@ -27,6 +27,7 @@ struct SysDesc {
     int64_t scr0;        // first element of the system's blocks in the batch scratch
     int cta0, ncta;      // gathering CTAs of the system
     T inv_h, self_coef;
+    int fpos0;           // tile-staged gathering: position of the system's first tile in its class's list (-1: none)
 };
 
 // System of particle i: the largest s with p0[s] <= i (p0 ascending, nsys >= 1).
@@ -283,6 +284,78 @@ k_mgather_flat(const SysDesc<T> *__restrict__ sd, const int *__restrict__ cta_sy
     if (part) {
         cta_energy_partial(esum, part + c);
         finish_energy_of(part + cta0, ncta, energy + sys, done + sys, ncta);
+    }
+}
+
+// FP32 tile-staged gathering over the edge-8 tiles of many systems (the
+// systems of one support class with P <= 10): CTA k takes global tile
+// tiles[k], stages that tile's extended block of its system's output grid in
+// shared memory (cp.async, wrapping periodic sides) and gathers phi and
+// F = -q grad phi of all the tile's particles with the particle loop of
+// k_gather_tile_f32fast (Eq. complete_integral, Eq. force-method-1); the
+// energy of each system is summed over its tiles' CTAs, whose partials lie at
+// part[fpos0 .. fpos0 + tiles of the system).
+template <int P, int NU>
+__global__ void __launch_bounds__(kThreads, P <= 8 ? 4 : 3)
+k_mgather_tile_f32(const SysDesc<float> *__restrict__ sd, const int *__restrict__ tile_sys,
+                   const int *__restrict__ tiles, const int *__restrict__ tile_off, const float4 *__restrict__ fq,
+                   const int4 *__restrict__ ia, WindowArgs<float> wa, float *__restrict__ phi, float *__restrict__ F,
+                   double *__restrict__ part, double *energy, int *done)
+{
+    using G = FastGeom<P>;
+    constexpr int NW = kThreads / 32;
+    constexpr int WR = 64;
+    static_assert(3 * P <= 32, "the tile-staged gathering serves P <= 10");
+    pdl_wait();
+    const int gt = tiles[blockIdx.x];
+    const int sys = tile_sys[gt];
+    const SysDesc<float> &d = sd[sys];
+    const TileGeom tg = d.tg;
+    const int tile = gt - d.tile0;
+    const int nt = tg.nt[0] * tg.nt[1] * tg.nt[2];
+    const int beg = tile_off[gt], end = tile_off[gt + 1];
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float *blk = reinterpret_cast<float *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));   // 128-byte aligned
+    float *wrow = blk + align_up_elems<float>(G::SBLK);                        // [warp][2][WR]
+    float4 *pst = reinterpret_cast<float4 *>(wrow + NW * 2 * WR);              // [warp][32] (t_x, t_y, t_z, q)
+    int *bst = reinterpret_cast<int *>(pst + NW * 32);                         // [warp][32] block offsets
+    float4 *rst = reinterpret_cast<float4 *>(bst + NW * 32);                   // [warp][32] (phi, g_x, g_y, g_z)
+    double esum = 0.0;
+    if (end > beg) {
+        int o[3];
+        tile_origin(tg, tile, o);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 a0 = make_int4(0, 0, 0, 0);
+        if (beg + warp + lane * NW < end) {
+            r0 = fq[beg + warp + lane * NW];
+            a0 = ia[beg + warp + lane * NW];
+        }
+        stage_block<float>(tg, o, d.grid_out, d.gout, blk);
+        const int kk = lane % P;
+        LaneCoef<float, NU> cf;
+        if (wa.kind == SE_WIN_PKB) cf.load(wa, P, kk);
+        int poff[G::NE];
+#pragma unroll
+        for (int e = 0; e < G::NE; ++e) {
+            const int pp = lane + 32 * e < P * P ? lane + 32 * e : 0;
+            poff[e] = (pp / P) * G::PITCH + pp % P;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        const int axc = min(lane / P, 3);
+        if (wa.kind == SE_WIN_PKB)
+            esum = gather_rounds_f32<P, NU, true, true>(blk, wrow + warp * 2 * WR, pst + warp * 32, bst + warp * 32,
+                                                        rst + warp * 32, beg + warp, end, NW, o, fq, ia, wa.alpha, cf,
+                                                        lane, axc, kk, poff, phi, F, d.inv_h, d.self_coef, r0, a0);
+        else
+            esum = gather_rounds_f32<P, NU, true, false>(blk, wrow + warp * 2 * WR, pst + warp * 32, bst + warp * 32,
+                                                         rst + warp * 32, beg + warp, end, NW, o, fq, ia, wa.alpha, cf,
+                                                         lane, axc, kk, poff, phi, F, d.inv_h, d.self_coef, r0, a0);
+    }
+    if (part) {
+        cta_energy_partial(esum, part + blockIdx.x);
+        finish_energy_of(part + d.fpos0, nt, energy + sys, done + sys, nt);
     }
 }
 

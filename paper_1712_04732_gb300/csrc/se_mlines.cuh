@@ -1,0 +1,297 @@
+// Multi-system transforms of a batch (Alg. 4 steps 2-4 for D = 3 and D = 2,
+// with the adaptive transform of Alg. 1 / Alg. 2 for the free direction):
+// every system's forward transform, scaling (Eq. scale) and inverse transform
+// in five kernel launches for the whole batch, each launch a list of line
+// groups of every system:
+//   pass XF  rows along x: real to half spectrum (two real rows packed in one
+//            complex transform of length M_0);
+//   pass YF  lines along y (length M_1), in place in the spectrum;
+//   pass Z   lines along z: forward transform, scaling, inverse transform in
+//            shared memory.  D = 3: length M_2, Eq. (scale) with G^{3P} (the
+//            k = 0 term dropped).  D = 2: the lines of the class J at length
+//            M~, the lines of the set I zero-padded to s M~ and the zero mode
+//            to s0 M~ (Alg. 1 steps 2-4, Alg. 2 steps 1-4), each scaled with
+//            its own factors and truncated back to M~;
+//   pass YI  lines along y, inverse;
+//   pass XI  half spectrum to real rows along x (two rows per transform).
+// Transforms are unnormalised (the scaling factors carry 1 / (number of
+// points)), the same convention as the single-system path, whose layouts
+// (real grid [z][y][x], spectrum [z][ky][kx] with M_0/2 + 1 values per row)
+// the passes read and write.
+//
+// The line transform is a Stockham autosort FFT in shared memory for any
+// length whose factors are listed in FftLen (Govindaraju et al. 2008 give the
+// pass structure): the pass of radix R with Ns points already combined maps
+// element j + u n/R, u < R, to position (j - j mod Ns) R + j mod Ns + t Ns,
+// t < R, and each output is one sum of R products with the twiddle
+// exp(-2 pi i u c / n), c = (j mod Ns) n / (Ns R) + t n / R, read from a table
+// of the n-th roots of unity (built in FP64 on the host).
+#pragma once
+
+#include "se_internal.h"
+
+namespace se {
+
+constexpr int kLineThreads = 256;
+constexpr int kLineElems = 2048;     // complex values per shared-memory buffer
+constexpr int kFftMaxFactors = 16;
+
+enum LinePass { kPassXF = 0, kPassYF = 1, kPassZ = 2, kPassYI = 3, kPassXI = 4 };
+enum LineKind { kLineJ = 0, kLineI = 1, kLineZero = 2 };
+
+struct FftLen {
+    int n;                    // transform length (<= kLineElems)
+    int nf;                   // radix passes
+    int tw;                   // offset of exp(-2 pi i m / n), m < n, in the twiddle table
+    int r[kFftMaxFactors];    // radices, product n
+};
+
+template <typename T>
+struct LineSys {
+    int D;
+    int n0, n1, n2, row;      // real grid n0 x n1 x n2 (x fastest); spectrum n2 x n1 x row, row = n0/2 + 1
+    int nI, nl0, nl1;         // D = 2: the set I (kx <= nl0, |ky| <= nl1, zero mode excluded), nI lines
+    FftLen lx, ly, lz, lI, l0;
+    const T *gin;
+    T *gout;
+    typename Cplx<T>::type *spec;
+    ScaleBox<T> sbJ, sbU;     // Eq. (scale) on the class J lines and on the set I
+    const T *tab0;            // zero mode: s0 M~ factors
+    const int2 *lines;        // (kx, ky index) of each line of the set I
+};
+
+// One CTA's work: system `sys` and, per pass,
+//   XF, XI: plane z = a, rows b .. b + n - 1;
+//   YF, YI: plane z = a, lines kx = b .. b + n - 1;
+//   Z: kind J: ky = a, lines kx = b .. b + n - 1; kind I: lines a .. a + n - 1
+//      of the set I; kind zero: the line (0, 0).
+struct LineItem {
+    int sys, kind, a, b, n;
+};
+
+// a / d for 0 <= a < 2^21 through the float reciprocal of d: the quotient's
+// error, below a / (d 2^22), stays under the distance 0.5 / d of (a + 0.5) / d
+// from the nearest integer (no integer division in the inner loops).
+struct FDiv {
+    int d;
+    float inv;
+    __device__ __forceinline__ explicit FDiv(int dd) : d(dd), inv(1.0f / float(dd)) {}
+    __device__ __forceinline__ int q(int a) const { return int((float(a) + 0.5f) * inv); }
+};
+
+template <typename C>
+__device__ __forceinline__ C cmul_acc(C acc, C x, C w)
+{
+    acc.x = fma(x.x, w.x, fma(-x.y, w.y, acc.x));
+    acc.y = fma(x.x, w.y, fma(x.y, w.x, acc.y));
+    return acc;
+}
+
+// nl transforms of length L.n held contiguously in a (nl L.n values); the
+// result ends in a or b, returned.  tw: the n-th roots in shared memory.
+template <typename T>
+__device__ typename Cplx<T>::type *line_fft(typename Cplx<T>::type *a, typename Cplx<T>::type *b, int nl,
+                                            const FftLen &L, const typename Cplx<T>::type *tw, bool inv)
+{
+    using C = typename Cplx<T>::type;
+    const int n = L.n, tot = nl * n;
+    const FDiv dn(n);
+    int Ns = 1;
+    for (int f = 0; f < L.nf; ++f) {
+        const int R = L.r[f], nR = n / R, step = n / (Ns * R);
+        const FDiv dR(nR), dN(Ns);
+        for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+            const int line = dn.q(idx), o = idx - line * n;
+            const int t = dR.q(o), j = o - t * nR;
+            const int jm = j - dN.q(j) * Ns;
+            const int c = jm * step + t * nR;
+            const C *src = a + line * n + j;
+            C acc;
+            acc.x = T(0);
+            acc.y = T(0);
+            int m = 0;
+            for (int u = 0; u < R; ++u) {
+                C w = tw[m];
+                if (inv) w.y = -w.y;
+                acc = cmul_acc(acc, src[u * nR], w);
+                m += c;
+                if (m >= n) m -= n;
+            }
+            b[line * n + (j - jm) * R + jm + t * Ns] = acc;
+        }
+        __syncthreads();
+        C *s = a;
+        a = b;
+        b = s;
+        Ns *= R;
+    }
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_twiddles(typename Cplx<T>::type *dst, const typename Cplx<T>::type *twall,
+                                               const FftLen &L)
+{
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) dst[i] = twall[L.tw + i];
+}
+
+// Eq. (scale) factor of a spectral box element (the expression of k_scale_box,
+// without its exclusion of the set I: those lines are scaled as their own kind).
+template <typename T>
+__device__ __forceinline__ T box_factor(const ScaleBox<T> &sb, int i0, int i1, int i2)
+{
+    const T den = sb.k0[i0] + sb.k1[i1] + sb.k2[i2];
+    return den == T(0) ? T(0) : sb.norm * sb.f0[i0] * sb.f1[i1] * sb.f2[i2] / den;
+}
+
+template <typename T, int PASS>
+__global__ void __launch_bounds__(kLineThreads)
+k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
+         const typename Cplx<T>::type *__restrict__ twall)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *A = reinterpret_cast<C *>(smraw);
+    C *B = A + kLineElems;
+    C *tw = B + kLineElems;
+    pdl_wait();
+    const LineItem it = items[blockIdx.x];
+    const LineSys<T> &s = sys[it.sys];
+    const int64_t zs = int64_t(s.n1) * s.row;           // spectrum plane stride
+    C zero;
+    zero.x = T(0);
+    zero.y = T(0);
+    if constexpr (PASS == kPassXF || PASS == kPassXI) {
+        const FftLen &L = s.lx;
+        const int n = L.n, nl = (it.n + 1) / 2;          // rows b + 2k (real part) and b + 2k + 1 (imaginary part)
+        const FDiv dn(n), drow(s.row);
+        const int64_t pz = int64_t(it.a) * s.n1 * s.n0;
+        stage_twiddles<T>(tw, twall, L);
+        if constexpr (PASS == kPassXF) {
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int k = dn.q(idx), x = idx - k * n;
+                const int ya = it.b + 2 * k;
+                C v;
+                v.x = s.gin[pz + int64_t(ya) * s.n0 + x];
+                v.y = 2 * k + 1 < it.n ? s.gin[pz + int64_t(ya + 1) * s.n0 + x] : T(0);
+                A[idx] = v;
+            }
+            __syncthreads();
+            const C *R = line_fft<T>(A, B, nl, L, tw, false);
+            // X_a = (Z_k + conj Z_{n-k}) / 2, X_b = (Z_k - conj Z_{n-k}) / 2i
+            for (int idx = threadIdx.x; idx < nl * s.row; idx += blockDim.x) {
+                const int k = drow.q(idx), kx = idx - k * s.row;
+                const C z = R[k * n + kx], zm = R[k * n + (kx == 0 ? 0 : n - kx)];
+                const int ya = it.b + 2 * k;
+                C xa, xb;
+                xa.x = T(0.5) * (z.x + zm.x);
+                xa.y = T(0.5) * (z.y - zm.y);
+                xb.x = T(0.5) * (z.y + zm.y);
+                xb.y = T(0.5) * (zm.x - z.x);
+                const int64_t o = int64_t(it.a) * zs + int64_t(ya) * s.row + kx;
+                s.spec[o] = xa;
+                if (2 * k + 1 < it.n) s.spec[o + s.row] = xb;
+            }
+        } else {
+            // Z = X_a + i X_b over the full length from the half spectra (Hermitian:
+            // the imaginary parts at kx = 0 and n/2 are dropped, as a C2R transform does)
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int k = dn.q(idx), kx = idx - k * n;
+                const int ya = it.b + 2 * k;
+                const bool mirror = kx >= s.row;
+                const int kk = mirror ? n - kx : kx;
+                const bool real_only = kk == 0 || 2 * kk == n;
+                const int64_t o = int64_t(it.a) * zs + int64_t(ya) * s.row + kk;
+                C xa = s.spec[o], xb = 2 * k + 1 < it.n ? s.spec[o + s.row] : zero;
+                if (real_only) {
+                    xa.y = T(0);
+                    xb.y = T(0);
+                } else if (mirror) {
+                    xa.y = -xa.y;
+                    xb.y = -xb.y;
+                }
+                C v;
+                v.x = xa.x - xb.y;
+                v.y = xa.y + xb.x;
+                A[idx] = v;
+            }
+            __syncthreads();
+            const C *R = line_fft<T>(A, B, nl, L, tw, true);
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int k = dn.q(idx), x = idx - k * n;
+                const int ya = it.b + 2 * k;
+                const C v = R[idx];
+                s.gout[pz + int64_t(ya) * s.n0 + x] = v.x;
+                if (2 * k + 1 < it.n) s.gout[pz + int64_t(ya + 1) * s.n0 + x] = v.y;
+            }
+        }
+    } else if constexpr (PASS == kPassYF || PASS == kPassYI) {
+        const FftLen &L = s.ly;
+        const int n = L.n, nl = it.n;
+        const FDiv dl(nl);
+        C *base = s.spec + int64_t(it.a) * zs + it.b;
+        stage_twiddles<T>(tw, twall, L);
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int y = dl.q(idx), k = idx - y * nl;     // consecutive threads: consecutive kx
+            A[k * n + y] = base[int64_t(y) * s.row + k];
+        }
+        __syncthreads();
+        const C *R = line_fft<T>(A, B, nl, L, tw, PASS == kPassYI);
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int y = dl.q(idx), k = idx - y * nl;
+            base[int64_t(y) * s.row + k] = R[k * n + y];
+        }
+    } else {
+        const FftLen &L = it.kind == kLineJ ? s.lz : it.kind == kLineI ? s.lI : s.l0;
+        const int n = L.n, nl = it.n, nz = s.n2;         // M~ (D = 2) or M_2 (D = 3) values per line
+        const FDiv dn(n), dl(nl);
+        stage_twiddles<T>(tw, twall, L);
+        // spectrum offset of line k of the item
+        auto line_at = [&](int k) -> int64_t {
+            if (it.kind == kLineJ) return int64_t(it.a) * s.row + it.b + k;
+            if (it.kind == kLineI) {
+                const int2 l = s.lines[it.a + k];
+                return int64_t(l.y) * s.row + l.x;
+            }
+            return 0;
+        };
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int z = dl.q(idx), k = idx - z * nl;
+            A[k * n + z] = z < nz ? s.spec[int64_t(z) * zs + line_at(k)] : zero;
+        }
+        __syncthreads();
+        C *R = line_fft<T>(A, B, nl, L, tw, false);
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int k = dn.q(idx), z = idx - k * n;
+            T f;
+            if (it.kind == kLineJ) f = box_factor<T>(s.sbJ, it.b + k, it.a, z);
+            else if (it.kind == kLineI) f = box_factor<T>(s.sbU, z, it.a + k, 0);
+            else f = s.tab0[z];
+            C v = R[idx];
+            v.x *= f;
+            v.y *= f;
+            R[idx] = v;
+        }
+        __syncthreads();
+        C *other = R == A ? B : A;
+        const C *Y = line_fft<T>(R, other, nl, L, tw, true);
+        for (int idx = threadIdx.x; idx < nl * nz; idx += blockDim.x) {
+            const int z = dl.q(idx), k = idx - z * nl;
+            if (it.kind == kLineJ && s.D == 2) {
+                // the lines of the set I and the zero mode are written by their own items
+                const int kx = it.b + k, ky = it.a;
+                if (kx <= s.nl0 && (ky <= s.nl1 || ky >= s.n1 - s.nl1)) continue;
+            }
+            s.spec[int64_t(z) * zs + line_at(k)] = Y[k * n + z];
+        }
+    }
+}
+
+// Dynamic shared memory of k_mlines.
+template <typename T>
+constexpr size_t mlines_smem()
+{
+    return size_t(3) * kLineElems * 2 * sizeof(T);
+}
+
+}  // namespace se

@@ -195,6 +195,98 @@ def test_fused_form_on_the_batched_workload():
     bb.close()
 
 
+def _systems_3p2p(n_sys, seed, n_min=300, n_max=6000):
+    sysl = wl.batch_systems(n_sys, seed=seed, n_min=n_min, n_max=n_max)
+    specs = [(len(q), D, 1.0, 8.0 * (len(q) / 1e4) ** (1.0 / 3.0)) for x, q, D in sysl]
+    return sysl, specs, np.concatenate([s[0] for s in sysl]), np.concatenate([s[1] for s in sysl])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_lines_form_matches_per_system_calls(dtype):
+    """The single-pipeline form (the transforms of all systems as line transforms
+    in five launches, the adaptive transform of the 2P systems included) against
+    one se_force per system on the same plans (cuFFT transforms) and against the
+    discrete oracle of each system's parameters.  The two transforms round
+    differently, so the forms agree to rounding: 1e-12 in FP64, 2e-6 in FP32."""
+    import paper_1712_04732_gb300 as se
+    sysl, specs, x, q = _systems_3p2p(12, seed=7)
+    b = se.Batch(specs, eps_rel=1e-5, dtype=dtype, autotune=False, form="lines")
+    xt = torch.tensor(x, dtype=dtype, device="cuda")
+    qt = torch.tensor(q, dtype=dtype, device="cuda")
+    F, phi, En = b.force(xt, qt)
+    F2, phi2, En2 = b.force(xt, qt)                 # graph replay
+    Fe, phie, Ene = b.force(xt, qt, each=True)
+    torch.cuda.synchronize()
+    assert b.form()[0] == "lines"
+    assert torch.equal(phi, phi2) and torch.equal(F, F2)
+    rt = 1e-12 if dtype == torch.float64 else 2e-6
+    off = 0
+    for i, (xs, qs, D) in enumerate(sysl):
+        n = len(qs)
+        assert _rel(phi[off:off + n].cpu().numpy(), phie[off:off + n].cpu().numpy()) < rt
+        assert _rel(F[off:off + n].cpu().numpy(), Fe[off:off + n].cpu().numpy()) < rt
+        off += n
+    np.testing.assert_allclose(En.cpu().numpy(), Ene.cpu().numpy(), rtol=10 * rt)
+    from oracle import se_discrete
+    off = 0
+    for i, (xs, qs, D) in enumerate(sysl):
+        n = len(qs)
+        info = b.system_info(i)
+        if D == 2:
+            assert info["s0_mt"] > info["Mt"]            # the zero mode is transformed padded
+        ref = se_discrete.SEOracle(D, 1.0, specs[i][3], info["M"], info["P"], "pkb", s_mt=info["s_mt"],
+                                   nl=info["n_l"])
+        pb, gb = ref.potential(xs, qs, grad=True)
+        tol = 1e-10 if dtype == torch.float64 else 2e-5
+        assert _rel(phi[off:off + n].double().cpu().numpy(), pb) < tol
+        assert _rel(F[off:off + n].double().cpu().numpy(), -qs[:, None] * gb) < 10 * tol
+        off += n
+    b.close()
+
+
+def test_lines_form_on_the_batched_workload():
+    """The 64-system workload of the benchmark in the single-pipeline form: at
+    most 50 kernel launches per call (no cuFFT), results equal to the
+    multi-system form with cuFFT transforms to FP32 rounding."""
+    import paper_1712_04732_gb300 as se
+    sysl, specs, x, q = _systems_3p2p(64, seed=1, n_min=1e3, n_max=1e5)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+    bl = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False, form="lines")
+    bf = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False, form="fused")
+    F, phi, En = bl.force(xt, qt)
+    Ff, phif, Enf = bf.force(xt, qt)
+    torch.cuda.synchronize()
+    form, kernels = bl.form()
+    assert form == "lines" and kernels <= 50, (form, kernels)
+    assert _rel(phi.cpu().numpy(), phif.cpu().numpy()) < 2e-6
+    assert _rel(F.cpu().numpy(), Ff.cpu().numpy()) < 2e-6
+    np.testing.assert_allclose(En.cpu().numpy(), Enf.cpu().numpy(), rtol=2e-5)
+    bl.close()
+    bf.close()
+
+
+def test_lines_form_needs_3p_or_2p_systems():
+    """A batch with a 1P or free-space system cannot take the single-pipeline
+    form: the call reports SE_EINVAL; the autotuner then picks another form."""
+    import paper_1712_04732_gb300 as se
+    from paper_1712_04732_gb300 import _native as nat
+    sysl, specs, x, q = _mixed_systems(4, seed=9)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+    b = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=False, form="lines")
+    with pytest.raises(nat.SEError) as ei:
+        b.force(xt, qt)
+    assert ei.value.name == "SE_EINVAL" and "D = 3 and 2" in str(ei.value)
+    b.close()
+    bt = se.Batch(specs, eps_rel=1e-5, dtype=torch.float32, autotune=True)
+    F, phi, En = bt.force(xt, qt)
+    torch.cuda.synchronize()
+    assert bt.form()[0] in ("fused", "branches")
+    assert torch.isfinite(F).all()
+    bt.close()
+
+
 def test_batch_form_flags_exclude_each_other():
     import paper_1712_04732_gb300 as se
     from paper_1712_04732_gb300 import _native as nat
@@ -204,8 +296,9 @@ def test_batch_form_flags_exclude_each_other():
     D = (ctypes.c_int * 1)(3)
     L = (ctypes.c_double * 1)(1.0)
     xi = (ctypes.c_double * 1)(8.0)
-    code = lib.se_batch_create(ctypes.byref(h), 1, n, D, L, xi, None, 1e-5, nat.SE_WIN_PKB, nat.SE_F32,
-                               nat.SE_BATCH_FUSED | nat.SE_BATCH_BRANCHES)
-    assert nat.STATUS[code] == "SE_EINVAL"
-    assert not h.value
+    for flags in (nat.SE_BATCH_FUSED | nat.SE_BATCH_BRANCHES, nat.SE_BATCH_LINES | nat.SE_BATCH_FUSED,
+                  nat.SE_BATCH_LINES | nat.SE_BATCH_BRANCHES):
+        code = lib.se_batch_create(ctypes.byref(h), 1, n, D, L, xi, None, 1e-5, nat.SE_WIN_PKB, nat.SE_F32, flags)
+        assert nat.STATUS[code] == "SE_EINVAL"
+        assert not h.value
     del se
