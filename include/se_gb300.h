@@ -265,9 +265,10 @@ se_status se_real_space(se_plan_t plan, int64_t N, const void *x, const void *q,
  * up to an FFT-friendly size; the AFT of D = 1, 2 systems gets eps_rel / 4.
  * With autotuning, the first call then measures, on its own inputs, the
  * relative rms errors of phi and F of (M, P) candidates around that rule
- * against an FP64 reference of each system and keeps the fastest candidate
+ * against an FP64 reference of each system and keeps, among the candidates
  * whose errors are both within eps_rel / 2 (se_batch_get_accuracy reports
- * them).  The window is w for all systems.  Every call replays one CUDA graph (captured on
+ * them), the one of least work: N P^3 window updates (doubled for P > 10)
+ * plus 64 per grid point.  The window is w for all systems.  Every call replays one CUDA graph (captured on
  * first use and whenever the pointers change) in one of three forms:
  *  - single pipeline (SE_BATCH_LINES; every system D = 3 or 2, force method 1):
  *    binning, gridding, block merge and gathering of all systems as one kernel

@@ -217,6 +217,20 @@ struct TuneBuf {
     }
 };
 
+// Work of a system's call at support P on plan p, in units of one window-point
+// update of one particle: n P^3 for the gridding and the gathering (doubled for
+// P > 10, where both leave the tile kernels of P <= 10), plus 64 per grid point
+// for the transforms and the scaling (the ratio of the two per-unit times of
+// the single-system pipeline on a grid of 2.9e6 points and 1.2e6 particles at
+// P = 8).  A model rather than a timed call: one system's call is dominated by
+// its launch latencies, which the batched forms do not pay per system.
+double work_model(int64_t n, int P, const se_plan_s *p)
+{
+    const double upd = double(n) * P * P * P * (P > 10 ? 2.0 : 1.0);
+    const double pts = double(p->grid_in_elems) + double(p->U_elems) + double(p->Z_elems);
+    return upd + 64.0 * pts;
+}
+
 // Stage 0 of the autotuner: the grid size M and support P of every system,
 // chosen on the call's own inputs.  The Sec. 6 rule gives (M0, P0); the
 // candidates are P in {P0 - 2, P0, P0 + 2, P0 + 4} and M in {M0, 1.25 M0,
@@ -225,8 +239,7 @@ struct TuneBuf {
 // P0 + 6), grid 1.5 M0 rounded up, AFT tolerance 1e-12, whose own error is far
 // below eps_rel); among the candidates whose relative rms errors of phi and F
 // are both within eps_rel / 2 (a margin for inputs that change between calls)
-// the fastest, by the median of three timed calls, is kept; if none is, the
-// most accurate.
+// the one of least work (work_model) is kept; if none is, the most accurate.
 se_status tune_params(se_batch_s *b, const void *x, const void *q)
 {
     const size_t e = elem(b);
@@ -238,13 +251,6 @@ se_status tune_params(se_batch_s *b, const void *x, const void *q)
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return se::fail(SE_ENOMEM, "parameter tuner scratch");
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    ce = cudaEventCreate(&e0);
-    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-    if (ce != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        return se::cuda_fail(ce, "tuner events");
     }
     std::vector<char> raw(e * 4 * nmax);
     std::vector<double> h64(4 * nmax), rphi(nmax), rF(3 * nmax), cphi(nmax), cF(3 * nmax);
@@ -297,7 +303,7 @@ se_status tune_params(se_batch_s *b, const void *x, const void *q)
                 for (const Cand &c : cands) dup = dup || (c.M == Mc && c.P == Pc);
                 if (!dup) cands.push_back({Mc, Pc});
             }
-        float best_t = 1e30f;
+        double best_cost = 1e300;
         double best_err = 1e30;
         int pick = -1, pick_acc = -1;
         std::vector<double> errs(cands.size() * 2, -1.0);
@@ -312,17 +318,12 @@ se_status tune_params(se_batch_s *b, const void *x, const void *q)
                 continue;
             }
             char *dF = static_cast<char *>(buf.out), *dphi = dF + 3 * e * n;
-            float t[3] = {0.f, 0.f, 0.f};
-            for (int r = 0; r < 4 && cs == SE_OK; ++r) {
-                ce = cudaEventRecord(e0, b->stream);
-                cs = se_force(p, n, xi_dev, qi_dev, dF, dphi, nullptr, 0);
-                if (ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                if (ce == cudaSuccess && r > 0) ce = cudaEventElapsedTime(&t[r - 1], e0, e1);
-                if (ce != cudaSuccess) cs = se::cuda_fail(ce, "timing a candidate");
-            }
+            cs = se_force(p, n, xi_dev, qi_dev, dF, dphi, nullptr, 0);
+            if (cs == SE_OK && (ce = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+                cs = se::cuda_fail(ce, "candidate run");
             if (cs == SE_OK && (ce = cudaMemcpy(raw.data(), dF, 4 * e * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
                 cs = se::cuda_fail(ce, "candidate results");
+            const double cost = work_model(n, cands[c].P, p);
             se_plan_destroy(p);
             if (cs != SE_OK) {
                 st = cs;
@@ -337,9 +338,8 @@ se_status tune_params(se_batch_s *b, const void *x, const void *q)
             const double ep = rel_rms(cphi, rphi, size_t(n)), ef = rel_rms(cF, rF, size_t(3 * n));
             errs[2 * c] = ep;
             errs[2 * c + 1] = ef;
-            std::sort(t, t + 3);
-            if (ep <= 0.5 * b->eps_rel && ef <= 0.5 * b->eps_rel && t[1] < best_t) {
-                best_t = t[1];
+            if (ep <= 0.5 * b->eps_rel && ef <= 0.5 * b->eps_rel && cost < best_cost) {
+                best_cost = cost;
                 pick = int(c);
             }
             if (std::max(ep, ef) < best_err) {
@@ -364,8 +364,6 @@ se_status tune_params(se_batch_s *b, const void *x, const void *q)
         b->err_phi[i] = errs[2 * pick];
         b->err_F[i] = errs[2 * pick + 1];
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return st;
 }
 
