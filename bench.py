@@ -501,7 +501,8 @@ def run_ours(a):
             x_np, q_np, spec = wl.make(WORKLOAD, seed=rank + 1)
             f = Form(se, spec, x_np, q_np, torch.float32, dev, fft_sizes=1)
             ms, _ = time_graph_steps(f.g, flush, a.steps, a.warmup, dev, world)
-            res = {"wire_1p": {"ms_per_step": ms, "value": spec["N"] / (ms * 1e-3)}}
+            stage_ms, _ = f.stage_profile(flush, max(3, min(a.steps, 20)), dev)
+            res = {"wire_1p": {"ms_per_step": ms, "value": spec["N"] / (ms * 1e-3), "stage_ms": stage_ms}}
             f.close()
         if rank == 0:
             print(json.dumps(res), flush=True)
