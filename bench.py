@@ -43,6 +43,10 @@ L2_FLUSH_BYTES = 256 << 20
 # (profiles/wire_1p_tile_kernels.md); the gridding stage is two launches (light
 # tiles 39.00 MB, heavy tiles 4.81 MB).  Set to None when a kernel changes.
 NCU_TRAFFIC = {"spread": 43.818e6, "gather": 61.208e6}
+# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum of the same capture: shared-memory
+# wavefronts per stage (gridding: light 33.686e6 + heavy 4.746e6 tiles; gathering
+# 53.781e6), the unit both tile kernels are bound by
+NCU_SMEM_WAVEFRONTS = {"spread": 38.432e6, "gather": 53.781e6}
 # targets of the oracle's sample on the headline workload (about 20 s of the
 # host's cores through the xi route of oracle A)
 CPU_TARGETS = 128
@@ -357,6 +361,15 @@ def rooflines(stage_ms, N, P, nu, peaks, traffic):
                              + (" (two launches: light and heavy tiles)" if k == "spread" else ""),
              "per_launch": f"{flop:.4e} flop ({cnt[k]} FMA/particle x {N})",
              "peak_source": "measured: se_measure_peak FP32 FMA chains on this GPU (of measured)"}
+        wf = NCU_SMEM_WAVEFRONTS.get(k)
+        if wf:
+            # one wavefront per clock per SM: the measured integer-atomic ceiling
+            # (32 distinct-bank updates = one wavefront) divided by 32
+            pk = peaks["smem_atomic_i32"]["value"] * 1e12 / 32.0
+            e["smem_pipe"] = {"achieved": wf / sec, "peak": pk, "unit": "wavefronts/s", "frac": wf / sec / pk,
+                              "wavefronts_per_stage": wf,
+                              "what": "shared-memory wavefronts (ncu, same kernels) over the stage time, against "
+                                      "one wavefront per clock per SM (measured atomic ceiling / 32)"}
         if k == "spread":
             upd = cnt["spread_updates"] * N / sec / 1e12
             e["atomic_updates"] = {"achieved": upd, "peak": peaks["smem_atomic_i32"]["value"], "unit": "Tupdates/s",
