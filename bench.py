@@ -62,7 +62,7 @@ def args_parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-form", choices=["auto", "lines", "fused", "branches"], default="auto",
                     help="execution form of the batched systems (auto: the autotuner's choice)")
-    ap.add_argument("--only", choices=["batch", "slab_2p", "wire_1p"], default=None,
+    ap.add_argument("--only", choices=["batch", "slab_2p", "wire_1p", "free_0p"], default=None,
                     help="time only the batched form or one workload's FP32 step (profiling aid; "
                          "prints its own JSON line)")
     return ap.parse_args()
@@ -510,6 +510,13 @@ def run_ours(a):
             res = {"batch_form": run_batch(se, wl, dev, flush, a.steps, a.batch_form)}
         elif a.only == "slab_2p":
             res = {"slab_2p": run_slab(se, wl, dev, flush, a.steps, a.warmup, world)}
+        elif a.only == "free_0p":
+            x_np, q_np, spec = wl.make("free_0p", seed=rank + 1)
+            f = Form(se, spec, x_np, q_np, torch.float32, dev)
+            ms, _ = time_graph_steps(f.g, flush, a.steps, a.warmup, dev, world)
+            stage_ms, _ = f.stage_profile(flush, max(3, min(a.steps, 20)), dev)
+            res = {"free_0p": {"ms_per_step": ms, "value": spec["N"] / (ms * 1e-3), "stage_ms": stage_ms}}
+            f.close()
         else:
             x_np, q_np, spec = wl.make(WORKLOAD, seed=rank + 1)
             f = Form(se, spec, x_np, q_np, torch.float32, dev, fft_sizes=1)
