@@ -344,10 +344,6 @@ se_status MOps<T>::build_lines(MBatch *m, const std::vector<se_plan_t> &plans)
         L.tw = it->second;
         return true;
     };
-    auto split = [](int total, int cap) {             // even chunks of at most cap
-        const int chunks = (total + cap - 1) / cap;
-        return (total + chunks - 1) / chunks;
-    };
     for (int i = 0; i < nsys; ++i) {
         const se_plan_s *p = plans[i];
         if (p->D != 3 && p->D != 2) return fail(SE_EINVAL, "multi-system transforms serve D = 3 and 2");
@@ -380,36 +376,41 @@ se_status MOps<T>::build_lines(MBatch *m, const std::vector<se_plan_t> &plans)
         }
         if (!ok) return fail(SE_EINVAL, "multi-system transforms: a transform longer than " +
                                             std::to_string(kLineElems) + " points");
-        // line groups of every pass (each of at most kLineElems values)
-        const int rows = std::max(2, 2 * (kLineElems / d.n0));
-        const int rx = split(d.n1, std::min(d.n1 + (d.n1 & 1), rows));
-        const int ry = split(d.row, std::max(1, kLineElems / d.n1));
-        for (int z = 0; z < d.n2; ++z) {
-            for (int y0 = 0; y0 < d.n1; y0 += rx + (rx & 1)) {
-                const LineItem it{i, 0, z, y0, std::min(rx + (rx & 1), d.n1 - y0)};
-                items[kPassXF].push_back(it);
-                items[kPassXI].push_back(it);
-            }
-            for (int k0 = 0; k0 < d.row; k0 += ry) {
-                const LineItem it{i, 0, z, k0, std::min(ry, d.row - k0)};
-                items[kPassYF].push_back(it);
-                items[kPassYI].push_back(it);
-            }
+        if (int64_t(d.n1) * d.n2 * d.n0 >= (int64_t(1) << 31))
+            return fail(SE_EINVAL, "multi-system transforms: a grid of 2^31 or more points");
+        // line groups of every pass (each of at most kLineElems values and
+        // kMaxLines lines), running across the planes of the system
+        const int64_t nrows = int64_t(d.n1) * d.n2;
+        const int rcap = std::min(2 * kMaxLines, 2 * std::max(1, kLineElems / d.n0));
+        for (int64_t r0 = 0; r0 < nrows; r0 += rcap) {
+            const LineItem it{i, 0, int(r0), 0, int(std::min<int64_t>(rcap, nrows - r0))};
+            items[kPassXF].push_back(it);
+            items[kPassXI].push_back(it);
         }
-        const int rz = split(d.row, std::max(1, kLineElems / d.lz.n));
-        for (int ky = 0; ky < d.n1; ++ky)
-            for (int k0 = 0; k0 < d.row; k0 += rz) {
-                // D = 2: a group made only of lines of the set I or the zero mode is left out
-                bool any = d.D == 3;
-                for (int kx = k0; kx < std::min(d.row, k0 + rz) && !any; ++kx)
-                    any = !(kx <= d.nl0 && (ky <= d.nl1 || ky >= d.n1 - d.nl1));
-                if (any) items[kPassZ].push_back(LineItem{i, kLineJ, ky, k0, std::min(rz, d.row - k0)});
+        const int64_t ylines = int64_t(d.n2) * d.row;
+        const int ycap = std::min(kMaxLines, std::max(1, kLineElems / d.n1));
+        for (int64_t l0 = 0; l0 < ylines; l0 += ycap) {
+            const LineItem it{i, 0, int(l0), 0, int(std::min<int64_t>(ycap, ylines - l0))};
+            items[kPassYF].push_back(it);
+            items[kPassYI].push_back(it);
+        }
+        const int zlines = d.n1 * d.row;
+        const int zcap = std::min(kMaxLines, std::max(1, kLineElems / d.lz.n));
+        for (int l0 = 0; l0 < zlines; l0 += zcap) {
+            const int cnt = std::min(zcap, zlines - l0);
+            // D = 2: a group made only of lines of the set I or the zero mode is left out
+            bool any = d.D == 3;
+            for (int l = l0; l < l0 + cnt && !any; ++l) {
+                const int ky = l / d.row, kx = l - ky * d.row;
+                any = !(kx <= d.nl0 && (ky <= d.nl1 || ky >= d.n1 - d.nl1));
             }
+            if (any) items[kPassZ].push_back(LineItem{i, kLineJ, l0, 0, cnt});
+        }
         if (p->D == 2) {
             if (d.nI > 0) {
-                const int ri = split(d.nI, std::max(1, kLineElems / d.lI.n));
-                for (int l0 = 0; l0 < d.nI; l0 += ri)
-                    items[kPassZ].push_back(LineItem{i, kLineI, l0, 0, std::min(ri, d.nI - l0)});
+                const int icap = std::min(kMaxLines, std::max(1, kLineElems / d.lI.n));
+                for (int l0 = 0; l0 < d.nI; l0 += icap)
+                    items[kPassZ].push_back(LineItem{i, kLineI, l0, 0, std::min(icap, d.nI - l0)});
             }
             items[kPassZ].push_back(LineItem{i, kLineZero, 0, 0, 1});
         }

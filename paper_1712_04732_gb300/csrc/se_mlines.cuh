@@ -34,6 +34,7 @@ namespace se {
 
 constexpr int kLineThreads = 256;
 constexpr int kLineElems = 2048;     // complex values per shared-memory buffer
+constexpr int kMaxLines = 1024;      // lines (row pairs) per CTA
 constexpr int kFftMaxFactors = 16;
 
 enum LinePass { kPassXF = 0, kPassYF = 1, kPassZ = 2, kPassYI = 3, kPassXI = 4 };
@@ -60,11 +61,12 @@ struct LineSys {
     const int2 *lines;        // (kx, ky index) of each line of the set I
 };
 
-// One CTA's work: system `sys` and, per pass,
-//   XF, XI: plane z = a, rows b .. b + n - 1;
-//   YF, YI: plane z = a, lines kx = b .. b + n - 1;
-//   Z: kind J: ky = a, lines kx = b .. b + n - 1; kind I: lines a .. a + n - 1
-//      of the set I; kind zero: the line (0, 0).
+// One CTA's work: system `sys` and, per pass (b unused),
+//   XF, XI: rows r = z n1 + y of the real grid, a .. a + n - 1;
+//   YF, YI: lines l = z row + kx of the spectrum along y, a .. a + n - 1;
+//   Z: kind J: lines l = ky row + kx along z, a .. a + n - 1; kind I: lines
+//      a .. a + n - 1 of the set I; kind zero: the line (0, 0).
+// Groups run across plane boundaries, so small systems take few CTAs.
 struct LineItem {
     int sys, kind, a, b, n;
 };
@@ -154,6 +156,9 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
     C *A = reinterpret_cast<C *>(smraw);
     C *B = A + kLineElems;
     C *tw = B + kLineElems;
+    int64_t *lbase = reinterpret_cast<int64_t *>(tw + kLineElems);   // [kMaxLines] spectrum offset of each line
+    int *lkx = reinterpret_cast<int *>(lbase + kMaxLines);          // [kMaxLines] (kx, ky) of each z line
+    int *lky = lkx + kMaxLines;
     pdl_wait();
     const LineItem it = items[blockIdx.x];
     const LineSys<T> &s = sys[it.sys];
@@ -162,18 +167,18 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
     zero.x = T(0);
     zero.y = T(0);
     if constexpr (PASS == kPassXF || PASS == kPassXI) {
+        // rows r = z n1 + y of the whole grid, a .. a + n - 1, in pairs (a + 2k, a + 2k + 1)
         const FftLen &L = s.lx;
-        const int n = L.n, nl = (it.n + 1) / 2;          // rows b + 2k (real part) and b + 2k + 1 (imaginary part)
+        const int n = L.n, nl = (it.n + 1) / 2;
         const FDiv dn(n), drow(s.row);
-        const int64_t pz = int64_t(it.a) * s.n1 * s.n0;
         stage_twiddles<T>(tw, twall, L);
         if constexpr (PASS == kPassXF) {
             for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
                 const int k = dn.q(idx), x = idx - k * n;
-                const int ya = it.b + 2 * k;
+                const int64_t ra = int64_t(it.a) + 2 * k;
                 C v;
-                v.x = s.gin[pz + int64_t(ya) * s.n0 + x];
-                v.y = 2 * k + 1 < it.n ? s.gin[pz + int64_t(ya + 1) * s.n0 + x] : T(0);
+                v.x = s.gin[ra * s.n0 + x];
+                v.y = 2 * k + 1 < it.n ? s.gin[(ra + 1) * s.n0 + x] : T(0);
                 A[idx] = v;
             }
             __syncthreads();
@@ -182,13 +187,12 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
             for (int idx = threadIdx.x; idx < nl * s.row; idx += blockDim.x) {
                 const int k = drow.q(idx), kx = idx - k * s.row;
                 const C z = R[k * n + kx], zm = R[k * n + (kx == 0 ? 0 : n - kx)];
-                const int ya = it.b + 2 * k;
                 C xa, xb;
                 xa.x = T(0.5) * (z.x + zm.x);
                 xa.y = T(0.5) * (z.y - zm.y);
                 xb.x = T(0.5) * (z.y + zm.y);
                 xb.y = T(0.5) * (zm.x - z.x);
-                const int64_t o = int64_t(it.a) * zs + int64_t(ya) * s.row + kx;
+                const int64_t o = (int64_t(it.a) + 2 * k) * s.row + kx;
                 s.spec[o] = xa;
                 if (2 * k + 1 < it.n) s.spec[o + s.row] = xb;
             }
@@ -197,11 +201,10 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
             // the imaginary parts at kx = 0 and n/2 are dropped, as a C2R transform does)
             for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
                 const int k = dn.q(idx), kx = idx - k * n;
-                const int ya = it.b + 2 * k;
                 const bool mirror = kx >= s.row;
                 const int kk = mirror ? n - kx : kx;
                 const bool real_only = kk == 0 || 2 * kk == n;
-                const int64_t o = int64_t(it.a) * zs + int64_t(ya) * s.row + kk;
+                const int64_t o = (int64_t(it.a) + 2 * k) * s.row + kk;
                 C xa = s.spec[o], xb = 2 * k + 1 < it.n ? s.spec[o + s.row] : zero;
                 if (real_only) {
                     xa.y = T(0);
@@ -219,52 +222,66 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
             const C *R = line_fft<T>(A, B, nl, L, tw, true);
             for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
                 const int k = dn.q(idx), x = idx - k * n;
-                const int ya = it.b + 2 * k;
+                const int64_t ra = int64_t(it.a) + 2 * k;
                 const C v = R[idx];
-                s.gout[pz + int64_t(ya) * s.n0 + x] = v.x;
-                if (2 * k + 1 < it.n) s.gout[pz + int64_t(ya + 1) * s.n0 + x] = v.y;
+                s.gout[ra * s.n0 + x] = v.x;
+                if (2 * k + 1 < it.n) s.gout[(ra + 1) * s.n0 + x] = v.y;
             }
         }
     } else if constexpr (PASS == kPassYF || PASS == kPassYI) {
+        // lines l = z row + kx, a .. a + n - 1, along y (element stride row)
         const FftLen &L = s.ly;
         const int n = L.n, nl = it.n;
         const FDiv dl(nl);
-        C *base = s.spec + int64_t(it.a) * zs + it.b;
+        for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+            const int l = it.a + k, z = l / s.row;
+            lbase[k] = int64_t(z) * zs + (l - z * s.row);
+        }
         stage_twiddles<T>(tw, twall, L);
+        __syncthreads();
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-            const int y = dl.q(idx), k = idx - y * nl;     // consecutive threads: consecutive kx
-            A[k * n + y] = base[int64_t(y) * s.row + k];
+            const int y = dl.q(idx), k = idx - y * nl;     // consecutive threads: consecutive lines
+            A[k * n + y] = s.spec[lbase[k] + int64_t(y) * s.row];
         }
         __syncthreads();
         const C *R = line_fft<T>(A, B, nl, L, tw, PASS == kPassYI);
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int y = dl.q(idx), k = idx - y * nl;
-            base[int64_t(y) * s.row + k] = R[k * n + y];
+            s.spec[lbase[k] + int64_t(y) * s.row] = R[k * n + y];
         }
     } else {
+        // lines along z: kind J the lines l = ky row + kx, a .. a + n - 1; kind I
+        // the lines a .. a + n - 1 of the set I; kind zero the line (0, 0)
         const FftLen &L = it.kind == kLineJ ? s.lz : it.kind == kLineI ? s.lI : s.l0;
         const int n = L.n, nl = it.n, nz = s.n2;         // M~ (D = 2) or M_2 (D = 3) values per line
         const FDiv dn(n), dl(nl);
-        stage_twiddles<T>(tw, twall, L);
-        // spectrum offset of line k of the item
-        auto line_at = [&](int k) -> int64_t {
-            if (it.kind == kLineJ) return int64_t(it.a) * s.row + it.b + k;
-            if (it.kind == kLineI) {
+        for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+            int kx = 0, ky = 0;
+            if (it.kind == kLineJ) {
+                const int l = it.a + k;
+                ky = l / s.row;
+                kx = l - ky * s.row;
+            } else if (it.kind == kLineI) {
                 const int2 l = s.lines[it.a + k];
-                return int64_t(l.y) * s.row + l.x;
+                kx = l.x;
+                ky = l.y;
             }
-            return 0;
-        };
+            lkx[k] = kx;
+            lky[k] = ky;
+            lbase[k] = int64_t(ky) * s.row + kx;
+        }
+        stage_twiddles<T>(tw, twall, L);
+        __syncthreads();
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int z = dl.q(idx), k = idx - z * nl;
-            A[k * n + z] = z < nz ? s.spec[int64_t(z) * zs + line_at(k)] : zero;
+            A[k * n + z] = z < nz ? s.spec[int64_t(z) * zs + lbase[k]] : zero;
         }
         __syncthreads();
         C *R = line_fft<T>(A, B, nl, L, tw, false);
         for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
             const int k = dn.q(idx), z = idx - k * n;
             T f;
-            if (it.kind == kLineJ) f = box_factor<T>(s.sbJ, it.b + k, it.a, z);
+            if (it.kind == kLineJ) f = box_factor<T>(s.sbJ, lkx[k], lky[k], z);
             else if (it.kind == kLineI) f = box_factor<T>(s.sbU, z, it.a + k, 0);
             else f = s.tab0[z];
             C v = R[idx];
@@ -279,19 +296,20 @@ k_mlines(const LineSys<T> *__restrict__ sys, const LineItem *__restrict__ items,
             const int z = dl.q(idx), k = idx - z * nl;
             if (it.kind == kLineJ && s.D == 2) {
                 // the lines of the set I and the zero mode are written by their own items
-                const int kx = it.b + k, ky = it.a;
+                const int kx = lkx[k], ky = lky[k];
                 if (kx <= s.nl0 && (ky <= s.nl1 || ky >= s.n1 - s.nl1)) continue;
             }
-            s.spec[int64_t(z) * zs + line_at(k)] = Y[k * n + z];
+            s.spec[int64_t(z) * zs + lbase[k]] = Y[k * n + z];
         }
     }
 }
 
-// Dynamic shared memory of k_mlines.
+// Dynamic shared memory of k_mlines: two line buffers, the roots of unity and
+// the per-line tables.
 template <typename T>
 constexpr size_t mlines_smem()
 {
-    return size_t(3) * kLineElems * 2 * sizeof(T);
+    return size_t(3) * kLineElems * 2 * sizeof(T) + size_t(kMaxLines) * (sizeof(int64_t) + 2 * sizeof(int));
 }
 
 }  // namespace se
