@@ -89,8 +89,129 @@ __device__ __forceinline__ C cmul_acc(C acc, C x, C w)
     return acc;
 }
 
+// i s z for s = +1 or -1 (a quarter turn).
+template <typename C, typename T>
+__device__ __forceinline__ C qturn(C z, T s)
+{
+    C r;
+    r.x = -s * z.y;
+    r.y = s * z.x;
+    return r;
+}
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b)
+{
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b)
+{
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+
+template <typename C, typename T>
+__device__ __forceinline__ C cscale(C a, T f)
+{
+    a.x *= f;
+    a.y *= f;
+    return a;
+}
+
+// In-register R-point DFT y_t = sum_u v_u exp(s 2 pi i u t / R), s = -1 forward,
+// +1 inverse, written out from the definition with the symmetric sums of
+// u and R - u (R = 2, 3, 4, 5).
+template <int R, typename C, typename T>
+__device__ __forceinline__ void small_dft(C *v, T s)
+{
+    if constexpr (R == 2) {
+        const C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const C e0 = cadd(v[0], v[2]), e1 = csub(v[0], v[2]);
+        const C o0 = cadd(v[1], v[3]), o1 = qturn(csub(v[1], v[3]), s);
+        v[0] = cadd(e0, o0);
+        v[2] = csub(e0, o0);
+        v[1] = cadd(e1, o1);
+        v[3] = csub(e1, o1);
+    } else if constexpr (R == 3) {
+        const T h = T(0.86602540378443864676);                     // sin(2 pi / 3)
+        const C t1 = cadd(v[1], v[2]);
+        const C t2 = csub(v[0], cscale(t1, T(0.5)));
+        const C t3 = qturn(cscale(csub(v[1], v[2]), h), s);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    } else {
+        static_assert(R == 5, "radix 2, 3, 4 or 5");
+        const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);   // cos(2 pi/5), cos(4 pi/5)
+        const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);    // sin(2 pi/5), sin(4 pi/5)
+        const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        const C t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        C a1, a2, b1, b2;
+        a1.x = v[0].x + c1 * t1.x + c2 * t2.x;
+        a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
+        a2.x = v[0].x + c2 * t1.x + c1 * t2.x;
+        a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
+        b1.x = s1 * t3.x + s2 * t4.x;
+        b1.y = s1 * t3.y + s2 * t4.y;
+        b2.x = s2 * t3.x - s1 * t4.x;
+        b2.y = s2 * t3.y - s1 * t4.y;
+        v[0] = cadd(v[0], cadd(t1, t2));
+        const C ib1 = qturn(b1, s), ib2 = qturn(b2, s);
+        v[1] = cadd(a1, ib1);
+        v[4] = csub(a1, ib1);
+        v[2] = cadd(a2, ib2);
+        v[3] = csub(a2, ib2);
+    }
+}
+
+// One Stockham pass of radix R (2, 3, 4, 5) over nl lines: butterfly j of a
+// line takes the inputs j + u n/R, multiplies input u by exp(-+2 pi i u (j mod
+// Ns) n / (Ns R) / n), runs the R-point DFT and writes output t to
+// (j - j mod Ns) R + j mod Ns + t Ns.
+template <int R, typename T>
+__device__ __forceinline__ void stockham_pass_r(const typename Cplx<T>::type *a, typename Cplx<T>::type *b, int nl,
+                                                int n, int Ns, const typename Cplx<T>::type *tw, bool inv)
+{
+    using C = typename Cplx<T>::type;
+    const int nR = n / R, step = n / (Ns * R);
+    const FDiv dR(nR), dN(Ns);
+    const T s = inv ? T(1) : T(-1);
+    for (int idx = threadIdx.x; idx < nl * nR; idx += blockDim.x) {
+        const int line = dR.q(idx), j = idx - line * nR;
+        const int jm = j - dN.q(j) * Ns;
+        const C *src = a + line * n + j;
+        C v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = src[u * nR];
+#pragma unroll
+        for (int u = 1; u < R; ++u) {
+            C w = tw[u * jm * step];                      // u jm step < n
+            if (inv) w.y = -w.y;
+            C z;
+            z.x = v[u].x * w.x - v[u].y * w.y;
+            z.y = v[u].x * w.y + v[u].y * w.x;
+            v[u] = z;
+        }
+        small_dft<R, C, T>(v, s);
+        C *dst = b + line * n + (j - jm) * R + jm;
+#pragma unroll
+        for (int t = 0; t < R; ++t) dst[t * Ns] = v[t];
+    }
+}
+
 // nl transforms of length L.n held contiguously in a (nl L.n values); the
 // result ends in a or b, returned.  tw: the n-th roots in shared memory.
+// Radices 2-5 take the in-register butterflies; any other radix (7, other
+// primes) forms each output as one sum of R products with the twiddle
+// exp(-+2 pi i u c / n), c = (j mod Ns) n / (Ns R) + t n / R.
 template <typename T>
 __device__ typename Cplx<T>::type *line_fft(typename Cplx<T>::type *a, typename Cplx<T>::type *b, int nl,
                                             const FftLen &L, const typename Cplx<T>::type *tw, bool inv)
@@ -100,31 +221,38 @@ __device__ typename Cplx<T>::type *line_fft(typename Cplx<T>::type *a, typename 
     const FDiv dn(n);
     int Ns = 1;
     for (int f = 0; f < L.nf; ++f) {
-        const int R = L.r[f], nR = n / R, step = n / (Ns * R);
-        const FDiv dR(nR), dN(Ns);
-        for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-            const int line = dn.q(idx), o = idx - line * n;
-            const int t = dR.q(o), j = o - t * nR;
-            const int jm = j - dN.q(j) * Ns;
-            const int c = jm * step + t * nR;
-            const C *src = a + line * n + j;
-            C acc;
-            acc.x = T(0);
-            acc.y = T(0);
-            int m = 0;
-            for (int u = 0; u < R; ++u) {
-                C w = tw[m];
-                if (inv) w.y = -w.y;
-                acc = cmul_acc(acc, src[u * nR], w);
-                m += c;
-                if (m >= n) m -= n;
+        const int R = L.r[f];
+        if (R == 4) stockham_pass_r<4, T>(a, b, nl, n, Ns, tw, inv);
+        else if (R == 2) stockham_pass_r<2, T>(a, b, nl, n, Ns, tw, inv);
+        else if (R == 3) stockham_pass_r<3, T>(a, b, nl, n, Ns, tw, inv);
+        else if (R == 5) stockham_pass_r<5, T>(a, b, nl, n, Ns, tw, inv);
+        else {
+            const int nR = n / R, step = n / (Ns * R);
+            const FDiv dR(nR), dN(Ns);
+            for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+                const int line = dn.q(idx), o = idx - line * n;
+                const int t = dR.q(o), j = o - t * nR;
+                const int jm = j - dN.q(j) * Ns;
+                const int c = jm * step + t * nR;
+                const C *src = a + line * n + j;
+                C acc;
+                acc.x = T(0);
+                acc.y = T(0);
+                int m = 0;
+                for (int u = 0; u < R; ++u) {
+                    C w = tw[m];
+                    if (inv) w.y = -w.y;
+                    acc = cmul_acc(acc, src[u * nR], w);
+                    m += c;
+                    if (m >= n) m -= n;
+                }
+                b[line * n + (j - jm) * R + jm + t * Ns] = acc;
             }
-            b[line * n + (j - jm) * R + jm + t * Ns] = acc;
         }
         __syncthreads();
-        C *s = a;
+        C *sw = a;
         a = b;
-        b = s;
+        b = sw;
         Ns *= R;
     }
     return a;
