@@ -107,7 +107,12 @@ typedef struct {
                            spectra and grids).  se_potential and se_vjp are unaffected. */
     int    fft_mode;    /* [<= 0] D = 0 transform: the z-direction FFT, scaling and inverse
                            FFT fused into one kernel per column when 2 M~ is a power of two
-                           from 16 to 1024 (cuFFT otherwise); 1 cuFFT for every stage */
+                           from 16 to 1024 (cuFFT otherwise); 1 cuFFT for every stage;
+                           2 (D = 1 plans; method 1) the free-direction transforms of every
+                           class, their padding (Alg. 1, Alg. 2) and the scaling as three
+                           line-transform launches (padded rows and columns that are zero or
+                           cut are never transformed) between cuFFT's x transforms, when
+                           every free-direction length is at most 2048; otherwise as 0 */
     int    fft_sizes;   /* [<= 0] free-direction transform lengths: the smallest the rules of
                            Sec. 3.3 and Sec. 6 allow; 1 each of M~_i, s0 M~_i and s M~_i rounded
                            up to the next even length whose prime factors are 2, 3, 5 and 7
@@ -124,7 +129,8 @@ typedef struct {
     int64_t capacity;     /* particles the workspace holds now */
     int64_t device_bytes; /* device memory held by the plan */
     int column_fft;       /* 1: the D = 0 z-direction FFT, scaling and inverse FFT run fused
-                             in one kernel (se_opts.fft_mode) */
+                             in one kernel; 2: the D = 1 free-direction transforms and scaling
+                             run as line transforms (se_opts.fft_mode) */
     /* per axis (non-cubic boxes; the scalar fields above are the cube's values:
        M of x, M~ / s0 M~ / s M~ of the first free axis, n_l of x) */
     int M_v[3];           /* grid intervals L_i / h */

@@ -40,7 +40,8 @@ class Plan:
     Keyword overrides (Sec. 6 defaults otherwise): lam, s0, s_mt, n_l, nu,
     shape, aft_eps, tile, spread_mode, gather_mode, split (kernel variants),
     force_method (1: gradient of the window, 2: i k in the scaling; Sec. 7.2),
-    fft_mode (1: cuFFT for every transform stage), fft_sizes (1: free-direction
+    fft_mode (1: cuFFT for every transform stage; 2: D = 1 free-direction transforms
+    as line transforms), fft_sizes (1: free-direction
     transform lengths rounded up to 2-3-5-7-smooth sizes).
     """
 

@@ -319,10 +319,11 @@ se_status se_plan_create(se_plan_t *out, const double box[3], int D, double xi, 
     if (o.tile > 0 && o.tile != 4 && o.tile != 8 && o.tile != 16) { delete p; return fail(SE_EINVAL, "tile must be 4, 8 or 16"); }
     if (o.force_method > 2) { delete p; return fail(SE_EINVAL, "force_method must be 1 or 2 (Sec. 7.2)"); }
     p->force_method = o.force_method == 2 ? 2 : 1;
-    if (o.fft_mode > 1) { delete p; return fail(SE_EINVAL, "fft_mode must be 0 or 1"); }
+    if (o.fft_mode > 2) { delete p; return fail(SE_EINVAL, "fft_mode must be 0, 1 or 2"); }
     if (o.fft_sizes > 1) { delete p; return fail(SE_EINVAL, "fft_sizes must be 0 or 1"); }
     const bool smooth = o.fft_sizes == 1;
     p->zcol_allowed = o.fft_mode != 1;
+    p->lines_requested = o.fft_mode == 2;
     // Sec. 6: shape parameters and PKB degree
     p->shape = o.shape > 0 ? o.shape : (w == SE_WIN_GAUSSIAN ? M_PI / 2.0 * P * 0.91 : 2.5 * P);
     p->nu = o.nu > 0 ? o.nu : std::min(P / 2 + 2, 9);
@@ -438,7 +439,7 @@ se_status se_plan_get_info(se_plan_t p, se_plan_info_t *info)
     info->xi = p->xi; info->shape = p->shape;
     info->capacity = p->cap;
     info->device_bytes = p->device_bytes;
-    info->column_fft = p->zcol ? 1 : 0;
+    info->column_fft = p->zcol ? 1 : p->lines1p ? 2 : 0;
     for (int a = 0; a < 3; ++a) {
         info->M_v[a] = p->Mv[a];
         info->Mt_v[a] = p->Mtv[a];

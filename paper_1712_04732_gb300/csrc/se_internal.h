@@ -235,6 +235,15 @@ struct se_plan_s {
     // D = 0 column stage (used when 2 M~ is a power of two in [16, 1024])
     bool zcol = false;
     bool zcol_allowed = true;            // se_opts.fft_mode != 1
+    // D = 1: the free-direction transforms and scaling as line transforms
+    // (se_mlines.cuh, k_lines1p): descriptor, items of the three passes
+    // (items [l1p_off[k], l1p_off[k] + l1p_count[k]) of pass k), roots of unity
+    bool lines_requested = false;        // se_opts.fft_mode == 2
+    bool lines1p = false;
+    void *l1p_desc = nullptr;
+    void *l1p_items = nullptr;
+    void *l1p_tw = nullptr;
+    int l1p_count[3] = {0, 0, 0}, l1p_off[3] = {0, 0, 0};
     int zcol_cols = 16;                  // columns per CTA
     void *ztw = nullptr;                 // twiddle table
     se::ZCol<float> zc_f{};
@@ -299,6 +308,9 @@ struct Ops {
     // as spread() for the call's N particles, with the per-tile gridding blocks in
     // caller-provided device memory
     static se_status spread_with_scratch(se_plan_s *p, int64_t N, void *dst, void *scratch);
+    // D = 1 plans: build the line-transform descriptor and items (sets lines1p;
+    // leaves it false when a padded length exceeds the line buffers)
+    static se_status build_lines1p(se_plan_s *p);
 };
 
 // Multi-system pipeline of a batch (se_mbatch_impl.cuh): binning, gridding,

@@ -9,6 +9,7 @@
 #include <unordered_map>
 
 #include "se_launch.cuh"
+#include "se_mlines.cuh"
 
 namespace se {
 
@@ -520,11 +521,138 @@ static se_status inverse(se_plan_s *p, typename Cplx<T>::type *spec, typename Cp
 }
 
 template <typename T>
+se_status Ops<T>::build_lines1p(se_plan_s *p)
+{
+    using C = typename Cplx<T>::type;
+    p->lines1p = false;
+    if (p->D != 1) return SE_OK;
+    Line1P<T> d;
+    std::memset(&d, 0, sizeof(d));
+    d.row = p->Mv[0] / 2 + 1;
+    d.Mt1 = p->Mtv[1];
+    d.Mt2 = p->Mtv[2];
+    d.nI = p->nI;
+    d.sy = p->sv[1];
+    d.sz = p->sv[2];
+    d.s0y = p->s0v[1];
+    d.s0z = p->s0v[2];
+    d.spec = static_cast<C *>(p->spec);
+    d.U = static_cast<C *>(p->U);
+    d.Z = static_cast<C *>(p->Z);
+    d.sbJ = sb_spec<T>(p);
+    d.sbU = sb_U<T>(p);
+    d.tab0 = static_cast<const T *>(p->sigma_tab);
+    // lengths and their roots of unity (FP64 on the host, stored in T)
+    std::vector<int> lens;
+    std::vector<double> roots;
+    auto len = [&](int n, FftLen &L) -> bool {
+        if (!line_factors(n, L)) return false;
+        int off = 0;
+        size_t k = 0;
+        for (; k < lens.size() && lens[k] != n; ++k) off += lens[k];
+        if (k == lens.size()) {
+            lens.push_back(n);
+            for (int m = 0; m < n; ++m) {
+                const double a = -2.0 * M_PI * double(m) / double(n);
+                roots.push_back(std::cos(a));
+                roots.push_back(std::sin(a));
+            }
+        }
+        L.tw = off;
+        return true;
+    };
+    if (!(len(d.Mt1, d.yJ) && len(d.Mt2, d.zJ) && len(d.s0y, d.y0) && len(d.s0z, d.z0) &&
+          (d.nI == 0 || (len(d.sy, d.yI) && len(d.sz, d.zI)))))
+        return SE_OK;                                      // a length beyond the line buffers: cuFFT path
+    std::vector<LineItem> items[3];                        // YF, Z, YI (YI = YF)
+    const int nJ = d.row - 1 - d.nI;
+    const int cyJ = std::max(1, std::min(kMaxLines, kLineElems / d.Mt1));
+    const int cyI = std::max(1, std::min(kMaxLines, kLineElems / std::max(1, d.sy)));
+    for (int z = 0; z < d.Mt2; ++z) {
+        for (int k0 = 0; k0 < nJ; k0 += cyJ)
+            items[0].push_back(LineItem{0, kLineJ, z, d.nI + 1 + k0, std::min(cyJ, nJ - k0)});
+        for (int k0 = 0; k0 < d.nI; k0 += cyI)
+            items[0].push_back(LineItem{0, kLineI, z, 1 + k0, std::min(cyI, d.nI - k0)});
+        items[0].push_back(LineItem{0, kLineZero, z, 0, 1});
+    }
+    const int czJ = std::max(1, std::min(kMaxLines, kLineElems / d.Mt2));
+    for (int y = 0; y < d.Mt1; ++y)
+        for (int k0 = 0; k0 < nJ; k0 += czJ)
+            items[1].push_back(LineItem{0, kLineJ, y, d.nI + 1 + k0, std::min(czJ, nJ - k0)});
+    if (d.nI > 0) {
+        const int czI = std::max(1, std::min(kMaxLines, kLineElems / d.sz));
+        for (int pl = 0; pl < d.nI; ++pl)
+            for (int y0 = 0; y0 < d.sy; y0 += czI)
+                items[1].push_back(LineItem{0, kLineI, pl, y0, std::min(czI, d.sy - y0)});
+    }
+    const int cz0 = std::max(1, std::min(kMaxLines, kLineElems / d.s0z));
+    for (int y0 = 0; y0 < d.s0y; y0 += cz0) items[1].push_back(LineItem{0, kLineZero, 0, y0, std::min(cz0, d.s0y - y0)});
+    std::vector<LineItem> all;
+    for (int k = 0; k < 3; ++k) {
+        const std::vector<LineItem> &v = items[k == 2 ? 0 : k];
+        p->l1p_off[k] = int(all.size());
+        p->l1p_count[k] = int(v.size());
+        all.insert(all.end(), v.begin(), v.end());
+    }
+    std::vector<C> rc(roots.size() / 2);
+    for (size_t k = 0; k < rc.size(); ++k) {
+        rc[k].x = T(roots[2 * k]);
+        rc[k].y = T(roots[2 * k + 1]);
+    }
+    se_status st;
+    if ((st = dev_alloc(p, &p->l1p_desc, sizeof(d))) != SE_OK) return st;
+    if ((st = dev_alloc(p, &p->l1p_items, sizeof(LineItem) * all.size())) != SE_OK) return st;
+    if ((st = dev_alloc(p, &p->l1p_tw, sizeof(C) * rc.size())) != SE_OK) return st;
+    cudaError_t e = cudaMemcpy(p->l1p_desc, &d, sizeof(d), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->l1p_items, all.data(), sizeof(LineItem) * all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->l1p_tw, rc.data(), sizeof(C) * rc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "line-transform tables");
+    p->lines1p = true;
+    return SE_OK;
+}
+
+// D = 1 with line transforms: R2C along x (cuFFT), the three line passes of
+// k_lines1p (free-direction transforms of every class with their padding,
+// scaling, inverse transforms and truncation), C2R along x.
+template <typename T>
+static se_status convolve_lines1p(se_plan_s *p, void *gin, void *gout)
+{
+    using C = typename Cplx<T>::type;
+    C *spec = reinterpret_cast<C *>(p->spec);
+    cufftResult r;
+    if ((r = fft_r2c(p->fwd, reinterpret_cast<T *>(gin), spec)) != CUFFT_SUCCESS) return cufft_fail(r, "forward x");
+    const auto *d = static_cast<const Line1P<T> *>(p->l1p_desc);
+    const auto *items = static_cast<const LineItem *>(p->l1p_items);
+    const auto *tw = static_cast<const C *>(p->l1p_tw);
+    constexpr size_t sm = mlines_smem<T>();
+    auto run = [&](auto kern, int k) -> se_status {
+        if (p->l1p_count[k] == 0) return SE_OK;
+        cudaError_t e = allow_smem(kern, sm);
+        if (e == cudaSuccess)
+            e = launch_pdl(kern, dim3(unsigned(p->l1p_count[k])), dim3(kLineThreads), sm, p->stream, 1, d,
+                           items + p->l1p_off[k], tw);
+        if (e != cudaSuccess) return cuda_fail(e, "line transform launch");
+        ++p->launches;
+        return SE_OK;
+    };
+    se_status st;
+    if ((st = run(k_lines1p<T, kPassYF>, 0)) != SE_OK) return st;
+    prof_mark(p, 4);
+    if ((st = run(k_lines1p<T, kPassZ>, 1)) != SE_OK) return st;
+    prof_mark(p, 5);
+    if ((st = run(k_lines1p<T, kPassYI>, 2)) != SE_OK) return st;
+    if ((r = fft_c2r(p->inv, spec, reinterpret_cast<T *>(gout))) != CUFFT_SUCCESS) return cufft_fail(r, "inverse x");
+    prof_mark(p, 6);
+    return SE_OK;
+}
+
+template <typename T>
 se_status Ops<T>::convolve(se_plan_s *p, void *gin, void *gout)
 {
     using C = typename Cplx<T>::type;
     se_status st;
     if (p->zcol) return convolve_zcol<T>(p, gin, gout, false);
+    if (p->lines1p) return convolve_lines1p<T>(p, gin, gout);
     if ((st = forward<T>(p, gin)) != SE_OK) return st;
     prof_mark(p, 4);
     if ((st = scale<T>(p, false)) != SE_OK) return st;

@@ -296,26 +296,6 @@ se_status MOps<T>::gather(MBatch *m, T *phi, T *F, double *energy, cudaStream_t 
     return SE_OK;
 }
 
-// Radices of a line transform of length n (4, 2, 3, 5, 7, then any other
-// prime factor); false when n is longer than the line buffers.
-static bool line_factors(int n, FftLen &L)
-{
-    L.n = n;
-    L.nf = 0;
-    if (n < 1 || n > kLineElems) return false;
-    int r = n;
-    auto take = [&](int f) {
-        while (r % f == 0 && L.nf < kFftMaxFactors) {
-            L.r[L.nf++] = f;
-            r /= f;
-        }
-    };
-    take(4);
-    take(2);
-    for (int f = 3; f <= r && L.nf < kFftMaxFactors; f += 2) take(f);
-    return r == 1;
-}
-
 template <typename T>
 se_status MOps<T>::build_lines(MBatch *m, const std::vector<se_plan_t> &plans)
 {

@@ -71,6 +71,26 @@ struct LineItem {
     int sys, kind, a, b, n;
 };
 
+// Radices of a line transform of length n (4, 2, 3, 5, 7, then any other
+// prime factor); false when n is longer than the line buffers.
+static inline bool line_factors(int n, FftLen &L)
+{
+    L.n = n;
+    L.nf = 0;
+    if (n < 1 || n > kLineElems) return false;
+    int r = n;
+    auto take = [&](int f) {
+        while (r % f == 0 && L.nf < kFftMaxFactors) {
+            L.r[L.nf++] = f;
+            r /= f;
+        }
+    };
+    take(4);
+    take(2);
+    for (int f = 3; f <= r && L.nf < kFftMaxFactors; f += 2) take(f);
+    return r == 1;
+}
+
 // a / d for 0 <= a < 2^21 through the float reciprocal of d: the quotient's
 // error, below a / (d 2^22), stays under the distance 0.5 / d of (a + 0.5) / d
 // from the nearest integer (no integer division in the inner loops).
@@ -438,6 +458,130 @@ template <typename T>
 constexpr size_t mlines_smem()
 {
     return size_t(3) * kLineElems * 2 * sizeof(T) + size_t(kMaxLines) * (sizeof(int64_t) + 2 * sizeof(int));
+}
+
+// ---------------------------------------------------------------------------
+// The same line transforms for one plan with D = 1 (x periodic, y and z free),
+// replacing the adaptive transform's padded 2D transforms (Alg. 1 steps 2-4,
+// Alg. 2 steps 1-4) and the scaling between the R2C and C2R transforms along
+// x.  The spectrum is [z][y][kx] (Mt2 x Mt1 x row); its kx planes fall in
+// three classes: kx = 0 (the zero mode, y and z padded to s0 M~), kx = 1 .. nI
+// (the set I, padded to s M~) and the rest (the class J, unpadded).  Three
+// launches:
+//   pass YF  lines along y of every plane and z < M~_2 (the rows z >= M~_2 of a
+//            padded plane are zero, so their transforms are skipped): J in
+//            place, I and the zero mode zero-padded into the planes U (s M~_1
+//            x s M~_2, y fastest) and Z (s0 M~_1 x s0 M~_2);
+//   pass Z   lines along z of every plane and y: zero-padded forward
+//            transform, Eq. (scale) with each class's factors, inverse
+//            transform, truncated to z < M~_2, in place;
+//   pass YI  lines along y, inverse, truncated to y < M~_1, into the spectrum.
+// The result equals the padded 2D transforms of the cuFFT path (the
+// transform of a zero-padded line is the same sum; rows and columns that are
+// cut afterwards are not formed).
+template <typename T>
+struct Line1P {
+    int row, Mt1, Mt2, nI;
+    int sy, sz, s0y, s0z;          // padded lengths of the set I and of the zero mode
+    FftLen yJ, zJ, yI, zI, y0, z0;
+    typename Cplx<T>::type *spec, *U, *Z;
+    ScaleBox<T> sbJ, sbU;          // sbJ over (kx, y, z); sbU over (y, z, plane of the set I)
+    const T *tab0;                 // zero mode: factor of (y, z) at z s0y + y
+};
+
+// Items of the three passes (sys unused):
+//   YF, YI: plane row z = a; kind J / I: lines kx = b .. b + n - 1; kind zero: kx = 0;
+//   Z: kind J: y = a, lines kx = b .. b + n - 1; kind I: plane kx = a + 1, lines
+//      y = b .. b + n - 1; kind zero: lines y = b .. b + n - 1.
+template <typename T, int PASS>
+__global__ void __launch_bounds__(kLineThreads)
+k_lines1p(const Line1P<T> *__restrict__ desc, const LineItem *__restrict__ items,
+          const typename Cplx<T>::type *__restrict__ twall)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *A = reinterpret_cast<C *>(smraw);
+    C *B = A + kLineElems;
+    C *tw = B + kLineElems;
+    pdl_wait();
+    const LineItem it = items[blockIdx.x];
+    const Line1P<T> &d = *desc;
+    const int nl = it.n;
+    const FDiv dl(nl);
+    C zero;
+    zero.x = T(0);
+    zero.y = T(0);
+    if constexpr (PASS == kPassYF || PASS == kPassYI) {
+        const FftLen &L = it.kind == kLineJ ? d.yJ : it.kind == kLineI ? d.yI : d.y0;
+        const int n = L.n, z = it.a;
+        const FDiv dn(n);
+        stage_twiddles<T>(tw, twall, L);
+        // spectrum element (z, y, kx) of line k
+        auto sp = [&](int k, int y) -> C * { return d.spec + (int64_t(z) * d.Mt1 + y) * d.row + it.b + k; };
+        // padded row of line k in U or Z
+        auto pad = [&](int k) -> C * {
+            return it.kind == kLineI ? d.U + (int64_t(it.b + k - 1) * d.sz + z) * d.sy : d.Z + int64_t(z) * d.s0y;
+        };
+        if (PASS == kPassYF || it.kind == kLineJ) {
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int y = dl.q(idx), k = idx - y * nl;           // consecutive threads: consecutive kx
+                A[k * n + y] = y < d.Mt1 ? *sp(k, y) : zero;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int k = dn.q(idx), y = idx - k * n;            // padded rows are contiguous in y
+                A[idx] = pad(k)[y];
+            }
+        }
+        __syncthreads();
+        const C *R = line_fft<T>(A, B, nl, L, tw, PASS == kPassYI);
+        if (PASS == kPassYI || it.kind == kLineJ) {
+            for (int idx = threadIdx.x; idx < nl * d.Mt1; idx += blockDim.x) {
+                const int y = dl.q(idx), k = idx - y * nl;
+                *sp(k, y) = R[k * n + y];
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+                const int k = dn.q(idx), y = idx - k * n;
+                pad(k)[y] = R[idx];
+            }
+        }
+    } else {
+        const FftLen &L = it.kind == kLineJ ? d.zJ : it.kind == kLineI ? d.zI : d.z0;
+        const int n = L.n;
+        const FDiv dn(n);
+        stage_twiddles<T>(tw, twall, L);
+        // element z of line k: J in the spectrum (stride Mt1 row), I / zero in U / Z
+        auto el = [&](int k, int z) -> C * {
+            if (it.kind == kLineJ) return d.spec + (int64_t(z) * d.Mt1 + it.a) * d.row + it.b + k;
+            if (it.kind == kLineI) return d.U + (int64_t(it.a) * d.sz + z) * d.sy + it.b + k;
+            return d.Z + int64_t(z) * d.s0y + it.b + k;
+        };
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int z = dl.q(idx), k = idx - z * nl;               // consecutive threads: consecutive lines
+            A[k * n + z] = z < d.Mt2 ? *el(k, z) : zero;
+        }
+        __syncthreads();
+        C *R = line_fft<T>(A, B, nl, L, tw, false);
+        for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+            const int k = dn.q(idx), z = idx - k * n;
+            T f;
+            if (it.kind == kLineJ) f = box_factor<T>(d.sbJ, it.b + k, it.a, z);
+            else if (it.kind == kLineI) f = box_factor<T>(d.sbU, it.b + k, z, it.a);
+            else f = d.tab0[int64_t(z) * d.s0y + it.b + k];
+            C v = R[idx];
+            v.x *= f;
+            v.y *= f;
+            R[idx] = v;
+        }
+        __syncthreads();
+        C *other = R == A ? B : A;
+        const C *Y = line_fft<T>(R, other, nl, L, tw, true);
+        for (int idx = threadIdx.x; idx < nl * d.Mt2; idx += blockDim.x) {
+            const int z = dl.q(idx), k = idx - z * nl;
+            *el(k, z) = Y[k * n + z];
+        }
+    }
 }
 
 }  // namespace se

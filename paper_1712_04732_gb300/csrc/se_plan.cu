@@ -838,7 +838,9 @@ se_status plan_build(se_plan_s *p)
     }
     if ((st = plan_set_fft_stream(p)) != SE_OK) return st;
     encode_gout_map(p);
-    return SE_OK;
+    if (p->D == 1 && p->lines_requested)
+        st = p->dtype == SE_F32 ? Ops<float>::build_lines1p(p) : Ops<double>::build_lines1p(p);
+    return st;
 }
 
 se_status plan_reserve(se_plan_s *p, int64_t n)
@@ -918,8 +920,10 @@ void plan_release(se_plan_s *p)
                      &p->scratch, (void **)&p->tile_cnt, (void **)&p->tile_off, (void **)&p->tile_part,
                      (void **)&p->red, (void **)&p->err, (void **)&p->counters, (void **)&p->tile_rank, &p->prt.frac_q,
                      (void **)&p->prt.idx_anc, &p->io_buf, &p->grid_in2, &p->grid_out2, &p->spec_d, &p->U_d, &p->Z_d,
-                     &p->grid_d, &p->ztw, (void **)&p->chunk_map, (void **)&p->heavy_tiles};
+                     &p->grid_d, &p->ztw, (void **)&p->chunk_map, (void **)&p->heavy_tiles, &p->l1p_desc,
+                     &p->l1p_items, &p->l1p_tw};
     for (void **b : bufs) dev_free(p, b);
+    p->lines1p = false;
 }
 
 }  // namespace se
