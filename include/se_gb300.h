@@ -112,7 +112,7 @@ typedef struct {
                            class, their padding (Alg. 1, Alg. 2) and the scaling as three
                            line-transform launches (padded rows and columns that are zero or
                            cut are never transformed) between cuFFT's x transforms, when
-                           every free-direction length is at most 2048; otherwise as 0 */
+                           every free-direction length is at most 1024; otherwise as 0 */
     int    fft_sizes;   /* [<= 0] free-direction transform lengths: the smallest the rules of
                            Sec. 3.3 and Sec. 6 allow; 1 each of M~_i, s0 M~_i and s M~_i rounded
                            up to the next even length whose prime factors are 2, 3, 5 and 7

@@ -33,8 +33,8 @@
 namespace se {
 
 constexpr int kLineThreads = 256;
-constexpr int kLineElems = 2048;     // complex values per shared-memory buffer
-constexpr int kMaxLines = 1024;      // lines (row pairs) per CTA
+constexpr int kLineElems = 1024;     // complex values per shared-memory buffer
+constexpr int kMaxLines = 512;       // lines (row pairs) per CTA
 constexpr int kFftMaxFactors = 16;
 
 enum LinePass { kPassXF = 0, kPassYF = 1, kPassZ = 2, kPassYI = 3, kPassXI = 4 };
@@ -145,7 +145,7 @@ __device__ __forceinline__ C cscale(C a, T f)
 
 // In-register R-point DFT y_t = sum_u v_u exp(s 2 pi i u t / R), s = -1 forward,
 // +1 inverse, written out from the definition with the symmetric sums of
-// u and R - u (R = 2, 3, 4, 5).
+// u and R - u (R = 2, 3, 4, 5, 7).
 template <int R, typename C, typename T>
 __device__ __forceinline__ void small_dft(C *v, T s)
 {
@@ -168,8 +168,39 @@ __device__ __forceinline__ void small_dft(C *v, T s)
         v[0] = cadd(v[0], t1);
         v[1] = cadd(t2, t3);
         v[2] = csub(t2, t3);
+    } else if constexpr (R == 7) {
+        // y_k = v0 + sum_u (v_u + v_{7-u}) cos(2 pi u k / 7) + i s (v_u - v_{7-u}) sin(2 pi u k / 7)
+        const T c[4] = {T(1), T(0.62348980185873353053), T(-0.22252093395631440429), T(-0.90096886790241912624)};
+        const T sn[4] = {T(0), T(0.78183148246802980871), T(0.97492791218182360702), T(0.43388373911755812048)};
+        C t[4], d[4];
+#pragma unroll
+        for (int u = 1; u <= 3; ++u) {
+            t[u] = cadd(v[u], v[7 - u]);
+            d[u] = csub(v[u], v[7 - u]);
+        }
+        const C v0 = v[0];
+        v[0] = cadd(v0, cadd(t[1], cadd(t[2], t[3])));
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) {
+            C a = v0, b;
+            b.x = T(0);
+            b.y = T(0);
+#pragma unroll
+            for (int u = 1; u <= 3; ++u) {
+                const int m = (u * k) % 7;
+                const T cm = m <= 3 ? c[m] : c[7 - m];
+                const T sm = m <= 3 ? sn[m] : -sn[7 - m];
+                a.x += cm * t[u].x;
+                a.y += cm * t[u].y;
+                b.x += sm * d[u].x;
+                b.y += sm * d[u].y;
+            }
+            const C ib = qturn(b, s);
+            v[k] = cadd(a, ib);
+            v[7 - k] = csub(a, ib);
+        }
     } else {
-        static_assert(R == 5, "radix 2, 3, 4 or 5");
+        static_assert(R == 5, "radix 2, 3, 4, 5 or 7");
         const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);   // cos(2 pi/5), cos(4 pi/5)
         const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);    // sin(2 pi/5), sin(4 pi/5)
         const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
@@ -192,7 +223,7 @@ __device__ __forceinline__ void small_dft(C *v, T s)
     }
 }
 
-// One Stockham pass of radix R (2, 3, 4, 5) over nl lines: butterfly j of a
+// One Stockham pass of radix R (2, 3, 4, 5, 7) over nl lines: butterfly j of a
 // line takes the inputs j + u n/R, multiplies input u by exp(-+2 pi i u (j mod
 // Ns) n / (Ns R) / n), runs the R-point DFT and writes output t to
 // (j - j mod Ns) R + j mod Ns + t Ns.
@@ -229,7 +260,7 @@ __device__ __forceinline__ void stockham_pass_r(const typename Cplx<T>::type *a,
 
 // nl transforms of length L.n held contiguously in a (nl L.n values); the
 // result ends in a or b, returned.  tw: the n-th roots in shared memory.
-// Radices 2-5 take the in-register butterflies; any other radix (7, other
+// Radices 2-5 and 7 take the in-register butterflies; any other radix (larger
 // primes) forms each output as one sum of R products with the twiddle
 // exp(-+2 pi i u c / n), c = (j mod Ns) n / (Ns R) + t n / R.
 template <typename T>
@@ -246,6 +277,7 @@ __device__ typename Cplx<T>::type *line_fft(typename Cplx<T>::type *a, typename 
         else if (R == 2) stockham_pass_r<2, T>(a, b, nl, n, Ns, tw, inv);
         else if (R == 3) stockham_pass_r<3, T>(a, b, nl, n, Ns, tw, inv);
         else if (R == 5) stockham_pass_r<5, T>(a, b, nl, n, Ns, tw, inv);
+        else if (R == 7) stockham_pass_r<7, T>(a, b, nl, n, Ns, tw, inv);
         else {
             const int nR = n / R, step = n / (Ns * R);
             const FDiv dR(nR), dN(Ns);
