@@ -97,7 +97,7 @@ typedef struct {
                            edge 8, P = 8 or 10) the staged block with four particles per warp
                            over chunks of at most 256 particles; 4 (FP32, same conditions) the
                            staged block with one particle per warp over the same chunks, which
-                           by default FP32 plans of that kind with 64 or more particles per tile
+                           by default FP32 plans of that kind with 32 or more particles per tile
                            take (the others mode 2) */
     int    split;       /* [<= 0] CTAs per tile for spread_mode 2 / gather_mode 1 (1..8) */
     int    force_method; /* [<= 0 -> 1] how se_force differentiates (Sec. 7.2): 1 gathers with

@@ -17,7 +17,7 @@ constexpr int kMaxNu = 12;      // largest PKB degree accepted
 constexpr int kThreads = 256;   // threads per CTA of the tile kernels
 constexpr int kGatherChunk = 256;  // particles per CTA of the tile-staged FP32 gathering (one round per warp)
 constexpr int kHeavyTile = 1536;   // FP32 gridding: tiles with more particles get a cluster of 8 CTAs
-constexpr int kTileGatherMean = 64;  // FP32 gathering: staged tiles from this many particles per tile on average
+constexpr int kTileGatherMean = 32;  // FP32 gathering: staged tiles from this many particles per tile on average
 
 // Row pitch (elements) of a gridding block in shared memory: the smallest
 // pitch >= B0 for which the gridding kernels' access pattern -- a warp's lanes

@@ -727,7 +727,7 @@ se_status Ops<T>::gather(se_plan_s *p, int64_t N, const T *q, T *phi, T *F, doub
     const int nu = p->window == SE_WIN_PKB ? p->nu : nu_default(p->P);
     // FP32 with edge-8 tiles (default mode): the tile-staged kernel; mode 2 reads the
     // grid directly, mode 1 is the generic staged kernel
-    // with P = 8 or 10 and at least 64 particles per tile on average, and mode 2 reads
+    // with P = 8 or 10 and at least kTileGatherMean (32) particles per tile on average, and mode 2 reads
     // the grid directly (the default otherwise); mode 1 is the generic staged kernel
     const bool fast = use_tile_gather<T>(p, N);
     const bool flat = !fast && p->gather_mode != 1;

@@ -127,7 +127,7 @@ def test_fused_form_matches_per_system_calls(dtype):
     plain se_force per system on the same plans.  The gridding blocks are
     fixed-point sums (exact in any order) and the merge order is fixed.  In
     FP64 the gathering is the same code in both, so potentials and forces are
-    bitwise equal; an FP32 se_force of a system with 64 or more particles per
+    bitwise equal; an FP32 se_force of a system with 32 or more particles per
     tile takes the tile-staged gathering, which sums the same products in
     another order, so FP32 agrees to rounding.  Graph replays are bitwise
     equal; the energy sums per-CTA partials over the sorted records, whose order
