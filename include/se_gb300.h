@@ -69,7 +69,10 @@ typedef enum {
 #define SE_SYNC_CHECK    4u  /* synchronise at the end and report device-side input errors */
 #define SE_HOST_IO       8u  /* x, q and the outputs are HOST pointers; the call copies
                                 them to and from the device on the plan's stream and
-                                returns after the results are in host memory.  With
+                                returns after the results are in host memory (page-locked
+                                x and q are read in place by the binning's first kernel,
+                                which writes the device copies, so the transfer overlaps
+                                the counting; without SE_CHECK_NEUTRAL).  With
                                 page-locked buffers (and without SE_CHECK_NEUTRAL or
                                 profiling) the call -- copies included -- is captured
                                 into a CUDA graph the first time and replayed while the

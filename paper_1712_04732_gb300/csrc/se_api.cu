@@ -61,6 +61,18 @@ static int smooth_even_up(int n)
     }
 }
 
+// True when ptr is page-locked host memory that kernels can read at the same
+// address (unified addressing); such input is read in place by the binning.
+static bool device_readable(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == ptr;
+}
+
 // Internal call flag: the call is being captured into a graph (no synchronisation).
 constexpr unsigned kInCapture = 1u << 30;
 
@@ -79,17 +91,27 @@ static se_status run(se_plan_s *p, int64_t N, const void *x, const void *q, void
     double *den = energy;
     const bool host = flags & SE_HOST_IO;
     cudaError_t e = cudaSuccess;
+    // page-locked x and q that the GPU reads at their own addresses: the counting
+    // pass of the binning reads them there and writes the device copies itself
+    bool direct = false;
+    T *cx = nullptr, *cq = nullptr;
     if (host) {
         if ((st = plan_io_reserve(p, N)) != SE_OK) return st;
         T *b = static_cast<T *>(p->io_buf);
         T *bx = b, *bq = b + 3 * N, *bphi = b + 4 * N, *bF = b + 5 * N;
         double *ben = reinterpret_cast<double *>(b + 8 * N);
-        if ((e = cudaMemcpyAsync(bx, x, sizeof(T) * 3 * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
-            return cuda_fail(e, "copy x");
-        if ((e = cudaMemcpyAsync(bq, q, sizeof(T) * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
-            return cuda_fail(e, "copy q");
-        dx = bx;
-        dq = bq;
+        direct = !(flags & SE_CHECK_NEUTRAL) && device_readable(x) && device_readable(q);
+        if (direct) {
+            cx = bx;
+            cq = bq;
+        } else {
+            if ((e = cudaMemcpyAsync(bx, x, sizeof(T) * 3 * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+                return cuda_fail(e, "copy x");
+            if ((e = cudaMemcpyAsync(bq, q, sizeof(T) * N, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+                return cuda_fail(e, "copy q");
+            dx = bx;
+            dq = bq;
+        }
         dphi = phi ? bphi : nullptr;
         dF = F ? bF : nullptr;
         den = energy ? ben : nullptr;
@@ -104,7 +126,11 @@ static se_status run(se_plan_s *p, int64_t N, const void *x, const void *q, void
             return fail(SE_ENONNEUTRAL, "sum of charges " + std::to_string(sums[0]) + " is not zero");
     }
     prof_mark(p, 0);
-    if ((st = Ops<T>::bin(p, N, dx, dq)) != SE_OK) return st;
+    if ((st = Ops<T>::bin(p, N, dx, dq, cx, cq)) != SE_OK) return st;
+    if (direct) {
+        dx = cx;
+        dq = cq;
+    }
     if ((st = Ops<T>::spread(p, N, nullptr, p->grid_in)) != SE_OK) return st;
     if (grad && p->force_method == 2) {
         // Sec. 7.2, method 2: i k in the scaling, four inverse transforms, gathering with W

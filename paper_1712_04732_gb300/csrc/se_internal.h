@@ -286,8 +286,10 @@ se_status noalloc_scratch_address(int dev, void **out);
 // per-precision launchers (se_kern_f32.cu / se_kern_f64.cu)
 template <typename T>
 struct Ops {
-    // stage: bin particles into tiles, sort them; x, q device arrays
-    static se_status bin(se_plan_s *p, int64_t N, const T *x, const T *q);
+    // stage: bin particles into tiles, sort them; x, q device arrays (or, with
+    // xcopy and qcopy, memory the GPU can read, copied there by the counting pass)
+    static se_status bin(se_plan_s *p, int64_t N, const T *x, const T *q, T *xcopy = nullptr,
+                         T *qcopy = nullptr);
     // spread the sorted particles (or the charges g instead of q when g != nullptr)
     // into grid `dst` (the forward-FFT input layout)
     static se_status spread(se_plan_s *p, int64_t N, const T *g, void *dst);

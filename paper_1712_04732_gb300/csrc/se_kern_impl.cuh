@@ -71,7 +71,7 @@ static bool want_lists(const se_plan_s *p, int64_t N)
 }
 
 template <typename T>
-se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
+se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q, T *xcopy, T *qcopy)
 {
     const int nt = p->tg.nt[0] * p->tg.nt[1] * p->tg.nt[2];
     cudaError_t e = cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * (nt + 1), p->stream);
@@ -90,8 +90,12 @@ se_status Ops<T>::bin(se_plan_s *p, int64_t N, const T *x, const T *q)
     k_bin_count<T><<<blocks_for(N, 256), 256, 0, p->stream>>>(a, N, x, q, p->tile_cnt, p->tile_rank, p->err, nt,
                                                                p->tile_off, p->counters, !local_scan && !scan_kernel,
                                                                false, nullptr, p->counters + 2, p->heavy_tiles,
-                                                               p->counters + 3);
+                                                               p->counters + 3, xcopy, qcopy);
     SE_LAUNCH_CHECK("bin_count");
+    if (xcopy) {                                           // the later stages read the device copies
+        x = xcopy;
+        q = qcopy;
+    }
     if (scan_kernel) {
         const size_t ssm = sizeof(int) * size_t(nt + 1);
         if ((e = allow_smem(k_scan_lists, ssm)) != cudaSuccess) return cuda_fail(e, "scan smem attribute");

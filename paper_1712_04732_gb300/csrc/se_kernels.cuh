@@ -233,12 +233,15 @@ static __global__ void __launch_bounds__(1024) k_work_lists(int nt, const int *_
 // the CTA that finishes last (otherwise k_bin_scatter scans the counts itself);
 // with staged_scan that CTA scans in (ntiles + 1) ints of dynamic shared memory
 // and, when cmap is given, also writes the work lists of the FP32 tile kernels.
+// With xcopy and qcopy, the positions and charges as read are also written
+// there (x and q may then be page-locked host memory the GPU reads directly:
+// the transfer overlaps the counting, and the later stages read the copies).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restrict__ q, int *__restrict__ cnt,
             int2 *__restrict__ tile_rank, int *err, int ntiles, int *__restrict__ off, int *done, bool scan_last,
             bool staged_scan, int2 *__restrict__ cmap, int *__restrict__ ncmap, int *__restrict__ heavy,
-            int *__restrict__ nheavy)
+            int *__restrict__ nheavy, T *__restrict__ xcopy, T *__restrict__ qcopy)
 {
     __shared__ int part[256];
     __shared__ int carry;
@@ -248,6 +251,12 @@ k_bin_count(BinArgs<T> a, int64_t N, const T *__restrict__ x, const T *__restric
     if (i < N) {
         T xp[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
         T qv = q[i];
+        if (xcopy) {
+            xcopy[3 * i] = xp[0];
+            xcopy[3 * i + 1] = xp[1];
+            xcopy[3 * i + 2] = xp[2];
+            qcopy[i] = qv;
+        }
         int anc[3];
         T frac[3];
         locate(a, xp, qv, anc, frac, err);
