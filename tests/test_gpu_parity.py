@@ -263,6 +263,29 @@ def test_host_io_path_equals_device_path():
     assert eh.item() == pytest.approx(En, rel=1e-6)
 
 
+@pytest.mark.parametrize("D", [3, 1])
+def test_host_io_page_locked_inputs_read_in_place_fp64(D):
+    """FP64 SE_HOST_IO calls with page-locked x and q (read in place by the
+    counting pass, which writes the device copies) against the device path:
+    the same kernels on the same values, so the results agree to the last bits
+    of the energy's summation order."""
+    se = _se()
+    N = 2000
+    x = wl.uniform_positions(N, 1.0, 40 + D)
+    q = wl.uniform_charges(N, 40 + D)
+    plan = se.Plan(D, 1.0, 6.0, 24, 8, "pkb", dtype=torch.float64)
+    F, phi, En = _run(plan, x, q)
+    xh = torch.tensor(x, dtype=torch.float64).pin_memory()
+    qh = torch.tensor(q, dtype=torch.float64).pin_memory()
+    Fh = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    ph = torch.empty(N, dtype=torch.float64).pin_memory()
+    eh = torch.empty((), dtype=torch.float64).pin_memory()
+    for _ in range(2):                               # eager capture, then the replayed graph
+        plan.force_host(xh, qh, Fh, ph, eh)
+        assert np.array_equal(ph.numpy(), phi) and np.array_equal(Fh.numpy(), F)
+        assert eh.item() == pytest.approx(En, rel=1e-13)
+
+
 def test_host_io_graph_replay_follows_new_contents_and_buffers():
     """Repeated SE_HOST_IO calls on the same page-locked buffers replay a captured
     graph: new contents written into the buffers between calls must be read
