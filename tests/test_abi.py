@@ -136,3 +136,26 @@ def test_allocation_failure_hook_is_host_only(lib):
     """Arming and disarming the injected allocation failure touches no GPU."""
     assert lib.se_debug_fail_alloc(3) == 0
     assert lib.se_debug_fail_alloc(0) == 0
+
+
+@pytest.mark.parametrize("field,value", [("fft_mode", 3), ("gather_mode", 5), ("force_method", 3)])
+def test_plan_create_rejects_bad_options(lib, field, value):
+    """Options out of range are refused on the host, before any device work:
+    fft_mode 0 (default), 1 (cuFFT everywhere) or 2 (D = 1 line transforms);
+    gather_mode up to 4; force_method 1 or 2."""
+    o = nat.Opts()
+    lib.se_opts_default(ctypes.byref(o))
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    assert lib.se_plan_create(ctypes.byref(h), b, 1, 8.0, 32, 8, nat.SE_WIN_PKB, nat.SE_F32, ctypes.byref(o)) == 1
+    assert not h.value
+    assert field.split("_")[0] in lib.se_last_error().decode()
+
+
+def test_batch_form_flags_are_distinct_bits():
+    flags = [nat.SE_BATCH_NO_AUTOTUNE, nat.SE_BATCH_BRANCHES, nat.SE_BATCH_FUSED, nat.SE_BATCH_LINES]
+    assert flags == [1, 2, 4, 8]
+    src = open(HEADER).read()
+    for name, v in zip(("SE_BATCH_NO_AUTOTUNE", "SE_BATCH_BRANCHES", "SE_BATCH_FUSED", "SE_BATCH_LINES"), flags):
+        assert re.search(rf"#define {name}\s+{v}u", src), name
